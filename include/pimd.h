@@ -1,0 +1,196 @@
+/*
+ * pimd.h -- C ABI of the GB300 bosonic / fictitious-particle PIMD hot path.
+ *
+ * Method: X. Xiong, "GPU acceleration of ab initio simulations of large-scale
+ * identical particles based on path integral molecular dynamics",
+ * arXiv 2404.02628.  Units hbar = m = k_B = 1 (Sec. IV A).
+ *
+ * The library computes, per MD step, for N particles of P beads in d
+ * dimensions at inverse temperature beta and exchange parameter xi in [0,1]:
+ *   (a1) ring-polymer springs and the spring-energy total     (Sec. III, E_int, E^[v,v])
+ *   (a2) the exchange recursions for V_xi^[1,N]                  (Sec. III, forward and
+ *                                                                 backward recursions)
+ *   (a3) connection probabilities -> endpoint-bead forces       (Sec. III, Pr[G(l)=l'],
+ *                                                                 exterior-bead forces)
+ *   (a4) harmonic trap + same-slice Gaussian pair forces         (Sec. II U; Sec. IV B)
+ *   (a5) velocity Verlet with massive Nose-Hoover chains         (Sec. IV A)
+ * The MD samples exp(-beta (V_xi + U/P)) (Sec. II, discretised Z).
+ *
+ * Conventions for every entry point:
+ *  - All device memory belongs to the caller.  Pointers named "device" must
+ *    be CUDA device pointers on the current device; the library never calls
+ *    cudaMalloc or cudaFree.  Host pointers are plain host memory.
+ *  - Work is enqueued on the stream given to pimd_bind / the call and is
+ *    asynchronous, except calls that return host data, which synchronise
+ *    that stream.
+ *  - Errors are returned as pimd_status; no call aborts or throws.  A
+ *    human-readable message for the last failure on a handle is available
+ *    from pimd_last_error (pimd_global_error for failures before a handle
+ *    exists).  Device-side failures (a bounded cross-block wait that gave up)
+ *    are recorded in the workspace and reported by the next synchronising
+ *    call as PIMD_ETIMEOUT.
+ *  - Bead arrays are slice-major FP64: element (bead j, component c,
+ *    particle l) of an array x lives at x[(j*d + c)*n_pad + l], 0-based,
+ *    n_pad >= N a multiple of 32; padding entries are never read.
+ *    Thermostat arrays add a leading chain index k: x[((k*P + j)*d + c)*n_pad + l].
+ */
+#ifndef PIMD_H
+#define PIMD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PIMD_OK = 0,
+    PIMD_EINVAL = 1,      /* bad argument (range, null pointer, size, alignment) */
+    PIMD_ENOMEM = 2,      /* caller-provided workspace too small                 */
+    PIMD_ECUDA = 3,       /* a CUDA runtime call failed                          */
+    PIMD_ETIMEOUT = 4,    /* a bounded cross-block wait gave up on the device    */
+    PIMD_ENONFINITE = 5,  /* an energy or force came out NaN/Inf                 */
+    PIMD_ESTATE = 6       /* call out of order (e.g. not bound yet)              */
+} pimd_status;
+
+enum { PIMD_PREC_FP64 = 0, PIMD_PREC_MIXED = 1 };
+/* Gaussian amplitude A in V_pair = A exp(-r^2/s^2): PAPER uses A = g/(pi s^2)
+ * as printed in the Hamiltonian of Sec. IV B; RAW uses A = g. */
+enum { PIMD_AMP_PAPER = 0, PIMD_AMP_RAW = 1 };
+/* Exchange kernel factors exp(-kappa |r_l^P - r_u^1|^2): STORE keeps all
+ * N(N+1)/2 of them in the workspace for one step (12 bytes each); RECOMPUTE
+ * keeps O(N * 32) and recomputes the rest where they are used. */
+enum { PIMD_TABLE_STORE = 0, PIMD_TABLE_RECOMPUTE = 1 };
+
+typedef struct pimd_ctx* pimd_t;
+
+typedef struct {
+    double dt;          /* MD time step (default 0.01)                                  */
+    int nhc_len;        /* Nose-Hoover chain length M >= 1 (default 4)                  */
+    double nhc_Q;       /* thermostat mass; <= 0 selects kT/omega_P^2 = beta/P (default) */
+    double mass;        /* bead mass m' of the dynamics (default 1)                     */
+    int precision;      /* PIMD_PREC_FP64 (default) or PIMD_PREC_MIXED: springs and pair
+                           forces in FP32 (FP64 masters, FP64 accumulation of energies);
+                           recursion, probabilities and estimators always FP64          */
+    int amp_convention; /* PIMD_AMP_PAPER (default) or PIMD_AMP_RAW                     */
+    int table_mode;     /* PIMD_TABLE_STORE (default) or PIMD_TABLE_RECOMPUTE           */
+    int thermostat;     /* 1 = massive NHC (default), 0 = plain velocity Verlet (NVE)   */
+    int helper_ctas;    /* exchange-recursion helper blocks; 0 = one per SM (default)   */
+    int spin_limit;     /* polls before a cross-block wait gives up; 0 = default (~1e7) */
+} pimd_config;
+
+typedef struct {
+    double* r;          /* device, [P][d][n_pad] bead positions                          */
+    double* p;          /* device, [P][d][n_pad] momenta                                 */
+    double* f;          /* device, [P][d][n_pad] forces -grad(V_xi + U/P), written here  */
+    double* eta;        /* device, [M][P][d][n_pad] thermostat positions                 */
+    double* peta;       /* device, [M][P][d][n_pad] thermostat momenta                   */
+    void* work;         /* device workspace, 256-byte aligned                             */
+    size_t work_bytes;  /* its size, at least pimd_workspace_bytes()                      */
+    int n_pad;          /* leading dimension of the bead arrays                           */
+} pimd_buffers;
+
+/* Per-configuration scalars (Sec. III, Sec. IV; the estimator formulas are
+ * not printed in the paper -- see the primitive/virial readings below). */
+typedef struct {
+    double E_prim;      /* P d N/(2 beta) - spring + U/P                                 */
+    double E_vir;       /* U/P + (1/2P) sum_{l,j} r_l^j . grad U                          */
+    double V_xi;        /* V_xi^[1,N] from the forward recursion                          */
+    double U_over_P;    /* (trap + pair energy summed over slices) / P                   */
+    double kinetic;     /* sum p^2 / (2 m')                                               */
+    double spring;      /* expected connected spring energy sum E_int + sum Pr 1/2 k |dr|^2 */
+    double H_conserved; /* kinetic + V_xi + U/P + sum (p_eta^2/(2Q) + eta/beta)           */
+    double virial;      /* sum_{l,j} r_l^j . grad U                                       */
+    double V_xi_bwd;    /* V_xi^[1,N] from the backward recursion (equals V_xi)           */
+    long long step;     /* MD steps taken since pimd_bind / pimd_set_state                */
+} pimd_estimates;
+
+/* ---- single system ------------------------------------------------------ */
+
+/* Creates a context for N particles, P >= 2 beads, d in {1,2,3}, beta > 0,
+ * trap frequency omega >= 0, Gaussian strength g and width s > 0 (Sec. IV B,
+ * width w read as s), xi in [0,1] (Sec. II; 0^0 = 1).  *out receives the
+ * handle.  PIMD_EINVAL on a bad argument.  Host only; no GPU work. */
+pimd_status pimd_create(int N, int P, int d, double beta, double omega, double g, double s,
+                        double xi, pimd_t* out);
+
+/* Fills *cfg with the defaults listed in pimd_config. */
+void pimd_default_config(pimd_config* cfg);
+
+/* Replaces the configuration (before pimd_bind; PIMD_ESTATE after). */
+pimd_status pimd_configure(pimd_t ctx, const pimd_config* cfg);
+
+/* Workspace bytes the caller must provide for n_pad (depends on N, P, d, M,
+ * table mode and the device's SM count).  Host only. */
+pimd_status pimd_workspace_bytes(pimd_t ctx, int n_pad, size_t* bytes);
+
+/* Binds caller-owned device buffers and a CUDA stream (cudaStream_t, may be
+ * NULL for the legacy default stream).  Zeroes the thermostat arrays and the
+ * step counter; r and p must already hold the initial state.  Computes the
+ * forces of r (asynchronously).  Captures the per-step CUDA graph on first
+ * pimd_step, so bind before any capture of the caller's own. */
+pimd_status pimd_bind(pimd_t ctx, const pimd_buffers* bufs, void* stream);
+
+/* Recomputes F = -grad(V_xi + U/P) for the bound r.  If V_total_out (host)
+ * is non-NULL, synchronises and stores V_xi + U/P there. */
+pimd_status pimd_forces(pimd_t ctx, double* V_total_out);
+
+/* Runs only the exchange part (a1-a3; springs, recursion, probabilities):
+ * f_out (device, bead layout) = -grad V_xi.  V_out (host, nullable): V_xi. */
+pimd_status pimd_exchange_forces(pimd_t ctx, double* f_out, double* V_out);
+
+/* Runs only the interaction part (a4; trap + pairs): f_out = -grad(U/P),
+ * U_out (host, nullable): U/P. */
+pimd_status pimd_interaction_forces(pimd_t ctx, double* f_out, double* U_out);
+
+/* Advances nsteps >= 0 MD steps (Sec. IV A; order per step:
+ * NHC(dt/2), p += F dt/2, r += p dt/m', forces, p += F dt/2, NHC(dt/2)),
+ * replaying one captured CUDA graph per step. */
+pimd_status pimd_step(pimd_t ctx, int nsteps);
+
+/* Same step sequence without the CUDA graph (plain launches). */
+pimd_status pimd_step_eager(pimd_t ctx, int nsteps);
+
+/* Estimators of the current state (synchronises).  PIMD_ENONFINITE if any
+ * field is NaN/Inf, PIMD_ETIMEOUT if a device wait gave up since the last
+ * check. */
+pimd_status pimd_estimators(pimd_t ctx, pimd_estimates* out);
+
+/* Host blob with r, p, eta, p_eta and the step counter. */
+pimd_status pimd_state_bytes(pimd_t ctx, size_t* bytes);
+pimd_status pimd_get_state(pimd_t ctx, void* host_blob, size_t bytes);   /* synchronises */
+pimd_status pimd_set_state(pimd_t ctx, const void* host_blob, size_t bytes); /* then forces */
+
+/* Synchronises the bound stream and reports device-side errors. */
+pimd_status pimd_sync(pimd_t ctx);
+
+const char* pimd_last_error(pimd_t ctx);
+const char* pimd_global_error(void);
+void pimd_destroy(pimd_t ctx);
+
+/* ---- exchange potential alone (for autograd) --------------------------- */
+/*
+ * V_ends(r^1, r^P) = V_xi^[1,N] - sum_l E_int^(l): the part of the exchange
+ * potential (Sec. III) that depends on the endpoint beads only, for spring
+ * constant k = P/beta^2 (so the caller supplies P).  r1 and rP are device
+ * arrays [d][ld] (component c of particle l at c*ld + l), ld >= N.
+ */
+typedef struct pimd_vb* pimd_vb_t;
+
+pimd_status pimd_vb_create(int N, int P, int d, double beta, double xi, pimd_vb_t* out);
+pimd_status pimd_vb_workspace_bytes(pimd_vb_t h, size_t* bytes);
+/* V_out: device double.  Saves the recursion state in work for backward. */
+pimd_status pimd_vb_forward(pimd_vb_t h, const double* r1, const double* rP, int ld,
+                            void* work, size_t work_bytes, double* V_out, void* stream);
+/* Adjoint (Sec. III connection probabilities): g_r1 = gV * dV_ends/dr^1 and
+ * g_rP = gV * dV_ends/dr^P ([d][ld], overwritten).  gV: device double.
+ * Must follow pimd_vb_forward on the same arrays and workspace. */
+pimd_status pimd_vb_backward(pimd_vb_t h, const double* r1, const double* rP, int ld,
+                             void* work, size_t work_bytes, const double* gV,
+                             double* g_r1, double* g_rP, void* stream);
+void pimd_vb_destroy(pimd_vb_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PIMD_H */

@@ -1,0 +1,339 @@
+"""GB300-native bosonic / fictitious-particle PIMD hot path (arXiv 2404.02628).
+
+Thin ctypes binding of the C ABI declared in ``include/pimd.h``.  Every step
+of the path runs in the sm_103a kernels of ``_build/libpimd.so``; this module
+only marshals arguments.  PyTorch provides device memory and streams.  There
+is no CPU fallback: if the library is missing or no GPU is present, the calls
+raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+__all__ = [
+    "PIMD_OK", "PimdError", "Config", "Buffers", "Estimates", "lib", "load", "symbols",
+    "pimd_create", "pimd_default_config", "pimd_configure", "pimd_workspace_bytes", "pimd_bind",
+    "pimd_forces", "pimd_exchange_forces", "pimd_interaction_forces", "pimd_step", "pimd_step_eager",
+    "pimd_estimators", "pimd_state_bytes", "pimd_get_state", "pimd_set_state", "pimd_sync",
+    "pimd_last_error", "pimd_global_error", "pimd_destroy", "pimd_vb_create", "pimd_vb_workspace_bytes",
+    "pimd_vb_forward", "pimd_vb_backward", "pimd_vb_destroy", "System",
+]
+
+PIMD_OK, PIMD_EINVAL, PIMD_ENOMEM, PIMD_ECUDA, PIMD_ETIMEOUT, PIMD_ENONFINITE, PIMD_ESTATE = range(7)
+STATUS_NAMES = {0: "PIMD_OK", 1: "PIMD_EINVAL", 2: "PIMD_ENOMEM", 3: "PIMD_ECUDA", 4: "PIMD_ETIMEOUT",
+                5: "PIMD_ENONFINITE", 6: "PIMD_ESTATE"}
+PREC_FP64, PREC_MIXED = 0, 1
+AMP_PAPER, AMP_RAW = 0, 1
+TABLE_STORE, TABLE_RECOMPUTE = 0, 1
+
+LIB_PATH = _build.LIB
+
+
+class PimdError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("nhc_len", ctypes.c_int), ("nhc_Q", ctypes.c_double),
+                ("mass", ctypes.c_double), ("precision", ctypes.c_int), ("amp_convention", ctypes.c_int),
+                ("table_mode", ctypes.c_int), ("thermostat", ctypes.c_int), ("helper_ctas", ctypes.c_int),
+                ("spin_limit", ctypes.c_int)]
+
+
+class Buffers(ctypes.Structure):
+    _fields_ = [("r", ctypes.c_void_p), ("p", ctypes.c_void_p), ("f", ctypes.c_void_p),
+                ("eta", ctypes.c_void_p), ("peta", ctypes.c_void_p), ("work", ctypes.c_void_p),
+                ("work_bytes", ctypes.c_size_t), ("n_pad", ctypes.c_int)]
+
+
+class Estimates(ctypes.Structure):
+    _fields_ = [("E_prim", ctypes.c_double), ("E_vir", ctypes.c_double), ("V_xi", ctypes.c_double),
+                ("U_over_P", ctypes.c_double), ("kinetic", ctypes.c_double), ("spring", ctypes.c_double),
+                ("H_conserved", ctypes.c_double), ("virial", ctypes.c_double), ("V_xi_bwd", ctypes.c_double),
+                ("step", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+
+_SIGS = {
+    "pimd_create": ([ctypes.c_int] * 3 + [ctypes.c_double] * 5 + [ctypes.POINTER(_vp)], ctypes.c_int),
+    "pimd_default_config": ([ctypes.POINTER(Config)], None),
+    "pimd_configure": ([_vp, ctypes.POINTER(Config)], ctypes.c_int),
+    "pimd_workspace_bytes": ([_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "pimd_bind": ([_vp, ctypes.POINTER(Buffers), _vp], ctypes.c_int),
+    "pimd_forces": ([_vp, _dp], ctypes.c_int),
+    "pimd_exchange_forces": ([_vp, _vp, _dp], ctypes.c_int),
+    "pimd_interaction_forces": ([_vp, _vp, _dp], ctypes.c_int),
+    "pimd_step": ([_vp, ctypes.c_int], ctypes.c_int),
+    "pimd_step_eager": ([_vp, ctypes.c_int], ctypes.c_int),
+    "pimd_estimators": ([_vp, ctypes.POINTER(Estimates)], ctypes.c_int),
+    "pimd_state_bytes": ([_vp, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "pimd_get_state": ([_vp, _vp, ctypes.c_size_t], ctypes.c_int),
+    "pimd_set_state": ([_vp, _vp, ctypes.c_size_t], ctypes.c_int),
+    "pimd_sync": ([_vp], ctypes.c_int),
+    "pimd_last_error": ([_vp], ctypes.c_char_p),
+    "pimd_global_error": ([], ctypes.c_char_p),
+    "pimd_destroy": ([_vp], None),
+    "pimd_vb_create": ([ctypes.c_int] * 3 + [ctypes.c_double] * 2 + [ctypes.POINTER(_vp)], ctypes.c_int),
+    "pimd_vb_workspace_bytes": ([_vp, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "pimd_vb_forward": ([_vp, _vp, _vp, ctypes.c_int, _vp, ctypes.c_size_t, _vp, _vp], ctypes.c_int),
+    "pimd_vb_backward": ([_vp, _vp, _vp, ctypes.c_int, _vp, ctypes.c_size_t, _vp, _vp, _vp, _vp], ctypes.c_int),
+    "pimd_vb_destroy": ([_vp], None),
+}
+
+
+def symbols():
+    """Names of every entry point declared in include/pimd.h that the binding wraps."""
+    return list(_SIGS)
+
+
+def load(path=None):
+    """Load the C-ABI library (no compilation, no GPU needed to load)."""
+    global _lib
+    if _lib is None:
+        path = path or LIB_PATH
+        if not os.path.exists(path):
+            raise RuntimeError("libpimd.so is not built (run __graft_entry__.build()); no CPU fallback exists")
+        L = ctypes.CDLL(path)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def lib():
+    return load()
+
+
+def _check(status, handle=None):
+    if status != PIMD_OK:
+        L = lib()
+        msg = L.pimd_last_error(handle) if handle else L.pimd_global_error()
+        raise PimdError(status, (msg or b"").decode())
+    return status
+
+
+# ---- one-to-one wrappers (same names as the C ABI) ------------------------
+
+def pimd_create(N, P, d, beta, omega, g, s, xi):
+    h = _vp()
+    _check(lib().pimd_create(N, P, d, beta, omega, g, s, xi, ctypes.byref(h)))
+    return h
+
+
+def pimd_default_config():
+    c = Config()
+    lib().pimd_default_config(ctypes.byref(c))
+    return c
+
+
+def pimd_configure(h, cfg):
+    return _check(lib().pimd_configure(h, ctypes.byref(cfg)), h)
+
+
+def pimd_workspace_bytes(h, n_pad):
+    n = ctypes.c_size_t()
+    _check(lib().pimd_workspace_bytes(h, n_pad, ctypes.byref(n)), h)
+    return n.value
+
+
+def pimd_bind(h, bufs, stream):
+    return _check(lib().pimd_bind(h, ctypes.byref(bufs), stream), h)
+
+
+def pimd_forces(h, want_value=True):
+    v = ctypes.c_double()
+    _check(lib().pimd_forces(h, ctypes.byref(v) if want_value else None), h)
+    return v.value if want_value else None
+
+
+def pimd_exchange_forces(h, f_ptr, want_value=True):
+    v = ctypes.c_double()
+    _check(lib().pimd_exchange_forces(h, f_ptr, ctypes.byref(v) if want_value else None), h)
+    return v.value if want_value else None
+
+
+def pimd_interaction_forces(h, f_ptr, want_value=True):
+    v = ctypes.c_double()
+    _check(lib().pimd_interaction_forces(h, f_ptr, ctypes.byref(v) if want_value else None), h)
+    return v.value if want_value else None
+
+
+def pimd_step(h, nsteps):
+    return _check(lib().pimd_step(h, nsteps), h)
+
+
+def pimd_step_eager(h, nsteps):
+    return _check(lib().pimd_step_eager(h, nsteps), h)
+
+
+def pimd_estimators(h):
+    e = Estimates()
+    _check(lib().pimd_estimators(h, ctypes.byref(e)), h)
+    return e.as_dict()
+
+
+def pimd_state_bytes(h):
+    n = ctypes.c_size_t()
+    _check(lib().pimd_state_bytes(h, ctypes.byref(n)), h)
+    return n.value
+
+
+def pimd_get_state(h, host_ptr, nbytes):
+    return _check(lib().pimd_get_state(h, host_ptr, nbytes), h)
+
+
+def pimd_set_state(h, host_ptr, nbytes):
+    return _check(lib().pimd_set_state(h, host_ptr, nbytes), h)
+
+
+def pimd_sync(h):
+    return _check(lib().pimd_sync(h), h)
+
+
+def pimd_last_error(h):
+    return (lib().pimd_last_error(h) or b"").decode()
+
+
+def pimd_global_error():
+    return (lib().pimd_global_error() or b"").decode()
+
+
+def pimd_destroy(h):
+    lib().pimd_destroy(h)
+
+
+def pimd_vb_create(N, P, d, beta, xi):
+    h = _vp()
+    _check(lib().pimd_vb_create(N, P, d, beta, xi, ctypes.byref(h)))
+    return h
+
+
+def pimd_vb_workspace_bytes(h):
+    n = ctypes.c_size_t()
+    _check(lib().pimd_vb_workspace_bytes(h, ctypes.byref(n)))
+    return n.value
+
+
+def pimd_vb_forward(h, r1, rP, ld, work, work_bytes, V_out, stream):
+    return _check(lib().pimd_vb_forward(h, r1, rP, ld, work, work_bytes, V_out, stream))
+
+
+def pimd_vb_backward(h, r1, rP, ld, work, work_bytes, gV, g_r1, g_rP, stream):
+    return _check(lib().pimd_vb_backward(h, r1, rP, ld, work, work_bytes, gV, g_r1, g_rP, stream))
+
+
+def pimd_vb_destroy(h):
+    lib().pimd_vb_destroy(h)
+
+
+# ---- convenience: torch-owned buffers ---------------------------------------
+
+class System:
+    """One PIMD system whose device buffers are torch tensors.
+
+    ``r`` and ``p`` are given particle-major, shape (N, P, d) (host numpy or
+    torch); the device copies live in slice-major (P, d, n_pad) float64
+    tensors.  All arithmetic happens in the C ABI's kernels.
+    """
+
+    def __init__(self, N, P, d, beta, omega=1.0, g=0.0, s=0.5, xi=1.0, r=None, p=None, device="cuda",
+                 stream=None, **cfg_kw):
+        import torch
+
+        self.torch = torch
+        self.N, self.P, self.d = N, P, d
+        self.beta = beta
+        self.h = pimd_create(N, P, d, beta, omega, g, s, xi)
+        cfg = pimd_default_config()
+        for k, v in cfg_kw.items():
+            setattr(cfg, k, v)
+        pimd_configure(self.h, cfg)
+        self.cfg = cfg
+        self.n_pad = (N + 31) // 32 * 32
+        dev = torch.device(device)
+        f64 = torch.float64
+        self.r = torch.zeros((P, d, self.n_pad), dtype=f64, device=dev)
+        self.p = torch.zeros_like(self.r)
+        self.f = torch.zeros_like(self.r)
+        M = cfg.nhc_len
+        self.eta = torch.zeros((M, P, d, self.n_pad), dtype=f64, device=dev)
+        self.peta = torch.zeros_like(self.eta)
+        nbytes = pimd_workspace_bytes(self.h, self.n_pad)
+        self.work = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+        base = self.work.data_ptr()
+        self.work_ptr = (base + 255) // 256 * 256
+        self.work_bytes = nbytes
+        if r is not None:
+            self.r[:, :, :N] = torch.as_tensor(r, dtype=f64).permute(1, 2, 0).to(dev)
+        if p is not None:
+            self.p[:, :, :N] = torch.as_tensor(p, dtype=f64).permute(1, 2, 0).to(dev)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        self.bufs = Buffers(self.r.data_ptr(), self.p.data_ptr(), self.f.data_ptr(), self.eta.data_ptr(),
+                            self.peta.data_ptr(), self.work_ptr, nbytes, self.n_pad)
+        pimd_bind(self.h, self.bufs, self.stream.cuda_stream)
+
+    # particle-major views (host numpy)
+    def positions(self):
+        return self.r[:, :, :self.N].permute(2, 0, 1).cpu().numpy()
+
+    def momenta(self):
+        return self.p[:, :, :self.N].permute(2, 0, 1).cpu().numpy()
+
+    def forces_array(self):
+        return self.f[:, :, :self.N].permute(2, 0, 1).cpu().numpy()
+
+    def forces(self):
+        return pimd_forces(self.h)
+
+    def exchange_forces(self):
+        out = self.torch.zeros_like(self.r)
+        V = pimd_exchange_forces(self.h, out.data_ptr())
+        return out[:, :, :self.N].permute(2, 0, 1).cpu().numpy(), V
+
+    def interaction_forces(self):
+        out = self.torch.zeros_like(self.r)
+        U = pimd_interaction_forces(self.h, out.data_ptr())
+        return out[:, :, :self.N].permute(2, 0, 1).cpu().numpy(), U
+
+    def step(self, n=1, graph=True):
+        (pimd_step if graph else pimd_step_eager)(self.h, n)
+
+    def estimators(self):
+        return pimd_estimators(self.h)
+
+    def get_state(self):
+        n = pimd_state_bytes(self.h)
+        buf = (ctypes.c_char * n)()
+        pimd_get_state(self.h, ctypes.addressof(buf), n)
+        return bytes(buf)
+
+    def set_state(self, blob):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        pimd_set_state(self.h, ctypes.addressof(buf), len(blob))
+
+    def sync(self):
+        pimd_sync(self.h)
+
+    def close(self):
+        if self.h:
+            pimd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

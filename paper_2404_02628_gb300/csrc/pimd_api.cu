@@ -1,0 +1,720 @@
+// C ABI of the PIMD hot path (include/pimd.h): argument checks, workspace
+// layout, kernel sequencing and the captured per-step CUDA graph.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+
+#include "../../include/pimd.h"
+#include "pimd_exchange.cuh"
+#include "pimd_md.cuh"
+
+namespace {
+
+thread_local std::string g_global_error;
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+    size_t total = 0;
+    size_t add(size_t bytes)
+    {
+        size_t off = total;
+        total = align256(total + bytes);
+        return off;
+    }
+};
+
+// Offsets of every workspace region.
+struct ExchLayout {
+    size_t Km, Ke, rho_m, rho_e, y_m, y_e, c_m, c_e, z_m, z_e, part_m, part_e, band_m, band_e, flags, err, lsum;
+};
+
+void exch_layout(Layout& L, ExchLayout& o, int N, int S, int store)
+{
+    const int nb = (N + 31) / 32, nbp = nb * 32;
+    const long long ntiles = store ? (long long)nb * (nb + 1) / 2 : (long long)(2 * nb - 1);
+    o.Km = L.add((size_t)ntiles * 1024 * sizeof(double));
+    o.Ke = L.add((size_t)ntiles * 1024 * sizeof(int));
+    o.rho_m = L.add(nbp * sizeof(double));
+    o.rho_e = L.add(nbp * sizeof(int));
+    o.y_m = L.add((nbp + 1) * sizeof(double));
+    o.y_e = L.add((nbp + 1) * sizeof(int));
+    o.c_m = L.add((nbp + 1) * sizeof(double));
+    o.c_e = L.add((nbp + 1) * sizeof(int));
+    o.z_m = L.add(nbp * sizeof(double));
+    o.z_e = L.add(nbp * sizeof(int));
+    o.part_m = L.add((size_t)2 * nb * S * 32 * 4 * sizeof(double));
+    o.part_e = L.add((size_t)2 * nb * S * 32 * sizeof(int));
+    o.band_m = L.add((size_t)2 * nb * 2 * 32 * 4 * sizeof(double));
+    o.band_e = L.add((size_t)2 * nb * 2 * 32 * sizeof(int));
+    o.flags = L.add((size_t)(2 * nb + 2 * nb * S) * sizeof(int));
+    o.err = L.add(4 * sizeof(int));
+    o.lsum = L.add((size_t)exch_prep_blocks(N) * 2 * sizeof(double));
+}
+
+ExchView exch_view(char* base, const ExchLayout& o, int N, int P, int d, double beta, double xi, int S, int store,
+                   const double* a, const double* b, int lda, int ldb, int spin_limit, int n_help)
+{
+    ExchView v;
+    memset(&v, 0, sizeof(v));
+    v.N = N;
+    v.nb = (N + 31) / 32;
+    v.d = d;
+    v.S = S;
+    v.store = store;
+    v.xi_zero = (xi == 0.0);
+    v.kappa = P / (2.0 * beta);
+    v.ks = P / (beta * beta);
+    v.beta = beta;
+    v.log_xi = (xi > 0.0) ? log(xi) : 0.0;
+    v.a = a;
+    v.b = b;
+    v.lda = lda;
+    v.ldb = ldb;
+    v.Km = (double*)(base + o.Km);
+    v.Ke = (int*)(base + o.Ke);
+    v.rho_m = (double*)(base + o.rho_m);
+    v.rho_e = (int*)(base + o.rho_e);
+    v.y_m = (double*)(base + o.y_m);
+    v.y_e = (int*)(base + o.y_e);
+    v.c_m = (double*)(base + o.c_m);
+    v.c_e = (int*)(base + o.c_e);
+    v.z_m = (double*)(base + o.z_m);
+    v.z_e = (int*)(base + o.z_e);
+    v.part_m = (double*)(base + o.part_m);
+    v.part_e = (int*)(base + o.part_e);
+    v.band_m = (double*)(base + o.band_m);
+    v.band_e = (int*)(base + o.band_e);
+    v.flags = (int*)(base + o.flags);
+    v.err = (int*)(base + o.err);
+    v.lsum = (double*)(base + o.lsum);
+    v.spin_limit = spin_limit > 0 ? spin_limit : (1 << 24);
+    if (n_help < 2) n_help = 2;
+    v.n_help_f = n_help / 2;
+    v.n_help_b = n_help - v.n_help_f;
+    return v;
+}
+
+int device_sms()
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    return sms;
+}
+
+int default_helpers(const pimd_config& cfg)
+{
+    if (cfg.helper_ctas > 0) return cfg.helper_ctas;
+    int sms = device_sms();
+    return sms > 4 ? sms - 2 : 2;
+}
+
+constexpr int EX_STREAMS = 4;
+
+}  // namespace
+
+struct pimd_ctx {
+    int N, P, d;
+    double beta, omega, g, s, xi, A;
+    pimd_config cfg;
+    std::string err;
+    // bound state
+    bool bound = false;
+    pimd_buffers buf;
+    cudaStream_t st = nullptr;
+    cudaStream_t cap = nullptr;  // private stream used only to capture the step graph
+    cudaGraphExec_t graph = nullptr;
+    bool graph_failed = false;
+    long long steps = 0;
+    Layout L;
+    ExchLayout ex;
+    size_t off_spr, off_pair, off_fin, off_md, off_sc, off_flag;
+    int n_help;
+    ExchView xv;
+    BeadView bv;
+    ForceParams fp;
+    MDParams mp;
+};
+
+struct pimd_vb {
+    int N, P, d;
+    double beta, xi;
+    int n_help;
+    Layout L;
+    ExchLayout ex;
+    size_t off_fin;
+};
+
+static pimd_status fail(pimd_t c, pimd_status s, const std::string& m)
+{
+    if (c) c->err = m;
+    else g_global_error = m;
+    return s;
+}
+
+static pimd_status cuda_fail(pimd_t c, cudaError_t e, const char* where)
+{
+    return fail(c, PIMD_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+extern "C" void pimd_default_config(pimd_config* cfg)
+{
+    if (!cfg) return;
+    memset(cfg, 0, sizeof(*cfg));
+    cfg->dt = 0.01;
+    cfg->nhc_len = 4;
+    cfg->nhc_Q = 0.0;
+    cfg->mass = 1.0;
+    cfg->precision = PIMD_PREC_FP64;
+    cfg->amp_convention = PIMD_AMP_PAPER;
+    cfg->table_mode = PIMD_TABLE_STORE;
+    cfg->thermostat = 1;
+    cfg->helper_ctas = 0;
+    cfg->spin_limit = 0;
+}
+
+extern "C" pimd_status pimd_create(int N, int P, int d, double beta, double omega, double g, double s, double xi,
+                                   pimd_t* out)
+{
+    if (!out) return fail(nullptr, PIMD_EINVAL, "pimd_create: out is NULL");
+    *out = nullptr;
+    if (N < 1 || N > (1 << 22)) return fail(nullptr, PIMD_EINVAL, "pimd_create: N must be in [1, 4194304]");
+    if (P < 2 || P > 65535) return fail(nullptr, PIMD_EINVAL, "pimd_create: P must be in [2, 65535]");
+    if (d < 1 || d > 3) return fail(nullptr, PIMD_EINVAL, "pimd_create: d must be 1, 2 or 3");
+    if (!(beta > 0.0) || !isfinite(beta)) return fail(nullptr, PIMD_EINVAL, "pimd_create: beta must be > 0");
+    if (!(omega >= 0.0) || !isfinite(omega)) return fail(nullptr, PIMD_EINVAL, "pimd_create: omega must be >= 0");
+    if (!isfinite(g)) return fail(nullptr, PIMD_EINVAL, "pimd_create: g must be finite");
+    if (!(s > 0.0) || !isfinite(s)) return fail(nullptr, PIMD_EINVAL, "pimd_create: s must be > 0");
+    if (!(xi >= 0.0 && xi <= 1.0)) return fail(nullptr, PIMD_EINVAL, "pimd_create: xi must be in [0, 1]");
+    pimd_ctx* c = new pimd_ctx();
+    c->N = N;
+    c->P = P;
+    c->d = d;
+    c->beta = beta;
+    c->omega = omega;
+    c->g = g;
+    c->s = s;
+    c->xi = xi;
+    pimd_default_config(&c->cfg);
+    c->A = g / (M_PI * s * s);
+    *out = c;
+    return PIMD_OK;
+}
+
+extern "C" pimd_status pimd_configure(pimd_t c, const pimd_config* cfg)
+{
+    if (!c || !cfg) return fail(c, PIMD_EINVAL, "pimd_configure: NULL argument");
+    if (c->bound) return fail(c, PIMD_ESTATE, "pimd_configure: context already bound");
+    if (!(cfg->dt > 0.0) || !isfinite(cfg->dt)) return fail(c, PIMD_EINVAL, "pimd_configure: dt must be > 0");
+    if (cfg->nhc_len < 1 || cfg->nhc_len > 8) return fail(c, PIMD_EINVAL, "pimd_configure: nhc_len must be in [1, 8]");
+    if (!(cfg->mass > 0.0)) return fail(c, PIMD_EINVAL, "pimd_configure: mass must be > 0");
+    if (cfg->precision != PIMD_PREC_FP64 && cfg->precision != PIMD_PREC_MIXED)
+        return fail(c, PIMD_EINVAL, "pimd_configure: unknown precision");
+    if (cfg->amp_convention != PIMD_AMP_PAPER && cfg->amp_convention != PIMD_AMP_RAW)
+        return fail(c, PIMD_EINVAL, "pimd_configure: unknown amp_convention");
+    if (cfg->table_mode != PIMD_TABLE_STORE && cfg->table_mode != PIMD_TABLE_RECOMPUTE)
+        return fail(c, PIMD_EINVAL, "pimd_configure: unknown table_mode");
+    if (cfg->helper_ctas < 0 || cfg->spin_limit < 0) return fail(c, PIMD_EINVAL, "pimd_configure: negative count");
+    c->cfg = *cfg;
+    c->A = (cfg->amp_convention == PIMD_AMP_PAPER) ? c->g / (M_PI * c->s * c->s) : c->g;
+    return PIMD_OK;
+}
+
+static void ctx_layout(pimd_ctx* c)
+{
+    c->L = Layout();
+    exch_layout(c->L, c->ex, c->N, EX_STREAMS, c->cfg.table_mode == PIMD_TABLE_STORE);
+    c->off_spr = c->L.add((size_t)springs_grid_x(c->N) * c->P * sizeof(double));
+    c->off_pair = c->L.add((size_t)pair_grid_x(c->N) * c->P * 2 * sizeof(double));
+    c->off_fin = c->L.add((size_t)exch_finalize_blocks(c->N) * sizeof(double));
+    c->off_md = c->L.add((size_t)md_blocks(c->N, c->P, c->d) * 2 * sizeof(double));
+    c->off_sc = c->L.add(SC_COUNT * sizeof(double));
+    c->off_flag = c->L.add(4 * sizeof(int));
+}
+
+extern "C" pimd_status pimd_workspace_bytes(pimd_t c, int n_pad, size_t* bytes)
+{
+    if (!c || !bytes) return fail(c, PIMD_EINVAL, "pimd_workspace_bytes: NULL argument");
+    if (n_pad < c->N || (n_pad & 31)) return fail(c, PIMD_EINVAL, "pimd_workspace_bytes: n_pad must be >= N and a multiple of 32");
+    ctx_layout(c);
+    *bytes = c->L.total;
+    return PIMD_OK;
+}
+
+static pimd_status enqueue_forces(pimd_ctx* c, cudaStream_t st, double* f, bool exch, bool inter)
+{
+    cudaError_t e;
+    ForceParams fp = c->fp;
+    fp.accumulate = 0;
+    double* work = (double*)c->buf.work;
+    char* base = (char*)c->buf.work;
+    (void)work;
+    if (exch) {
+        e = launch_springs(c->bv, fp, f, (double*)(base + c->off_spr), st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "springs kernel");
+        fp.accumulate = 1;
+    } else {
+        e = launch_zero((double*)(base + c->off_spr), springs_grid_x(c->N) * c->P, st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "zero kernel");
+    }
+    if (inter) {
+        e = launch_pair(c->bv, fp, f, (double*)(base + c->off_pair), st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "pair kernel");
+    } else {
+        e = launch_zero((double*)(base + c->off_pair), (size_t)pair_grid_x(c->N) * c->P * 2, st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "zero kernel");
+    }
+    if (exch) {
+        e = exch_launch_forward(c->xv, st, 1);
+        if (e != cudaSuccess) return cuda_fail(c, e, "exchange recursion");
+        FinalizeOut o;
+        memset(&o, 0, sizeof(o));
+        o.f = f;
+        o.ldf = c->buf.n_pad;
+        o.P = c->P;
+        o.part = (double*)(base + c->off_fin);
+        e = exch_launch_adjoint(c->xv, o, exch_finalize_blocks(c->N), st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "exchange forces");
+    }
+    return PIMD_OK;
+}
+
+static pimd_status enqueue_scalars(pimd_ctx* c, cudaStream_t st)
+{
+    char* base = (char*)c->buf.work;
+    cudaError_t e = launch_md_energy(c->bv, c->mp, (double*)(base + c->off_md), st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "energy kernel");
+    ScalarSources s;
+    memset(&s, 0, sizeof(s));
+    s.springs = (double*)(base + c->off_spr);
+    s.n_springs = springs_grid_x(c->N) * c->P;
+    s.lsum = c->xv.lsum;
+    s.n_lsum = exch_prep_blocks(c->N);
+    s.pair = (double*)(base + c->off_pair);
+    s.n_pair = pair_grid_x(c->N) * c->P;
+    s.fin = (double*)(base + c->off_fin);
+    s.n_fin = exch_finalize_blocks(c->N);
+    s.md = (double*)(base + c->off_md);
+    s.n_md = md_blocks(c->N, c->P, c->d);
+    s.y_m = c->xv.y_m;
+    s.y_e = c->xv.y_e;
+    s.c_m = c->xv.c_m;
+    s.c_e = c->xv.c_e;
+    s.N = c->N;
+    s.xi_zero = c->xv.xi_zero;
+    s.log_xi = c->xv.log_xi;
+    s.out = (double*)(base + c->off_sc);
+    e = launch_scalars(s, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "scalar reduction");
+    return PIMD_OK;
+}
+
+static pimd_status enqueue_step(pimd_ctx* c, cudaStream_t st)
+{
+    cudaError_t e = launch_md_pre(c->bv, c->mp, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "md pre kernel");
+    pimd_status s = enqueue_forces(c, st, c->buf.f, true, true);
+    if (s != PIMD_OK) return s;
+    e = launch_md_post(c->bv, c->mp, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "md post kernel");
+    return PIMD_OK;
+}
+
+static pimd_status check_device_error(pimd_ctx* c)
+{
+    int h[2] = {0, 0};
+    char* base = (char*)c->buf.work;
+    cudaError_t e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
+    e = cudaMemcpy(&h[0], c->xv.err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "error word read");
+    e = cudaMemcpy(&h[1], base + c->off_flag, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "flag read");
+    if (h[0] != 0) {
+        cudaMemsetAsync(c->xv.err, 0, sizeof(int), c->st);
+        cudaStreamSynchronize(c->st);
+        char msg[160];
+        snprintf(msg, sizeof msg, "device wait gave up (code 0x%08x); increase spin_limit or check co-residency", h[0]);
+        return fail(c, PIMD_ETIMEOUT, msg);
+    }
+    return PIMD_OK;
+}
+
+extern "C" pimd_status pimd_bind(pimd_t c, const pimd_buffers* b, void* stream)
+{
+    if (!c || !b) return fail(c, PIMD_EINVAL, "pimd_bind: NULL argument");
+    if (c->bound) return fail(c, PIMD_ESTATE, "pimd_bind: already bound");
+    if (!b->r || !b->p || !b->f || !b->work) return fail(c, PIMD_EINVAL, "pimd_bind: NULL buffer");
+    if (c->cfg.thermostat && (!b->eta || !b->peta)) return fail(c, PIMD_EINVAL, "pimd_bind: thermostat buffers missing");
+    if (b->n_pad < c->N || (b->n_pad & 31)) return fail(c, PIMD_EINVAL, "pimd_bind: n_pad must be >= N and a multiple of 32");
+    if (((uintptr_t)b->work & 255) != 0) return fail(c, PIMD_EINVAL, "pimd_bind: workspace must be 256-byte aligned");
+    ctx_layout(c);
+    if (b->work_bytes < c->L.total) {
+        char msg[160];
+        snprintf(msg, sizeof msg, "pimd_bind: workspace too small (%zu < %zu bytes)", b->work_bytes, c->L.total);
+        return fail(c, PIMD_ENOMEM, msg);
+    }
+    c->buf = *b;
+    c->st = (cudaStream_t)stream;
+    c->n_help = default_helpers(c->cfg);
+    const int np = b->n_pad;
+    c->xv = exch_view((char*)b->work, c->ex, c->N, c->P, c->d, c->beta, c->xi, EX_STREAMS,
+                      c->cfg.table_mode == PIMD_TABLE_STORE, b->r + (size_t)(c->P - 1) * c->d * np, b->r, np, np,
+                      c->cfg.spin_limit, c->n_help);
+    c->bv.N = c->N;
+    c->bv.P = c->P;
+    c->bv.d = c->d;
+    c->bv.ld = np;
+    c->bv.r = b->r;
+    c->bv.p = b->p;
+    c->bv.f = b->f;
+    c->bv.eta = b->eta;
+    c->bv.peta = b->peta;
+    c->bv.M = c->cfg.nhc_len;
+    c->fp.ks = c->P / (c->beta * c->beta);
+    c->fp.omega2 = c->omega * c->omega;
+    c->fp.A = c->A;
+    c->fp.inv_s2 = 1.0 / (c->s * c->s);
+    c->fp.mixed = c->cfg.precision == PIMD_PREC_MIXED;
+    c->fp.accumulate = 0;
+    c->mp.dt = c->cfg.dt;
+    c->mp.mass = c->cfg.mass;
+    c->mp.kT = 1.0 / c->beta;
+    c->mp.Q = c->cfg.nhc_Q > 0.0 ? c->cfg.nhc_Q : c->beta / c->P;
+    c->mp.thermostat = c->cfg.thermostat;
+    cudaError_t e;
+    if (c->cfg.thermostat) {
+        const size_t n = (size_t)c->cfg.nhc_len * c->P * c->d * np;
+        e = cudaMemsetAsync(b->eta, 0, n * sizeof(double), c->st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->peta, 0, n * sizeof(double), c->st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "pimd_bind: thermostat reset");
+    }
+    e = cudaMemsetAsync(c->xv.err, 0, 4 * sizeof(int), c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pimd_bind: error word reset");
+    e = cudaMemsetAsync((char*)b->work + c->off_flag, 0, 4 * sizeof(int), c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pimd_bind: flag reset");
+    c->bound = true;
+    c->steps = 0;
+    pimd_status s = enqueue_forces(c, c->st, b->f, true, true);
+    if (s != PIMD_OK) {
+        c->bound = false;
+        return s;
+    }
+    return PIMD_OK;
+}
+
+extern "C" pimd_status pimd_forces(pimd_t c, double* V_out)
+{
+    if (!c) return fail(c, PIMD_EINVAL, "pimd_forces: NULL handle");
+    if (!c->bound) return fail(c, PIMD_ESTATE, "pimd_forces: not bound");
+    pimd_status s = enqueue_forces(c, c->st, c->buf.f, true, true);
+    if (s != PIMD_OK) return s;
+    if (V_out) {
+        s = enqueue_scalars(c, c->st);
+        if (s != PIMD_OK) return s;
+        s = check_device_error(c);
+        if (s != PIMD_OK) return s;
+        double t[SC_COUNT];
+        cudaError_t e = cudaMemcpy(t, (char*)c->buf.work + c->off_sc, sizeof t, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(c, e, "pimd_forces: scalar read");
+        const double Vxi = t[SC_EINT] + (t[SC_GLINK] - t[SC_LAMBDA]) / c->beta;
+        *V_out = Vxi + t[SC_U] / c->P;
+        if (!isfinite(*V_out)) return fail(c, PIMD_ENONFINITE, "pimd_forces: non-finite potential");
+    }
+    return PIMD_OK;
+}
+
+static pimd_status partial_forces(pimd_t c, double* f_out, double* out, bool exch, const char* name)
+{
+    if (!c || !f_out) return fail(c, PIMD_EINVAL, std::string(name) + ": NULL argument");
+    if (!c->bound) return fail(c, PIMD_ESTATE, std::string(name) + ": not bound");
+    if (!exch) {
+        cudaError_t e = cudaMemsetAsync(f_out, 0, (size_t)c->P * c->d * c->buf.n_pad * sizeof(double), c->st);
+        if (e != cudaSuccess) return cuda_fail(c, e, name);
+    }
+    pimd_status s = enqueue_forces(c, c->st, f_out, exch, !exch);
+    if (s != PIMD_OK) return s;
+    if (out) {
+        s = enqueue_scalars(c, c->st);
+        if (s != PIMD_OK) return s;
+        s = check_device_error(c);
+        if (s != PIMD_OK) return s;
+        double t[SC_COUNT];
+        cudaError_t e = cudaMemcpy(t, (char*)c->buf.work + c->off_sc, sizeof t, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(c, e, name);
+        *out = exch ? t[SC_EINT] + (t[SC_GLINK] - t[SC_LAMBDA]) / c->beta : t[SC_U] / c->P;
+    }
+    return PIMD_OK;
+}
+
+extern "C" pimd_status pimd_exchange_forces(pimd_t c, double* f_out, double* V_out)
+{
+    return partial_forces(c, f_out, V_out, true, "pimd_exchange_forces");
+}
+
+extern "C" pimd_status pimd_interaction_forces(pimd_t c, double* f_out, double* U_out)
+{
+    return partial_forces(c, f_out, U_out, false, "pimd_interaction_forces");
+}
+
+extern "C" pimd_status pimd_step_eager(pimd_t c, int nsteps)
+{
+    if (!c) return fail(c, PIMD_EINVAL, "pimd_step_eager: NULL handle");
+    if (!c->bound) return fail(c, PIMD_ESTATE, "pimd_step_eager: not bound");
+    if (nsteps < 0) return fail(c, PIMD_EINVAL, "pimd_step_eager: nsteps < 0");
+    for (int n = 0; n < nsteps; ++n) {
+        pimd_status s = enqueue_step(c, c->st);
+        if (s != PIMD_OK) return s;
+    }
+    c->steps += nsteps;
+    return PIMD_OK;
+}
+
+static pimd_status build_graph(pimd_ctx* c)
+{
+    cudaError_t e;
+    if (!c->cap) {
+        e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(c, e, "graph stream");
+    }
+    e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(c, e, "begin capture");
+    pimd_status s = enqueue_step(c, c->cap);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(c->cap, &g);
+    if (s != PIMD_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
+    e = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->graph = nullptr;
+        return cuda_fail(c, e, "graph instantiate");
+    }
+    return PIMD_OK;
+}
+
+extern "C" pimd_status pimd_step(pimd_t c, int nsteps)
+{
+    if (!c) return fail(c, PIMD_EINVAL, "pimd_step: NULL handle");
+    if (!c->bound) return fail(c, PIMD_ESTATE, "pimd_step: not bound");
+    if (nsteps < 0) return fail(c, PIMD_EINVAL, "pimd_step: nsteps < 0");
+    if (!c->graph && !c->graph_failed) {
+        if (build_graph(c) != PIMD_OK) {
+            c->graph_failed = true;
+            cudaGetLastError();
+        }
+    }
+    if (!c->graph) return pimd_step_eager(c, nsteps);
+    for (int n = 0; n < nsteps; ++n) {
+        cudaError_t e = cudaGraphLaunch(c->graph, c->st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "graph launch");
+    }
+    c->steps += nsteps;
+    return PIMD_OK;
+}
+
+extern "C" pimd_status pimd_estimators(pimd_t c, pimd_estimates* out)
+{
+    if (!c || !out) return fail(c, PIMD_EINVAL, "pimd_estimators: NULL argument");
+    if (!c->bound) return fail(c, PIMD_ESTATE, "pimd_estimators: not bound");
+    pimd_status s = enqueue_scalars(c, c->st);
+    if (s != PIMD_OK) return s;
+    char* base = (char*)c->buf.work;
+    cudaError_t e = cudaMemsetAsync(base + c->off_flag, 0, sizeof(int), c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pimd_estimators: flag reset");
+    e = launch_nonfinite_scan(c->buf.f, c->N, c->P, c->d, c->buf.n_pad, (int*)(base + c->off_flag), c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pimd_estimators: scan");
+    s = check_device_error(c);
+    if (s != PIMD_OK) return s;
+    double t[SC_COUNT];
+    int flag = 0;
+    e = cudaMemcpy(t, base + c->off_sc, sizeof t, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&flag, base + c->off_flag, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pimd_estimators: read");
+    const double P = c->P, N = c->N, d = c->d, beta = c->beta;
+    out->V_xi = t[SC_EINT] + (t[SC_GLINK] - t[SC_LAMBDA]) / beta;
+    out->V_xi_bwd = t[SC_EINT] + (t[SC_GLINK] - t[SC_LAMBDA_B]) / beta;
+    out->U_over_P = t[SC_U] / P;
+    out->spring = t[SC_EINT] + t[SC_SPRING_X];
+    out->virial = t[SC_VIRIAL];
+    out->kinetic = t[SC_KIN];
+    out->E_prim = 0.5 * P * d * N / beta - out->spring + out->U_over_P;
+    out->E_vir = out->U_over_P + out->virial / (2.0 * P);
+    out->H_conserved = out->kinetic + out->V_xi + out->U_over_P + (c->cfg.thermostat ? t[SC_THERMO] : 0.0);
+    out->step = c->steps;
+    const double* q = &out->E_prim;
+    for (int i = 0; i < 9; ++i)
+        if (!isfinite(q[i])) return fail(c, PIMD_ENONFINITE, "pimd_estimators: non-finite estimate");
+    if (flag) return fail(c, PIMD_ENONFINITE, "pimd_estimators: non-finite force");
+    return PIMD_OK;
+}
+
+extern "C" pimd_status pimd_state_bytes(pimd_t c, size_t* bytes)
+{
+    if (!c || !bytes) return fail(c, PIMD_EINVAL, "pimd_state_bytes: NULL argument");
+    if (!c->bound) return fail(c, PIMD_ESTATE, "pimd_state_bytes: not bound");
+    const size_t n = (size_t)c->P * c->d * c->buf.n_pad;
+    const size_t m = c->cfg.thermostat ? (size_t)c->cfg.nhc_len * n : 0;
+    *bytes = 64 + (2 * n + 2 * m) * sizeof(double);
+    return PIMD_OK;
+}
+
+struct StateHeader {
+    char magic[8];
+    long long N, P, d, n_pad, M, steps, thermostat, pad;
+};
+
+extern "C" pimd_status pimd_get_state(pimd_t c, void* host, size_t bytes)
+{
+    size_t need = 0;
+    pimd_status s = pimd_state_bytes(c, &need);
+    if (s != PIMD_OK) return s;
+    if (!host || bytes < need) return fail(c, PIMD_EINVAL, "pimd_get_state: buffer too small");
+    const size_t n = (size_t)c->P * c->d * c->buf.n_pad;
+    const size_t m = c->cfg.thermostat ? (size_t)c->cfg.nhc_len * n : 0;
+    StateHeader h;
+    memset(&h, 0, sizeof h);
+    memcpy(h.magic, "PIMDST1", 8);
+    h.N = c->N;
+    h.P = c->P;
+    h.d = c->d;
+    h.n_pad = c->buf.n_pad;
+    h.M = c->cfg.nhc_len;
+    h.steps = c->steps;
+    h.thermostat = c->cfg.thermostat;
+    char* out = (char*)host;
+    memcpy(out, &h, sizeof h);
+    double* q = (double*)(out + 64);
+    cudaError_t e = cudaMemcpyAsync(q, c->buf.r, n * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(q + n, c->buf.p, n * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess && m) e = cudaMemcpyAsync(q + 2 * n, c->buf.eta, m * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess && m) e = cudaMemcpyAsync(q + 2 * n + m, c->buf.peta, m * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pimd_get_state");
+    return PIMD_OK;
+}
+
+extern "C" pimd_status pimd_set_state(pimd_t c, const void* host, size_t bytes)
+{
+    size_t need = 0;
+    pimd_status s = pimd_state_bytes(c, &need);
+    if (s != PIMD_OK) return s;
+    if (!host || bytes < need) return fail(c, PIMD_EINVAL, "pimd_set_state: buffer too small");
+    StateHeader h;
+    memcpy(&h, host, sizeof h);
+    if (memcmp(h.magic, "PIMDST1", 8) != 0 || h.N != c->N || h.P != c->P || h.d != c->d || h.n_pad != c->buf.n_pad ||
+        h.M != c->cfg.nhc_len || h.thermostat != c->cfg.thermostat)
+        return fail(c, PIMD_EINVAL, "pimd_set_state: blob does not match this context");
+    const size_t n = (size_t)c->P * c->d * c->buf.n_pad;
+    const size_t m = c->cfg.thermostat ? (size_t)c->cfg.nhc_len * n : 0;
+    const double* q = (const double*)((const char*)host + 64);
+    cudaError_t e = cudaMemcpyAsync(c->buf.r, q, n * sizeof(double), cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->buf.p, q + n, n * sizeof(double), cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess && m) e = cudaMemcpyAsync(c->buf.eta, q + 2 * n, m * sizeof(double), cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess && m) e = cudaMemcpyAsync(c->buf.peta, q + 2 * n + m, m * sizeof(double), cudaMemcpyHostToDevice, c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pimd_set_state");
+    c->steps = h.steps;
+    return enqueue_forces(c, c->st, c->buf.f, true, true);
+}
+
+extern "C" pimd_status pimd_sync(pimd_t c)
+{
+    if (!c) return fail(c, PIMD_EINVAL, "pimd_sync: NULL handle");
+    if (!c->bound) return fail(c, PIMD_ESTATE, "pimd_sync: not bound");
+    return check_device_error(c);
+}
+
+extern "C" const char* pimd_last_error(pimd_t c) { return c ? c->err.c_str() : g_global_error.c_str(); }
+extern "C" const char* pimd_global_error(void) { return g_global_error.c_str(); }
+
+extern "C" void pimd_destroy(pimd_t c)
+{
+    if (!c) return;
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->cap) cudaStreamDestroy(c->cap);
+    delete c;
+}
+
+// ---------------------------------------------------------------------------
+// Exchange potential alone (autograd).
+
+extern "C" pimd_status pimd_vb_create(int N, int P, int d, double beta, double xi, pimd_vb_t* out)
+{
+    if (!out) return fail(nullptr, PIMD_EINVAL, "pimd_vb_create: out is NULL");
+    *out = nullptr;
+    if (N < 1 || N > (1 << 22) || P < 2 || d < 1 || d > 3 || !(beta > 0.0) || !(xi >= 0.0 && xi <= 1.0))
+        return fail(nullptr, PIMD_EINVAL, "pimd_vb_create: bad argument");
+    pimd_vb* h = new pimd_vb();
+    h->N = N;
+    h->P = P;
+    h->d = d;
+    h->beta = beta;
+    h->xi = xi;
+    pimd_config cfg;
+    pimd_default_config(&cfg);
+    h->n_help = default_helpers(cfg);
+    exch_layout(h->L, h->ex, N, EX_STREAMS, 1);
+    h->off_fin = h->L.add((size_t)exch_finalize_blocks(N) * sizeof(double));
+    *out = h;
+    return PIMD_OK;
+}
+
+extern "C" pimd_status pimd_vb_workspace_bytes(pimd_vb_t h, size_t* bytes)
+{
+    if (!h || !bytes) return fail(nullptr, PIMD_EINVAL, "pimd_vb_workspace_bytes: NULL argument");
+    *bytes = h->L.total;
+    return PIMD_OK;
+}
+
+static pimd_status vb_check(pimd_vb_t h, const double* r1, const double* rP, int ld, void* work, size_t bytes, const char* nm)
+{
+    if (!h || !r1 || !rP || !work) return fail(nullptr, PIMD_EINVAL, std::string(nm) + ": NULL argument");
+    if (ld < h->N) return fail(nullptr, PIMD_EINVAL, std::string(nm) + ": ld < N");
+    if (((uintptr_t)work & 255) != 0) return fail(nullptr, PIMD_EINVAL, std::string(nm) + ": workspace not 256-byte aligned");
+    if (bytes < h->L.total) return fail(nullptr, PIMD_ENOMEM, std::string(nm) + ": workspace too small");
+    return PIMD_OK;
+}
+
+extern "C" pimd_status pimd_vb_forward(pimd_vb_t h, const double* r1, const double* rP, int ld, void* work,
+                                       size_t work_bytes, double* V_out, void* stream)
+{
+    pimd_status s = vb_check(h, r1, rP, ld, work, work_bytes, "pimd_vb_forward");
+    if (s != PIMD_OK) return s;
+    if (!V_out) return fail(nullptr, PIMD_EINVAL, "pimd_vb_forward: V_out is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    ExchView v = exch_view((char*)work, h->ex, h->N, h->P, h->d, h->beta, h->xi, EX_STREAMS, 1, rP, r1, ld, ld, 0, h->n_help);
+    cudaError_t e = cudaMemsetAsync(v.err, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = exch_launch_forward(v, st, 1);
+    if (e == cudaSuccess) e = exch_launch_vb_value(v, exch_prep_blocks(h->N), V_out, st);
+    if (e != cudaSuccess) return fail(nullptr, PIMD_ECUDA, std::string("pimd_vb_forward: ") + cudaGetErrorString(e));
+    return PIMD_OK;
+}
+
+extern "C" pimd_status pimd_vb_backward(pimd_vb_t h, const double* r1, const double* rP, int ld, void* work,
+                                        size_t work_bytes, const double* gV, double* g_r1, double* g_rP, void* stream)
+{
+    pimd_status s = vb_check(h, r1, rP, ld, work, work_bytes, "pimd_vb_backward");
+    if (s != PIMD_OK) return s;
+    if (!gV || !g_r1 || !g_rP) return fail(nullptr, PIMD_EINVAL, "pimd_vb_backward: NULL output");
+    cudaStream_t st = (cudaStream_t)stream;
+    ExchView v = exch_view((char*)work, h->ex, h->N, h->P, h->d, h->beta, h->xi, EX_STREAMS, 1, rP, r1, ld, ld, 0, h->n_help);
+    FinalizeOut o;
+    memset(&o, 0, sizeof(o));
+    o.g1 = g_r1;
+    o.gP = g_rP;
+    o.ldg = ld;
+    o.gscale = gV;
+    o.P = h->P;
+    o.part = (double*)((char*)work + h->off_fin);
+    cudaError_t e = exch_launch_adjoint(v, o, exch_finalize_blocks(h->N), st);
+    if (e != cudaSuccess) return fail(nullptr, PIMD_ECUDA, std::string("pimd_vb_backward: ") + cudaGetErrorString(e));
+    return PIMD_OK;
+}
+
+extern "C" void pimd_vb_destroy(pimd_vb_t h) { delete h; }

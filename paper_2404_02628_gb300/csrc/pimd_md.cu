@@ -1,0 +1,375 @@
+// Springs (a1), trap + pairs (a4), NHC velocity Verlet (a5) and scalar
+// reductions for sm_103a.
+#include <math.h>
+
+#include "pimd_md.cuh"
+
+namespace {
+
+constexpr int SPR_T = 128;
+constexpr int PAIR_T = 128;
+constexpr int MD_T = 256;
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// ---------------------------------------------------------------------------
+// (a1) Internal ring-polymer springs (Sec. III interior-bead formula and the
+// within-particle half of the exterior-bead formulas): F_l^j = -k (2 r^j -
+// r^{j+1} - r^{j-1}), with the missing neighbour of beads 1 and P dropped.
+// Also sum_l E_int^(l) (always FP64).
+__global__ void __launch_bounds__(SPR_T) springs_kernel(BeadView b, ForceParams fp, double* f, double* part)
+{
+    __shared__ double red[32];
+    const int l = blockIdx.x * SPR_T + threadIdx.x, j = blockIdx.y;
+    double e = 0.0;
+    if (l < b.N) {
+        for (int c = 0; c < b.d; ++c) {
+            const size_t o = ((size_t)j * b.d + c) * b.ld + l;
+            const double x = b.r[o];
+            const double xm = (j > 0) ? b.r[o - (size_t)b.d * b.ld] : x;
+            const double xp = (j < b.P - 1) ? b.r[o + (size_t)b.d * b.ld] : x;
+            double fo;
+            if (fp.mixed) {
+                const float xf = (float)x;
+                fo = (double)(-(float)fp.ks * ((xf - (float)xm) + (xf - (float)xp)));
+            } else {
+                fo = -fp.ks * ((x - xm) + (x - xp));
+            }
+            f[o] = fp.accumulate ? f[o] + fo : fo;
+            if (j < b.P - 1) e = fma(xp - x, xp - x, e);
+        }
+    }
+    double v[1] = {0.5 * fp.ks * e};
+    block_reduce<1>(v, red);
+    if (threadIdx.x == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = v[0];
+}
+
+// ---------------------------------------------------------------------------
+// (a4) Trap + Gaussian pairs in each bead slice (Sec. II U, Sec. IV B):
+// V_slice = sum_l 1/2 omega^2 r_l^2 + 1/2 sum_{i!=k} A exp(-|r_i - r_k|^2/s^2),
+// F += -grad(V_slice)/P.  One thread per particle, the partner slice staged in
+// shared memory 128 particles at a time.  Writes per-block (energy, virial).
+
+template <int D>
+__global__ void __launch_bounds__(PAIR_T) pair_kernel_f64(BeadView b, ForceParams fp, double* f, double* part)
+{
+    __shared__ double sx[D][PAIR_T];
+    __shared__ double red[64];
+    const int i = blockIdx.x * PAIR_T + threadIdx.x, j = blockIdx.y;
+    const double* rs = b.r + (size_t)j * D * b.ld;
+    double xi[D], g[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        xi[c] = (i < b.N) ? rs[(size_t)c * b.ld + i] : 0.0;
+        g[c] = 0.0;
+    }
+    double esum = 0.0;
+    if (fp.A != 0.0) {
+        for (int k0 = 0; k0 < b.N; k0 += PAIR_T) {
+            const int k = k0 + threadIdx.x;
+#pragma unroll
+            for (int c = 0; c < D; ++c) sx[c][threadIdx.x] = (k < b.N) ? rs[(size_t)c * b.ld + k] : 0.0;
+            __syncthreads();
+            const int kn = min(PAIR_T, b.N - k0);
+            for (int kk = 0; kk < kn; ++kk) {
+                double q2 = 0.0, dx[D];
+#pragma unroll
+                for (int c = 0; c < D; ++c) {
+                    dx[c] = xi[c] - sx[c][kk];
+                    q2 = fma(dx[c], dx[c], q2);
+                }
+                double ee = (k0 + kk == i) ? 0.0 : exp(-q2 * fp.inv_s2);
+                esum += ee;
+#pragma unroll
+                for (int c = 0; c < D; ++c) g[c] = fma(ee, dx[c], g[c]);
+            }
+            __syncthreads();
+        }
+    }
+    double v[2] = {0.0, 0.0};
+    if (i < b.N) {
+        const double cpair = -2.0 * fp.A * fp.inv_s2;  // grad_i of A e^{-q2/s2} = cpair * e * dx
+        double t2 = 0.0, vir = 0.0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            const double grad = fp.omega2 * xi[c] + cpair * g[c];
+            const size_t o = ((size_t)j * D + c) * b.ld + i;
+            const double fo = -grad / b.P;
+            f[o] = fp.accumulate ? f[o] + fo : fo;
+            t2 = fma(xi[c], xi[c], t2);
+            vir = fma(xi[c], grad, vir);
+        }
+        v[0] = 0.5 * fp.omega2 * t2 + 0.5 * fp.A * esum;
+        v[1] = vir;
+    }
+    block_reduce<2>(v, red);
+    if (threadIdx.x == 0) {
+        part[2 * (blockIdx.y * gridDim.x + blockIdx.x) + 0] = v[0];
+        part[2 * (blockIdx.y * gridDim.x + blockIdx.x) + 1] = v[1];
+    }
+}
+
+// FP32 pair arithmetic with exp2 on the MUFU unit; coordinates pre-scaled by
+// sqrt(log2(e))/s so that each pair costs one ex2 and no extra multiply.
+template <int D>
+__global__ void __launch_bounds__(PAIR_T) pair_kernel_f32(BeadView b, ForceParams fp, double* f, double* part)
+{
+    __shared__ float sx[D][PAIR_T];
+    __shared__ double red[64];
+    const int i = blockIdx.x * PAIR_T + threadIdx.x, j = blockIdx.y;
+    const double* rs = b.r + (size_t)j * D * b.ld;
+    const float sc = (float)sqrt(fp.inv_s2 * 1.4426950408889634);
+    double xd[D];
+    float xi[D], g[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        xd[c] = (i < b.N) ? rs[(size_t)c * b.ld + i] : 0.0;
+        xi[c] = (float)xd[c] * sc;
+        g[c] = 0.0f;
+    }
+    float esum = 0.0f;
+    if (fp.A != 0.0) {
+        for (int k0 = 0; k0 < b.N; k0 += PAIR_T) {
+            const int k = k0 + threadIdx.x;
+#pragma unroll
+            for (int c = 0; c < D; ++c) sx[c][threadIdx.x] = (k < b.N) ? (float)rs[(size_t)c * b.ld + k] * sc : 1.0e18f;
+            __syncthreads();
+#pragma unroll 8
+            for (int kk = 0; kk < PAIR_T; ++kk) {
+                float dx[D], nq = 0.0f;
+#pragma unroll
+                for (int c = 0; c < D; ++c) {
+                    dx[c] = xi[c] - sx[c][kk];
+                    nq = fmaf(-dx[c], dx[c], nq);
+                }
+                const float ee = ex2_approx(nq);
+                esum += ee;
+#pragma unroll
+                for (int c = 0; c < D; ++c) g[c] = fmaf(ee, dx[c], g[c]);
+            }
+            __syncthreads();
+        }
+        if (i < b.N) esum -= 1.0f;  // the k == i term contributed exp(0) = 1 and no force
+    }
+    double v[2] = {0.0, 0.0};
+    if (i < b.N) {
+        const double cpair = -2.0 * fp.A * fp.inv_s2 / (double)sc;
+        double t2 = 0.0, vir = 0.0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            const double grad = fp.omega2 * xd[c] + cpair * (double)g[c];
+            const size_t o = ((size_t)j * D + c) * b.ld + i;
+            const double fo = -grad / b.P;
+            f[o] = fp.accumulate ? f[o] + fo : fo;
+            t2 = fma(xd[c], xd[c], t2);
+            vir = fma(xd[c], grad, vir);
+        }
+        v[0] = 0.5 * fp.omega2 * t2 + 0.5 * fp.A * (double)esum;
+        v[1] = vir;
+    }
+    block_reduce<2>(v, red);
+    if (threadIdx.x == 0) {
+        part[2 * (blockIdx.y * gridDim.x + blockIdx.x) + 0] = v[0];
+        part[2 * (blockIdx.y * gridDim.x + blockIdx.x) + 1] = v[1];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// (a5) Massive Nose-Hoover chains (one chain of M thermostats of mass Q per
+// degree of freedom) with the reversible Trotter half step of length tau:
+// last link, links M-1..1 with exp(-tau/4 p_{k+1}/Q) scalings, the particle
+// momentum scaled by exp(-tau p_1/Q), positions eta += tau p_eta/Q, then the
+// links again in the opposite order.
+
+__device__ __forceinline__ void nhc_half_step(double& p, double* eta, double* pe, int M, double m, double Q,
+                                              double kT, double tau)
+{
+    double G = ((M >= 2) ? pe[M - 2] * pe[M - 2] / Q : p * p / m) - kT;
+    pe[M - 1] += 0.5 * tau * G;
+    for (int k = M - 2; k >= 0; --k) {
+        const double a = exp(-0.25 * tau * pe[k + 1] / Q);
+        G = ((k == 0) ? p * p / m : pe[k - 1] * pe[k - 1] / Q) - kT;
+        pe[k] = pe[k] * a * a + 0.5 * tau * G * a;
+    }
+    p *= exp(-tau * pe[0] / Q);
+    for (int k = 0; k < M; ++k) eta[k] += tau * pe[k] / Q;
+    for (int k = 0; k <= M - 2; ++k) {
+        const double a = exp(-0.25 * tau * pe[k + 1] / Q);
+        G = ((k == 0) ? p * p / m : pe[k - 1] * pe[k - 1] / Q) - kT;
+        pe[k] = pe[k] * a * a + 0.5 * tau * G * a;
+    }
+    G = ((M >= 2) ? pe[M - 2] * pe[M - 2] / Q : p * p / m) - kT;
+    pe[M - 1] += 0.5 * tau * G;
+}
+
+constexpr int MAX_M = 8;
+
+template <bool PRE>
+__global__ void __launch_bounds__(MD_T) md_kernel(BeadView b, MDParams mp)
+{
+    const size_t stride = (size_t)b.P * b.d * b.ld;
+    for (size_t o = (size_t)blockIdx.x * MD_T + threadIdx.x; o < stride; o += (size_t)gridDim.x * MD_T) {
+        const int l = (int)(o % b.ld);
+        if (l >= b.N) continue;
+        double p = b.p[o];
+        double eta[MAX_M], pe[MAX_M];
+        if (mp.thermostat) {
+            for (int k = 0; k < b.M; ++k) {
+                eta[k] = b.eta[k * stride + o];
+                pe[k] = b.peta[k * stride + o];
+            }
+        }
+        if (PRE) {
+            if (mp.thermostat) nhc_half_step(p, eta, pe, b.M, mp.mass, mp.Q, mp.kT, 0.5 * mp.dt);
+            p += 0.5 * mp.dt * b.f[o];
+            b.r[o] += mp.dt * p / mp.mass;
+        } else {
+            p += 0.5 * mp.dt * b.f[o];
+            if (mp.thermostat) nhc_half_step(p, eta, pe, b.M, mp.mass, mp.Q, mp.kT, 0.5 * mp.dt);
+        }
+        b.p[o] = p;
+        if (mp.thermostat) {
+            for (int k = 0; k < b.M; ++k) {
+                b.eta[k * stride + o] = eta[k];
+                b.peta[k * stride + o] = pe[k];
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(MD_T) md_energy_kernel(BeadView b, MDParams mp, double* part)
+{
+    __shared__ double red[64];
+    const size_t stride = (size_t)b.P * b.d * b.ld;
+    double v[2] = {0.0, 0.0};
+    for (size_t o = (size_t)blockIdx.x * MD_T + threadIdx.x; o < stride; o += (size_t)gridDim.x * MD_T) {
+        const int l = (int)(o % b.ld);
+        if (l >= b.N) continue;
+        v[0] += 0.5 * b.p[o] * b.p[o] / mp.mass;
+        if (mp.thermostat)
+            for (int k = 0; k < b.M; ++k) {
+                const double pe = b.peta[k * stride + o];
+                v[1] += 0.5 * pe * pe / mp.Q + b.eta[k * stride + o] * mp.kT;
+            }
+    }
+    block_reduce<2>(v, red);
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = v[0];
+        part[2 * blockIdx.x + 1] = v[1];
+    }
+}
+
+// Fixed-order reduction of every per-block partial into the scalar slots.
+__global__ void scalars_kernel(ScalarSources s)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double t[SC_COUNT];
+    for (int q = 0; q < SC_COUNT; ++q) t[q] = 0.0;
+    for (int i = 0; i < s.n_springs; ++i) t[SC_EINT] += s.springs[i];
+    for (int i = 0; i < s.n_lsum; ++i) {
+        t[SC_GLINK] += s.lsum[2 * i];
+        t[SC_L0] += s.lsum[2 * i + 1];
+    }
+    for (int i = 0; i < s.n_pair; ++i) {
+        t[SC_U] += s.pair[2 * i];
+        t[SC_VIRIAL] += s.pair[2 * i + 1];
+    }
+    for (int i = 0; i < s.n_fin; ++i) t[SC_SPRING_X] += s.fin[i];
+    for (int i = 0; i < s.n_md; ++i) {
+        t[SC_KIN] += s.md[2 * i];
+        t[SC_THERMO] += s.md[2 * i + 1];
+    }
+    if (s.xi_zero) {
+        t[SC_LAMBDA] = t[SC_L0];
+        t[SC_LAMBDA_B] = t[SC_L0];
+    } else {
+        t[SC_LAMBDA] = s.N * s.log_xi + wef_log(Wef{s.y_m[s.N], s.y_e[s.N]});
+        t[SC_LAMBDA_B] = s.N * s.log_xi + wef_log(Wef{s.c_m[0], s.c_e[0]});
+    }
+    for (int q = 0; q < SC_COUNT; ++q) s.out[q] = t[q];
+}
+
+__global__ void zero_kernel(double* x, size_t n)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) x[i] = 0.0;
+}
+
+__global__ void nonfinite_kernel(const double* x, int N, int P, int d, int ld, int* flag)
+{
+    const size_t n = (size_t)P * d * ld;
+    for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x)
+        if ((int)(o % ld) < N && !isfinite(x[o])) atomicOr(flag, 1);
+}
+
+}  // namespace
+
+int springs_grid_x(int N) { return (N + SPR_T - 1) / SPR_T; }
+int pair_grid_x(int N) { return (N + PAIR_T - 1) / PAIR_T; }
+int md_blocks(int N, int P, int d)
+{
+    long long n = (long long)N * P * d;
+    long long b = (n + MD_T - 1) / MD_T;
+    return (int)(b < 152 * 8 ? b : 152 * 8);
+}
+
+cudaError_t launch_springs(const BeadView& b, const ForceParams& fp, double* f_out, double* part, cudaStream_t st)
+{
+    springs_kernel<<<dim3(springs_grid_x(b.N), b.P), SPR_T, 0, st>>>(b, fp, f_out, part);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pair(const BeadView& b, const ForceParams& fp, double* f_out, double* part, cudaStream_t st)
+{
+    dim3 grid(pair_grid_x(b.N), b.P);
+    if (fp.mixed) {
+        if (b.d == 1) pair_kernel_f32<1><<<grid, PAIR_T, 0, st>>>(b, fp, f_out, part);
+        else if (b.d == 2) pair_kernel_f32<2><<<grid, PAIR_T, 0, st>>>(b, fp, f_out, part);
+        else pair_kernel_f32<3><<<grid, PAIR_T, 0, st>>>(b, fp, f_out, part);
+    } else {
+        if (b.d == 1) pair_kernel_f64<1><<<grid, PAIR_T, 0, st>>>(b, fp, f_out, part);
+        else if (b.d == 2) pair_kernel_f64<2><<<grid, PAIR_T, 0, st>>>(b, fp, f_out, part);
+        else pair_kernel_f64<3><<<grid, PAIR_T, 0, st>>>(b, fp, f_out, part);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_md_pre(const BeadView& b, const MDParams& mp, cudaStream_t st)
+{
+    md_kernel<true><<<md_blocks(b.N, b.P, b.d), MD_T, 0, st>>>(b, mp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_md_post(const BeadView& b, const MDParams& mp, cudaStream_t st)
+{
+    md_kernel<false><<<md_blocks(b.N, b.P, b.d), MD_T, 0, st>>>(b, mp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_md_energy(const BeadView& b, const MDParams& mp, double* part, cudaStream_t st)
+{
+    md_energy_kernel<<<md_blocks(b.N, b.P, b.d), MD_T, 0, st>>>(b, mp, part);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scalars(const ScalarSources& s, cudaStream_t st)
+{
+    scalars_kernel<<<1, 32, 0, st>>>(s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero(double* x, size_t n, cudaStream_t st)
+{
+    zero_kernel<<<152, 256, 0, st>>>(x, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nonfinite_scan(const double* x, int N, int P, int d, int ld, int* flag, cudaStream_t st)
+{
+    nonfinite_kernel<<<152, 256, 0, st>>>(x, N, P, d, ld, flag);
+    return cudaGetLastError();
+}

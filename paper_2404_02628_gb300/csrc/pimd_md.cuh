@@ -1,0 +1,69 @@
+// Ring-polymer springs (a1), trap + Gaussian pair forces (a4), the massive
+// Nose-Hoover-chain velocity-Verlet update (a5) and the per-step scalar
+// reductions.  Bead arrays are slice-major FP64: x[(j*d + c)*ld + l].
+#pragma once
+#include "pimd_device.cuh"
+
+struct BeadView {
+    int N, P, d, ld;
+    double* r;
+    double* p;
+    double* f;
+    double* eta;   // [M][P][d][ld]
+    double* peta;
+    int M;
+};
+
+struct ForceParams {
+    double ks;      // spring constant m omega_P^2 = P/beta^2
+    double omega2;  // trap omega^2
+    double A, inv_s2;
+    int mixed;      // FP32 springs and pairs
+    int accumulate; // 0: overwrite f, 1: add into f
+};
+
+struct MDParams {
+    double dt, mass, Q, kT;
+    int thermostat;
+};
+
+// Scalar slots of the per-step reduction (device array of doubles).
+enum {
+    SC_EINT = 0,   // sum of internal spring energies sum_l E_int^(l)
+    SC_GLINK,      // sum_{i<N-1} g(i,i+1) = beta * sum of link spring energies
+    SC_L0,         // xi = 0: ln of the diagonal chain product
+    SC_LAMBDA,     // ln W_N (forward)
+    SC_LAMBDA_B,   // ln W_N (backward)
+    SC_U,          // U = sum over slices of (trap + pair) energy
+    SC_VIRIAL,     // sum r . grad U
+    SC_SPRING_X,   // exchange part of the expected spring energy
+    SC_KIN,        // sum p^2/(2m')
+    SC_THERMO,     // sum p_eta^2/(2Q) + eta kT
+    SC_COUNT
+};
+
+struct ScalarSources {
+    const double* springs; int n_springs;   // [n] E_int partials
+    const double* lsum; int n_lsum;         // [n][2]
+    const double* pair; int n_pair;         // [n][2]: energy, virial
+    const double* fin; int n_fin;           // [n]
+    const double* md; int n_md;             // [n][2]: kinetic, thermostat
+    const double* y_m; const int* y_e;      // forward Z at index N
+    const double* c_m; const int* c_e;      // backward Z at index 0
+    int N, xi_zero;
+    double log_xi;
+    double* out;                            // [SC_COUNT]
+};
+
+int springs_grid_x(int N);
+int pair_grid_x(int N);
+int md_blocks(int N, int P, int d);
+
+cudaError_t launch_springs(const BeadView& b, const ForceParams& fp, double* f_out, double* part, cudaStream_t st);
+cudaError_t launch_pair(const BeadView& b, const ForceParams& fp, double* f_out, double* part, cudaStream_t st);
+cudaError_t launch_md_pre(const BeadView& b, const MDParams& mp, cudaStream_t st);
+cudaError_t launch_md_post(const BeadView& b, const MDParams& mp, cudaStream_t st);
+cudaError_t launch_md_energy(const BeadView& b, const MDParams& mp, double* part, cudaStream_t st);
+cudaError_t launch_scalars(const ScalarSources& s, cudaStream_t st);
+cudaError_t launch_zero(double* x, size_t n, cudaStream_t st);
+cudaError_t launch_nonfinite_scan(const double* x, int N, int P, int d, int ld, int* flag, cudaStream_t st);

@@ -1,0 +1,96 @@
+"""The C-ABI library loads and exports every entry point include/*.h declares;
+host-side argument checks (no GPU work)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    from paper_2404_02628_gb300 import build
+
+    build.build()
+    import paper_2404_02628_gb300 as p
+
+    p.load()
+    return p
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(pimd_\w+)\s*\(", text):
+            names.add(m.group(1))
+    return names
+
+
+def test_every_declared_symbol_is_exported(pkg):
+    names = declared_functions()
+    assert len(names) >= 20
+    L = pkg.load()
+    for n in sorted(names):
+        assert hasattr(L, n), n
+    assert set(pkg.symbols()) <= names
+
+
+def test_binding_covers_header(pkg):
+    assert declared_functions() <= set(pkg.symbols())
+
+
+def test_create_rejects_bad_arguments(pkg):
+    bad = [(0, 4, 2, 1.0, 1.0, 0.0, 0.5, 1.0), (4, 1, 2, 1.0, 1.0, 0.0, 0.5, 1.0),
+           (4, 4, 4, 1.0, 1.0, 0.0, 0.5, 1.0), (4, 4, 2, 0.0, 1.0, 0.0, 0.5, 1.0),
+           (4, 4, 2, 1.0, 1.0, 0.0, 0.0, 1.0), (4, 4, 2, 1.0, 1.0, 0.0, 0.5, 1.5),
+           (4, 4, 2, 1.0, 1.0, 0.0, 0.5, -0.1), (4, 4, 2, 1.0, -1.0, 0.0, 0.5, 1.0)]
+    for args in bad:
+        with pytest.raises(pkg.PimdError) as ei:
+            pkg.pimd_create(*args)
+        assert ei.value.status == pkg.PIMD_EINVAL
+
+
+def test_config_and_workspace_host_logic(pkg):
+    h = pkg.pimd_create(100, 8, 2, 2.0, 1.0, 3.0, 0.5, 1.0)
+    try:
+        cfg = pkg.pimd_default_config()
+        assert cfg.dt == 0.01 and cfg.nhc_len == 4 and cfg.thermostat == 1
+        cfg.nhc_len = 0
+        with pytest.raises(pkg.PimdError):
+            pkg.pimd_configure(h, cfg)
+        cfg.nhc_len = 4
+        pkg.pimd_configure(h, cfg)
+        with pytest.raises(pkg.PimdError):
+            pkg.pimd_workspace_bytes(h, 100)  # not a multiple of 32
+        n_store = pkg.pimd_workspace_bytes(h, 128)
+        cfg.table_mode = pkg.TABLE_RECOMPUTE
+        pkg.pimd_configure(h, cfg)
+        n_rec = pkg.pimd_workspace_bytes(h, 128)
+        assert n_rec < n_store
+        # state calls before bind are refused
+        with pytest.raises(pkg.PimdError) as ei:
+            pkg.pimd_step(h, 1)
+        assert ei.value.status == pkg.PIMD_ESTATE
+    finally:
+        pkg.pimd_destroy(h)
+
+
+def test_workspace_scales_quadratically_in_store_mode(pkg):
+    def ws(N, mode):
+        h = pkg.pimd_create(N, 32, 2, 3.0, 1.0, 0.0, 0.5, 1.0)
+        cfg = pkg.pimd_default_config()
+        cfg.table_mode = mode
+        pkg.pimd_configure(h, cfg)
+        n = pkg.pimd_workspace_bytes(h, (N + 31) // 32 * 32)
+        pkg.pimd_destroy(h)
+        return n
+
+    a, b = ws(10000, pkg.TABLE_STORE), ws(40000, pkg.TABLE_STORE)
+    assert 14 < b / a < 18
+    c, d = ws(10000, pkg.TABLE_RECOMPUTE), ws(40000, pkg.TABLE_RECOMPUTE)
+    assert d / c < 5 and d < 0.01 * b
