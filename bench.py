@@ -1,0 +1,392 @@
+"""Throughput of the bosonic-PIMD hot path on GB300: MD steps per second.
+
+Workload (default): 1600 weakly interacting trapped bosons, d=2, P=32 beads,
+beta=3, xi=1, Gaussian g=1, s=0.5 (A = g/(pi s^2)), massive Nose-Hoover
+chains M=4, dt=0.01, mixed precision (FP32 springs and pairs, exchange
+recursion/probabilities/estimators at FP64 accuracy).  Seeded synthetic beads
+~N(0,1).  A step = one full pass of the hot path: NHC half step, half kick,
+drift, springs, trap+pairs, exchange recursion and endpoint forces, half kick,
+NHC half step.
+
+One JSON line on stdout (rank 0).  Under torchrun each rank runs its own
+independent replica (the path does not shard), value = replica-steps/s over
+all ranks, timing = max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
+METRIC = "PIMD steps/s at N=1600 & N=10000 (P=32); batched replica-steps/s vs plain FP64"
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 dense FP64 (profiling recipe's nominal table)
+FP32_TFLOPS_DERIVED = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FMA/clk x 2 x 2.07 GHz
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="gauss1600")
+    ap.add_argument("--no-extra", action="store_true", help="skip the N=10000 line item and the CPU baseline")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------
+# multi-rank plumbing (torch.distributed; no data-path collective)
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def init_dist(backend):
+    import torch.distributed as dist
+
+    ws, rank, _ = dist_info()
+    if ws > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend, rank=rank, world_size=ws)
+    return dist
+
+
+def max_over_ranks(x, device=None):
+    """Max of a float over all ranks (identity on one rank)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(device=None):
+    import torch.distributed as dist
+
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        if device is not None and device.type == "cuda":
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# roofline bookkeeping: algorithmic work per launch of each kernel
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def kernel_work(name, w):
+    """(bound, work per launch, unit, peak, peak_source) for a kernel slot.
+
+    Exchange terms T = N(N+1)/2 (all cycle factors exp(-kappa|r^P_l - r^1_u|^2)).
+    """
+    N, P, d = w["N"], w["P"], w["d"]
+    T = N * (N + 1) / 2
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    hbm_src = "of measured" if hbm else "of fallback"
+    hbm = hbm or 6800.0
+    dof = N * P * d
+    if name == "exch_recursion":
+        # forward and backward passes: per term one multiply-add for the
+        # recursion and d for the weighted endpoint sums, FP64-accurate
+        flops = 2 * T * (1 + d) * 2
+        return "alu", flops / 1e12, "TFLOP/s", FP64_NOMINAL_TFLOPS, "FP64 nominal (recipe)"
+    if name == "exch_table":
+        # per term: d differences, d squares, one scale -> 3d+1 flops, plus one exp
+        flops = T * (3 * d + 2)
+        return "alu", flops / 1e12, "TFLOP/s", FP64_NOMINAL_TFLOPS, "FP64 nominal (recipe)"
+    if name == "pair":
+        pairs = P * N * N
+        flops = pairs * (3 * d + 2 * d + 2)
+        return "alu", flops / 1e12, "TFLOP/s", FP32_TFLOPS_DERIVED, "FP32 derived (152 SM x 128 FMA x 2.07 GHz)"
+    if name in ("md_pre", "md_post"):
+        M = w["M"]
+        byts = dof * 8 * (3 + 2 * M) * 2 - dof * 8 * (1 if name == "md_post" else 0)
+        return "hbm", byts / 1e9, "GB/s", hbm, hbm_src
+    if name == "springs":
+        return "hbm", dof * 8 * 2 / 1e9, "GB/s", hbm, hbm_src
+    return "hbm", dof * 8 / 1e9, "GB/s", hbm, hbm_src
+
+
+# --------------------------------------------------------------------------
+# our arm
+
+def make_system(pkg, w, device, seed_offset=0):
+    from workloads import beads, momenta
+
+    r = beads(w["N"], w["P"], w["d"], w["seed"] + seed_offset)
+    p = momenta(w["N"], w["P"], w["d"], w["beta"], w["seed"] + seed_offset)
+    prec = pkg.PREC_MIXED if w["precision"] == "mixed" else pkg.PREC_FP64
+    return pkg.System(w["N"], w["P"], w["d"], w["beta"], w["omega"], w["g"], w["s"], w["xi"], r=r, p=p,
+                      device=device, precision=prec, nhc_len=w["M"], dt=w["dt"])
+
+
+def timed_steps(S, K, flush, stream):
+    """K graph-replayed steps, L2 flushed between steps (outside the events)."""
+    import torch
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for i in range(K):
+        flush.fill_(i & 0xFF)
+        ev[i][0].record(stream)
+        S.step(1)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev)
+
+
+def run_ours(args):
+    import torch
+
+    import paper_2404_02628_gb300 as pkg
+    from workloads import WORKLOADS
+
+    ws, rank, local = dist_info()
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    dist = init_dist("nccl")
+    pkg.load()
+    w = dict(WORKLOADS[args.workload])
+    S = make_system(pkg, w, device, seed_offset=rank)
+    stream = torch.cuda.current_stream(device)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=device)
+    S.step(max(args.warmup, 3))
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    barrier(device)
+    torch.cuda.synchronize()
+    clocks.start()
+    t0 = time.perf_counter()
+    ms = timed_steps(S, args.steps, flush, stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    barrier(device)
+    ms_max = max_over_ranks(ms, device)
+    value = ws * args.steps / (ms_max / 1e3)
+
+    # per-kernel times (eager steps with events between kernels) -> roofline
+    prof = pkg.pimd_step_profiled(S.h, args.steps)
+    per = {}
+    for name, t in prof:
+        per.setdefault(name, [0.0, 0])
+        per[name][0] += t
+        per[name][1] += 1
+    n_kernels = len(prof)
+    dom = max(per, key=lambda k: per[k][0])
+    avg_ms = per[dom][0] / (per[dom][1] * args.steps)
+    bound, work, unit, peak, peak_src = kernel_work(dom, w)
+    achieved = work / (avg_ms / 1e3)
+    kernels = {k: round(v[0] / args.steps * 1e3, 2) for k, v in sorted(per.items(), key=lambda x: -x[1][0])}
+
+    # end to end through the C ABI with host buffers (pinned), each step:
+    # H2D of the full state, one step, D2H of the estimators
+    nb = pkg.pimd_state_bytes(S.h)
+    host = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
+    pkg.pimd_get_state(S.h, host.data_ptr(), nb)
+    est_bytes = 80
+    K2 = min(args.steps, 100)
+    torch.cuda.synchronize()
+    barrier(device)
+    t0 = time.perf_counter()
+    for _ in range(K2):
+        pkg.pimd_set_state(S.h, host.data_ptr(), nb)
+        pkg.pimd_step(S.h, 1)
+        est = pkg.pimd_estimators(S.h)
+    torch.cuda.synchronize()
+    t_e2e = max_over_ranks(time.perf_counter() - t0, device)
+    e2e = {"value": round(ws * K2 / t_e2e, 3), "unit": "steps/s", "h2d_bytes_per_step": nb,
+           "d2h_bytes_per_step": est_bytes, "steps": K2}
+
+    extra = {}
+    if not args.no_extra and rank == 0 and ws == 1:
+        w2 = dict(WORKLOADS["ideal10000"])
+        S2 = make_system(pkg, w2, device)
+        S2.step(3)
+        torch.cuda.synchronize()
+        K3 = max(3, min(args.steps // 10, 20))
+        ms2 = timed_steps(S2, K3, flush, stream)
+        extra["ideal10000"] = {"value": round(K3 / (ms2 / 1e3), 3), "unit": "steps/s", "steps": K3,
+                               "ms_per_step": round(ms2 / K3, 4),
+                               "config": {"N": 10000, "P": 32, "d": 2, "beta": 3.0, "xi": 1.0, "g": 0.0,
+                                          "precision": "fp64 exchange + fp32 springs"}}
+        S2.close()
+
+    cpu = None
+    if not args.no_extra and rank == 0 and ws == 1:
+        cpu = cpu_baseline(w, budget_s=12.0)
+
+    S.close()
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": round(value, 3), "unit": "steps/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 pairs/springs + f64-accurate exchange", "data": "synthetic",
+            "config": {"workload": "gauss1600: N=1600 trapped bosons, d=2, P=32, beta=3, xi=1, "
+                                   "Gaussian g=1 s=0.5, NHC M=4, dt=0.01, mixed precision",
+                       "N": w["N"], "P": w["P"], "d": w["d"], "beta": w["beta"], "xi": w["xi"],
+                       "g": w["g"], "s": w["s"], "amp": "g/(pi s^2)", "parallelism": "replicas x%d" % ws,
+                       "l2": "flushed between timed steps (512 MB write)"},
+            "roofline": {"kernel": dom, "bound": bound, "achieved": round(achieved, 6), "peak": peak,
+                         "unit": unit, "frac": round(achieved / peak, 6), "traffic": None,
+                         "peak_source": peak_src, "avg_launch_ms": round(avg_ms, 5)},
+            "kernels_us_per_step": kernels,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": n_kernels * args.steps,
+            "clocks": clk,
+            "wall_s_timed_region": round(wall, 4),
+        }
+        if extra:
+            out["also"] = extra
+        print(json.dumps(out), flush=True)
+    if dist.is_initialized():
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------------------------------
+# oracle on the host cores
+
+def cpu_baseline(w, budget_s=12.0):
+    import numpy as np
+
+    import oracle
+    from workloads import beads, momenta
+
+    r = beads(w["N"], w["P"], w["d"], w["seed"])
+    p = momenta(w["N"], w["P"], w["d"], w["beta"], w["seed"])
+    A = w["g"] / (np.pi * w["s"] ** 2)
+    st = oracle.MDState(r, p, w["M"])
+    t0 = time.perf_counter()
+    oracle.md_run(st, w["beta"], w["xi"], w["omega"], A, w["s"], w["dt"], w["beta"] / w["P"], 1)
+    first = time.perf_counter() - t0
+    n = max(1, int(budget_s / max(first / 2, 1e-3)))
+    t0 = time.perf_counter()
+    oracle.md_run(st, w["beta"], w["xi"], w["omega"], A, w["s"], w["dt"], w["beta"] / w["P"], n)
+    dt = time.perf_counter() - t0
+    return {"value": round(n / dt, 5), "unit": "steps/s", "cores": 1, "kind": "oracle",
+            "sample": "%d MD steps of the same N=%d workload (after 1 untimed step), single-threaded "
+                      "FP64 C oracle" % (n, w["N"])}
+
+
+def run_reference(args):
+    from workloads import WORKLOADS
+
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return
+    w = dict(WORKLOADS[args.workload])
+    import numpy as np
+
+    import oracle
+    from workloads import beads, momenta
+
+    r = beads(w["N"], w["P"], w["d"], w["seed"])
+    p = momenta(w["N"], w["P"], w["d"], w["beta"], w["seed"])
+    A = w["g"] / (np.pi * w["s"] ** 2)
+    st = oracle.MDState(r, p, w["M"])
+    oracle.md_run(st, w["beta"], w["xi"], w["omega"], A, w["s"], w["dt"], w["beta"] / w["P"], max(1, min(args.warmup, 2)))
+    t0 = time.perf_counter()
+    oracle.md_run(st, w["beta"], w["xi"], w["omega"], A, w["s"], w["dt"], w["beta"] / w["P"], 1)
+    per = time.perf_counter() - t0
+    K = max(1, min(args.steps, int(90.0 / max(per, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.md_run(st, w["beta"], w["xi"], w["omega"], A, w["s"], w["dt"], w["beta"] / w["P"], K)
+    dt = time.perf_counter() - t0
+    v = K / dt
+    sample = ("%d of the %d requested MD steps of the N=%d workload (bounded to ~90 s of CPU), "
+              "single-threaded FP64 C oracle" % (K, args.steps, w["N"]))
+    out = {"impl": "reference", "metric": METRIC, "value": round(v, 5), "unit": "steps/s", "n_gpus": ws,
+           "steps": K, "warmup": args.warmup, "ms_per_step": round(1e3 * dt / K, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "gauss1600: N=1600 trapped bosons, d=2, P=32, beta=3, xi=1, Gaussian g=1 "
+                                  "s=0.5, NHC M=4, dt=0.01", "N": w["N"], "P": w["P"]},
+           "cpu_baseline": {"value": round(v, 5), "unit": "steps/s", "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": round(v, 5), "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

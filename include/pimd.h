@@ -156,10 +156,21 @@ pimd_status pimd_step_eager(pimd_t ctx, int nsteps);
  * check. */
 pimd_status pimd_estimators(pimd_t ctx, pimd_estimates* out);
 
-/* Host blob with r, p, eta, p_eta and the step counter. */
+/* Host blob: a 64-byte header (sizes, step counter) followed by r, p, f,
+ * eta, p_eta in the bead layout.  get synchronises; set copies
+ * asynchronously from the caller's (ideally pinned) buffer, which must stay
+ * valid until the stream reaches the copy.  The forces travel with the state,
+ * so a restored run continues bitwise as if uninterrupted. */
 pimd_status pimd_state_bytes(pimd_t ctx, size_t* bytes);
-pimd_status pimd_get_state(pimd_t ctx, void* host_blob, size_t bytes);   /* synchronises */
-pimd_status pimd_set_state(pimd_t ctx, const void* host_blob, size_t bytes); /* then forces */
+pimd_status pimd_get_state(pimd_t ctx, void* host_blob, size_t bytes);
+pimd_status pimd_set_state(pimd_t ctx, const void* host_blob, size_t bytes);
+
+/* Runs nsteps MD steps without the graph, with CUDA events between kernels
+ * on the bound stream; ms_out[slot] accumulates each kernel's time (slot
+ * names from pimd_profile_slot_name).  *n_slots receives the kernel count of
+ * one step.  Synchronises.  Used by bench.py for the per-kernel roofline. */
+pimd_status pimd_step_profiled(pimd_t ctx, int nsteps, double* ms_out, int max_slots, int* n_slots);
+const char* pimd_profile_slot_name(pimd_t ctx, int slot);
 
 /* Synchronises the bound stream and reports device-side errors. */
 pimd_status pimd_sync(pimd_t ctx);

@@ -19,7 +19,8 @@ __all__ = [
     "pimd_forces", "pimd_exchange_forces", "pimd_interaction_forces", "pimd_step", "pimd_step_eager",
     "pimd_estimators", "pimd_state_bytes", "pimd_get_state", "pimd_set_state", "pimd_sync",
     "pimd_last_error", "pimd_global_error", "pimd_destroy", "pimd_vb_create", "pimd_vb_workspace_bytes",
-    "pimd_vb_forward", "pimd_vb_backward", "pimd_vb_destroy", "System",
+    "pimd_vb_forward", "pimd_vb_backward", "pimd_vb_destroy", "pimd_step_profiled",
+    "pimd_profile_slot_name", "System",
 ]
 
 PIMD_OK, PIMD_EINVAL, PIMD_ENOMEM, PIMD_ECUDA, PIMD_ETIMEOUT, PIMD_ENONFINITE, PIMD_ESTATE = range(7)
@@ -89,6 +90,8 @@ _SIGS = {
     "pimd_vb_forward": ([_vp, _vp, _vp, ctypes.c_int, _vp, ctypes.c_size_t, _vp, _vp], ctypes.c_int),
     "pimd_vb_backward": ([_vp, _vp, _vp, ctypes.c_int, _vp, ctypes.c_size_t, _vp, _vp, _vp, _vp], ctypes.c_int),
     "pimd_vb_destroy": ([_vp], None),
+    "pimd_step_profiled": ([_vp, ctypes.c_int, _dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "pimd_profile_slot_name": ([_vp, ctypes.c_int], ctypes.c_char_p),
 }
 
 
@@ -177,6 +180,18 @@ def pimd_step(h, nsteps):
 
 def pimd_step_eager(h, nsteps):
     return _check(lib().pimd_step_eager(h, nsteps), h)
+
+
+def pimd_step_profiled(h, nsteps, max_slots=64):
+    """Eager steps with per-kernel CUDA-event times; returns [(name, total_ms)]."""
+    ms = (ctypes.c_double * max_slots)()
+    n = ctypes.c_int()
+    _check(lib().pimd_step_profiled(h, nsteps, ms, max_slots, ctypes.byref(n)), h)
+    return [((lib().pimd_profile_slot_name(h, i) or b"").decode(), ms[i]) for i in range(n.value)]
+
+
+def pimd_profile_slot_name(h, slot):
+    return (lib().pimd_profile_slot_name(h, slot) or b"").decode()
 
 
 def pimd_estimators(h):

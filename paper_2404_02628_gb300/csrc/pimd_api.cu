@@ -137,6 +137,7 @@ struct pimd_ctx {
     BeadView bv;
     ForceParams fp;
     MDParams mp;
+    const char* slot_names[64] = {};
 };
 
 struct pimd_vb {
@@ -244,16 +245,16 @@ extern "C" pimd_status pimd_workspace_bytes(pimd_t c, int n_pad, size_t* bytes)
     return PIMD_OK;
 }
 
-static pimd_status enqueue_forces(pimd_ctx* c, cudaStream_t st, double* f, bool exch, bool inter)
+static pimd_status enqueue_forces(pimd_ctx* c, cudaStream_t st, double* f, bool exch, bool inter,
+                                  ProfMarks* pm = nullptr)
 {
     cudaError_t e;
     ForceParams fp = c->fp;
     fp.accumulate = 0;
-    double* work = (double*)c->buf.work;
     char* base = (char*)c->buf.work;
-    (void)work;
     if (exch) {
         e = launch_springs(c->bv, fp, f, (double*)(base + c->off_spr), st);
+        prof_mark(pm, "springs", st);
         if (e != cudaSuccess) return cuda_fail(c, e, "springs kernel");
         fp.accumulate = 1;
     } else {
@@ -262,13 +263,14 @@ static pimd_status enqueue_forces(pimd_ctx* c, cudaStream_t st, double* f, bool 
     }
     if (inter) {
         e = launch_pair(c->bv, fp, f, (double*)(base + c->off_pair), st);
+        prof_mark(pm, "pair", st);
         if (e != cudaSuccess) return cuda_fail(c, e, "pair kernel");
     } else {
         e = launch_zero((double*)(base + c->off_pair), (size_t)pair_grid_x(c->N) * c->P * 2, st);
         if (e != cudaSuccess) return cuda_fail(c, e, "zero kernel");
     }
     if (exch) {
-        e = exch_launch_forward(c->xv, st, 1);
+        e = exch_launch_forward(c->xv, st, 1, pm);
         if (e != cudaSuccess) return cuda_fail(c, e, "exchange recursion");
         FinalizeOut o;
         memset(&o, 0, sizeof(o));
@@ -276,7 +278,7 @@ static pimd_status enqueue_forces(pimd_ctx* c, cudaStream_t st, double* f, bool 
         o.ldf = c->buf.n_pad;
         o.P = c->P;
         o.part = (double*)(base + c->off_fin);
-        e = exch_launch_adjoint(c->xv, o, exch_finalize_blocks(c->N), st);
+        e = exch_launch_adjoint(c->xv, o, exch_finalize_blocks(c->N), st, pm);
         if (e != cudaSuccess) return cuda_fail(c, e, "exchange forces");
     }
     return PIMD_OK;
@@ -312,13 +314,15 @@ static pimd_status enqueue_scalars(pimd_ctx* c, cudaStream_t st)
     return PIMD_OK;
 }
 
-static pimd_status enqueue_step(pimd_ctx* c, cudaStream_t st)
+static pimd_status enqueue_step(pimd_ctx* c, cudaStream_t st, ProfMarks* pm = nullptr)
 {
     cudaError_t e = launch_md_pre(c->bv, c->mp, st);
+    prof_mark(pm, "md_pre", st);
     if (e != cudaSuccess) return cuda_fail(c, e, "md pre kernel");
-    pimd_status s = enqueue_forces(c, st, c->buf.f, true, true);
+    pimd_status s = enqueue_forces(c, st, c->buf.f, true, true, pm);
     if (s != PIMD_OK) return s;
     e = launch_md_post(c->bv, c->mp, st);
+    prof_mark(pm, "md_post", st);
     if (e != cudaSuccess) return cuda_fail(c, e, "md post kernel");
     return PIMD_OK;
 }
@@ -519,6 +523,54 @@ extern "C" pimd_status pimd_step(pimd_t c, int nsteps)
     return PIMD_OK;
 }
 
+extern "C" pimd_status pimd_step_profiled(pimd_t c, int nsteps, double* ms_out, int max_slots, int* n_slots)
+{
+    if (!c || !ms_out || !n_slots || max_slots < 1) return fail(c, PIMD_EINVAL, "pimd_step_profiled: bad argument");
+    if (!c->bound) return fail(c, PIMD_ESTATE, "pimd_step_profiled: not bound");
+    if (nsteps < 1) return fail(c, PIMD_EINVAL, "pimd_step_profiled: nsteps < 1");
+    ProfMarks pm;
+    memset(&pm, 0, sizeof pm);
+    for (int i = 0; i < 64; ++i) {
+        cudaError_t e = cudaEventCreate(&pm.ev[i]);
+        if (e != cudaSuccess) {
+            for (int k = 0; k < i; ++k) cudaEventDestroy(pm.ev[k]);
+            return cuda_fail(c, e, "pimd_step_profiled: event create");
+        }
+    }
+    for (int i = 0; i < max_slots; ++i) ms_out[i] = 0.0;
+    pimd_status s = PIMD_OK;
+    int nk = 0;
+    for (int n = 0; n < nsteps && s == PIMD_OK; ++n) {
+        pm.n = 0;
+        prof_mark(&pm, "start", c->st);
+        s = enqueue_step(c, c->st, &pm);
+        if (s != PIMD_OK) break;
+        cudaError_t e = cudaEventSynchronize(pm.ev[pm.n - 1]);
+        if (e != cudaSuccess) {
+            s = cuda_fail(c, e, "pimd_step_profiled: sync");
+            break;
+        }
+        nk = pm.n - 1;
+        for (int k = 1; k < pm.n && k - 1 < max_slots; ++k) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, pm.ev[k - 1], pm.ev[k]);
+            ms_out[k - 1] += ms;
+            c->slot_names[k - 1] = pm.name[k];
+        }
+    }
+    for (int i = 0; i < 64; ++i) cudaEventDestroy(pm.ev[i]);
+    if (s != PIMD_OK) return s;
+    c->steps += nsteps;
+    *n_slots = nk < max_slots ? nk : max_slots;
+    return check_device_error(c);
+}
+
+extern "C" const char* pimd_profile_slot_name(pimd_t c, int slot)
+{
+    if (!c || slot < 0 || slot >= 64 || !c->slot_names[slot]) return "";
+    return c->slot_names[slot];
+}
+
 extern "C" pimd_status pimd_estimators(pimd_t c, pimd_estimates* out)
 {
     if (!c || !out) return fail(c, PIMD_EINVAL, "pimd_estimators: NULL argument");
@@ -561,7 +613,7 @@ extern "C" pimd_status pimd_state_bytes(pimd_t c, size_t* bytes)
     if (!c->bound) return fail(c, PIMD_ESTATE, "pimd_state_bytes: not bound");
     const size_t n = (size_t)c->P * c->d * c->buf.n_pad;
     const size_t m = c->cfg.thermostat ? (size_t)c->cfg.nhc_len * n : 0;
-    *bytes = 64 + (2 * n + 2 * m) * sizeof(double);
+    *bytes = 64 + (3 * n + 2 * m) * sizeof(double);
     return PIMD_OK;
 }
 
@@ -593,8 +645,9 @@ extern "C" pimd_status pimd_get_state(pimd_t c, void* host, size_t bytes)
     double* q = (double*)(out + 64);
     cudaError_t e = cudaMemcpyAsync(q, c->buf.r, n * sizeof(double), cudaMemcpyDeviceToHost, c->st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(q + n, c->buf.p, n * sizeof(double), cudaMemcpyDeviceToHost, c->st);
-    if (e == cudaSuccess && m) e = cudaMemcpyAsync(q + 2 * n, c->buf.eta, m * sizeof(double), cudaMemcpyDeviceToHost, c->st);
-    if (e == cudaSuccess && m) e = cudaMemcpyAsync(q + 2 * n + m, c->buf.peta, m * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(q + 2 * n, c->buf.f, n * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess && m) e = cudaMemcpyAsync(q + 3 * n, c->buf.eta, m * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess && m) e = cudaMemcpyAsync(q + 3 * n + m, c->buf.peta, m * sizeof(double), cudaMemcpyDeviceToHost, c->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
     if (e != cudaSuccess) return cuda_fail(c, e, "pimd_get_state");
     return PIMD_OK;
@@ -616,11 +669,12 @@ extern "C" pimd_status pimd_set_state(pimd_t c, const void* host, size_t bytes)
     const double* q = (const double*)((const char*)host + 64);
     cudaError_t e = cudaMemcpyAsync(c->buf.r, q, n * sizeof(double), cudaMemcpyHostToDevice, c->st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->buf.p, q + n, n * sizeof(double), cudaMemcpyHostToDevice, c->st);
-    if (e == cudaSuccess && m) e = cudaMemcpyAsync(c->buf.eta, q + 2 * n, m * sizeof(double), cudaMemcpyHostToDevice, c->st);
-    if (e == cudaSuccess && m) e = cudaMemcpyAsync(c->buf.peta, q + 2 * n + m, m * sizeof(double), cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->buf.f, q + 2 * n, n * sizeof(double), cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess && m) e = cudaMemcpyAsync(c->buf.eta, q + 3 * n, m * sizeof(double), cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess && m) e = cudaMemcpyAsync(c->buf.peta, q + 3 * n + m, m * sizeof(double), cudaMemcpyHostToDevice, c->st);
     if (e != cudaSuccess) return cuda_fail(c, e, "pimd_set_state");
     c->steps = h.steps;
-    return enqueue_forces(c, c->st, c->buf.f, true, true);
+    return PIMD_OK;
 }
 
 extern "C" pimd_status pimd_sync(pimd_t c)

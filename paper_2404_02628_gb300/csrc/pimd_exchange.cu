@@ -710,13 +710,23 @@ int exch_finalize_blocks(int N) { return (N + 255) / 256; }
 
 size_t exch_recursion_smem() { return EX_WARPS * sizeof(ExSlot) + sizeof(ChainSmem); }
 
-cudaError_t exch_launch_forward(const ExchView& v, cudaStream_t st, int coop)
+void prof_mark(ProfMarks* pm, const char* name, cudaStream_t st)
+{
+    if (!pm || pm->n >= 64) return;
+    cudaEventRecord(pm->ev[pm->n], st);
+    pm->name[pm->n] = name;
+    pm->n++;
+}
+
+cudaError_t exch_launch_forward(const ExchView& v, cudaStream_t st, int coop, ProfMarks* pm)
 {
     exch_prep_kernel<<<exch_prep_blocks(v.N), 256, 0, st>>>(v);
+    prof_mark(pm, "exch_prep", st);
     if (v.xi_zero) return cudaGetLastError();
     const long long ntiles = v.store ? (long long)v.nb * (v.nb + 1) / 2 : (long long)(2 * v.nb - 1);
     const int tgrid = (int)min(ntiles, (long long)152 * 64);
     exch_table_kernel<<<tgrid, 256, 0, st>>>(v, ntiles);
+    prof_mark(pm, "exch_table", st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t smem = exch_recursion_smem();
@@ -737,13 +747,20 @@ cudaError_t exch_launch_forward(const ExchView& v, cudaStream_t st, int coop)
     attr[0].val.cooperative = coop ? 1 : 0;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, exch_recursion_kernel, v);
+    e = cudaLaunchKernelEx(&cfg, exch_recursion_kernel, v);
+    prof_mark(pm, "exch_recursion", st);
+    return e;
 }
 
-cudaError_t exch_launch_adjoint(const ExchView& v, const FinalizeOut& o, int nblk_fin, cudaStream_t st)
+cudaError_t exch_launch_adjoint(const ExchView& v, const FinalizeOut& o, int nblk_fin, cudaStream_t st,
+                                ProfMarks* pm)
 {
-    if (!v.xi_zero) exch_band_kernel<<<dim3(v.nb, 2), 64, 0, st>>>(v);
+    if (!v.xi_zero) {
+        exch_band_kernel<<<dim3(v.nb, 2), 64, 0, st>>>(v);
+        prof_mark(pm, "exch_band", st);
+    }
     exch_finalize_kernel<<<nblk_fin, 256, 0, st>>>(v, o);
+    prof_mark(pm, "exch_finalize", st);
     return cudaGetLastError();
 }
 

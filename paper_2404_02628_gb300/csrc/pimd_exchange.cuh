@@ -66,8 +66,17 @@ struct FinalizeOut {
     double* part;          // per-block partial sums [grid][1]: exchange spring energy
 };
 
-cudaError_t exch_launch_forward(const ExchView& v, cudaStream_t st, int coop);
-cudaError_t exch_launch_adjoint(const ExchView& v, const FinalizeOut& o, int nblk_fin, cudaStream_t st);
+// Optional per-kernel event marks (bench profiling); null = no marks.
+struct ProfMarks {
+    cudaEvent_t ev[64];
+    const char* name[64];
+    int n;
+};
+void prof_mark(ProfMarks* pm, const char* name, cudaStream_t st);
+
+cudaError_t exch_launch_forward(const ExchView& v, cudaStream_t st, int coop, ProfMarks* pm = nullptr);
+cudaError_t exch_launch_adjoint(const ExchView& v, const FinalizeOut& o, int nblk_fin, cudaStream_t st,
+                                ProfMarks* pm = nullptr);
 cudaError_t exch_launch_vb_value(const ExchView& v, int nprep, double* V_out, cudaStream_t st);
 int exch_prep_blocks(int N);
 int exch_finalize_blocks(int N);

@@ -1,0 +1,60 @@
+"""bench.py's multi-rank logic on CPU: world_size 2 over gloo (no GPU)."""
+import os
+import socket
+
+import pytest
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, ws, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(ws),
+                      LOCAL_RANK=str(rank))
+    import bench
+
+    dist = bench.init_dist("gloo")
+    bench.barrier(None)
+    m = bench.max_over_ranks(1.5 * (rank + 1))
+    info = bench.dist_info()
+    dist.destroy_process_group()
+    q.put((rank, m, info))
+
+
+def test_max_over_ranks_gloo_world2():
+    import torch.multiprocessing as mp
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    out.sort()
+    assert [o[1] for o in out] == [3.0, 3.0]
+    assert out[0][2] == (2, 0, 0) and out[1][2] == (2, 1, 1)
+
+
+def test_single_rank_is_identity():
+    import bench
+
+    assert bench.max_over_ranks(2.5) == 2.5
+
+
+def test_kernel_work_table():
+    import bench
+    from workloads import WORKLOADS
+
+    w = WORKLOADS["gauss1600"]
+    for name in ("exch_recursion", "exch_table", "pair", "md_pre", "md_post", "springs", "other"):
+        bound, work, unit, peak, src = bench.kernel_work(name, w)
+        assert bound in ("alu", "hbm") and work > 0 and peak > 0
