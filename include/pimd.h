@@ -201,6 +201,25 @@ pimd_status pimd_vb_backward(pimd_vb_t h, const double* r1, const double* rP, in
                              double* g_r1, double* g_rP, void* stream);
 void pimd_vb_destroy(pimd_vb_t h);
 
+/* Same value as pimd_vb_forward (V_ends), for callers that cannot allocate
+ * device memory: a host program or plug-in that only receives the input and
+ * output arrays from another code (for instance an MD engine that owns the
+ * device heap, or a caller inside a region where allocation is not allowed)
+ * and so cannot provide the workspace pimd_vb_forward needs.  The paper has
+ * no counterpart; this is a packaging variant of the forward recursion.
+ *
+ * Scratch lives in a fixed 8 MiB array inside the library, which every GPU
+ * that loads the library keeps until the process exits.  N must be at most
+ * 1024, otherwise PIMD_EINVAL with a message; no cudaMalloc/cudaFree or other
+ * allocating routine is called.  r1, rP: device [d][ld]; V_out: device double.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current), so make that first call before any
+ * stream capture.  All calls share the one array and each call overwrites it:
+ * calls whose work overlaps on the GPU (different streams, or different host
+ * threads) race and give wrong results; serialise them on one stream. */
+pimd_status pimd_vb_forward_noalloc(int N, int P, int d, double beta, double xi, const double* r1,
+                                    const double* rP, int ld, double* V_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -20,7 +20,7 @@ __all__ = [
     "pimd_estimators", "pimd_state_bytes", "pimd_get_state", "pimd_set_state", "pimd_sync",
     "pimd_last_error", "pimd_global_error", "pimd_destroy", "pimd_vb_create", "pimd_vb_workspace_bytes",
     "pimd_vb_forward", "pimd_vb_backward", "pimd_vb_destroy", "pimd_step_profiled",
-    "pimd_profile_slot_name", "System",
+    "pimd_profile_slot_name", "pimd_vb_forward_noalloc", "System",
 ]
 
 PIMD_OK, PIMD_EINVAL, PIMD_ENOMEM, PIMD_ECUDA, PIMD_ETIMEOUT, PIMD_ENONFINITE, PIMD_ESTATE = range(7)
@@ -92,6 +92,8 @@ _SIGS = {
     "pimd_vb_destroy": ([_vp], None),
     "pimd_step_profiled": ([_vp, ctypes.c_int, _dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "pimd_profile_slot_name": ([_vp, ctypes.c_int], ctypes.c_char_p),
+    "pimd_vb_forward_noalloc": ([ctypes.c_int] * 3 + [ctypes.c_double] * 2 + [_vp, _vp, ctypes.c_int, _vp, _vp],
+                                ctypes.c_int),
 }
 
 
@@ -252,6 +254,11 @@ def pimd_vb_backward(h, r1, rP, ld, work, work_bytes, gV, g_r1, g_rP, stream):
 
 def pimd_vb_destroy(h):
     lib().pimd_vb_destroy(h)
+
+
+def pimd_vb_forward_noalloc(N, P, d, beta, xi, r1, rP, ld, V_out, stream):
+    """V_ends without a caller workspace (library-owned fixed scratch, N <= 1024)."""
+    return _check(lib().pimd_vb_forward_noalloc(N, P, d, beta, xi, r1, rP, ld, V_out, stream))
 
 
 # ---- convenience: torch-owned buffers ---------------------------------------

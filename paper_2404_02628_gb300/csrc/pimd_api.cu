@@ -772,3 +772,69 @@ extern "C" pimd_status pimd_vb_backward(pimd_vb_t h, const double* r1, const dou
 }
 
 extern "C" void pimd_vb_destroy(pimd_vb_t h) { delete h; }
+
+// ---------------------------------------------------------------------------
+// Exchange potential with library-owned scratch, for callers that cannot
+// allocate device memory (see pimd_vb_forward_noalloc in pimd.h).
+
+#include <mutex>
+
+#define PIMD_NOALLOC_MAX_N 1024
+#define PIMD_NOALLOC_BYTES ((size_t)8 << 20)
+
+// Fixed scratch for the whole recursion state of one call (factor table,
+// chain vectors, flags, partial sums).  Every GPU that loads the library
+// holds these 8 MiB until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[PIMD_NOALLOC_BYTES];
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_ptr[128];
+
+// Device address of the scratch array on the current device.  The array's
+// name in host code is only a host-side stand-in, so the address is looked up
+// once per device (with that device current) and cached.
+static pimd_status noalloc_scratch(void** out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(nullptr, PIMD_ECUDA, std::string("pimd_vb_forward_noalloc: ") + cudaGetErrorString(e));
+    if (dev < 0 || dev >= 128) return fail(nullptr, PIMD_EINVAL, "pimd_vb_forward_noalloc: device index out of range");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(nullptr, PIMD_ECUDA, std::string("pimd_vb_forward_noalloc: scratch address lookup failed: ") +
+                                                 cudaGetErrorString(e));
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return PIMD_OK;
+}
+
+extern "C" pimd_status pimd_vb_forward_noalloc(int N, int P, int d, double beta, double xi, const double* r1,
+                                               const double* rP, int ld, double* V_out, void* stream)
+{
+    if (N < 1 || N > PIMD_NOALLOC_MAX_N)
+        return fail(nullptr, PIMD_EINVAL, "pimd_vb_forward_noalloc: N must be in [1, 1024] (fixed 8 MiB scratch)");
+    if (P < 2 || d < 1 || d > 3 || !(beta > 0.0) || !(xi >= 0.0 && xi <= 1.0))
+        return fail(nullptr, PIMD_EINVAL, "pimd_vb_forward_noalloc: bad argument");
+    if (!r1 || !rP || !V_out || ld < N) return fail(nullptr, PIMD_EINVAL, "pimd_vb_forward_noalloc: NULL pointer or ld < N");
+    Layout L;
+    ExchLayout ex;
+    exch_layout(L, ex, N, EX_STREAMS, 1);
+    if (L.total > PIMD_NOALLOC_BYTES)
+        return fail(nullptr, PIMD_EINVAL, "pimd_vb_forward_noalloc: N too large for the fixed scratch");
+    void* base = nullptr;
+    pimd_status s = noalloc_scratch(&base);
+    if (s != PIMD_OK) return s;
+    pimd_config cfg;
+    pimd_default_config(&cfg);
+    cudaStream_t st = (cudaStream_t)stream;
+    ExchView v = exch_view((char*)base, ex, N, P, d, beta, xi, EX_STREAMS, 1, rP, r1, ld, ld, 0, default_helpers(cfg));
+    cudaError_t e = cudaMemsetAsync(v.err, 0, sizeof(int), st);  // error word must start at zero
+    if (e == cudaSuccess) e = exch_launch_forward(v, st, 1);      // also zeroes the chain flags
+    if (e == cudaSuccess) e = exch_launch_vb_value(v, exch_prep_blocks(N), V_out, st);
+    if (e != cudaSuccess) return fail(nullptr, PIMD_ECUDA, std::string("pimd_vb_forward_noalloc: ") + cudaGetErrorString(e));
+    return PIMD_OK;
+}
