@@ -77,7 +77,15 @@ typedef struct {
     int thermostat;     /* 1 = massive NHC (default), 0 = plain velocity Verlet (NVE)   */
     int helper_ctas;    /* exchange-recursion helper blocks; 0 = one per SM (default)   */
     int spin_limit;     /* polls before a cross-block wait gives up; 0 = default (~1e7) */
+    int exchange_arith; /* PIMD_XARITH_DF (default): exchange recursion, probabilities and
+                           endpoint forces in double-float (FP32 pairs, ~48-bit mantissa, int32
+                           exponent) on the FP32 pipe; PIMD_XARITH_FP64: native FP64 throughout */
+    int exch_band;      /* look-ahead band width W of the double-float recursion, 2..8
+                           (0 = default 4): the chain block adds the W-2 tiles next to the
+                           diagonal itself, helper blocks the rest */
 } pimd_config;
+
+enum { PIMD_XARITH_DF = 0, PIMD_XARITH_FP64 = 1 };
 
 typedef struct {
     double* r;          /* device, [P][d][n_pad] bead positions                          */

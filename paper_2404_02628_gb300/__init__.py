@@ -29,6 +29,7 @@ STATUS_NAMES = {0: "PIMD_OK", 1: "PIMD_EINVAL", 2: "PIMD_ENOMEM", 3: "PIMD_ECUDA
 PREC_FP64, PREC_MIXED = 0, 1
 AMP_PAPER, AMP_RAW = 0, 1
 TABLE_STORE, TABLE_RECOMPUTE = 0, 1
+XARITH_DF, XARITH_FP64 = 0, 1
 
 LIB_PATH = _build.LIB
 
@@ -43,7 +44,7 @@ class Config(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("nhc_len", ctypes.c_int), ("nhc_Q", ctypes.c_double),
                 ("mass", ctypes.c_double), ("precision", ctypes.c_int), ("amp_convention", ctypes.c_int),
                 ("table_mode", ctypes.c_int), ("thermostat", ctypes.c_int), ("helper_ctas", ctypes.c_int),
-                ("spin_limit", ctypes.c_int)]
+                ("spin_limit", ctypes.c_int), ("exchange_arith", ctypes.c_int), ("exch_band", ctypes.c_int)]
 
 
 class Buffers(ctypes.Structure):

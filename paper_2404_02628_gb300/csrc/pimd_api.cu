@@ -9,6 +9,7 @@
 #include "../../include/pimd.h"
 #include "pimd_exchange.cuh"
 #include "pimd_md.cuh"
+#include "pimd_xdf.cuh"
 
 namespace {
 
@@ -114,6 +115,95 @@ int default_helpers(const pimd_config& cfg)
 
 constexpr int EX_STREAMS = 4;
 
+// Workspace regions of the double-float exchange path.
+struct XLayout {
+    size_t ah, al, bh, bl, crh, crl, tab, Mh, Ml, Me, Gh, Gl, Ge, Qh, Ql, Qe, Ph, Pl, Pe, yh, yl, ye, ch, cl, ce,
+        parth, partl, parte, bandh, bandl, bande, flags, err, lsum, lam;
+};
+
+void xdf_layout(Layout& L, XLayout& o, int N, int S, int W, int store)
+{
+    const int nb = (N + 1 + 31) / 32, np = nb * 32;
+    const long long nt = xdf_ntiles(nb, W, store);
+    const size_t f = sizeof(float), i4 = sizeof(int);
+    o.ah = L.add(3 * np * f);
+    o.al = L.add(3 * np * f);
+    o.bh = L.add(3 * np * f);
+    o.bl = L.add(3 * np * f);
+    o.crh = L.add(np * f);
+    o.crl = L.add(np * f);
+    o.tab = L.add(256 * sizeof(float2));
+    o.Mh = L.add((size_t)nt * 1024 * f);
+    o.Ml = L.add((size_t)nt * 1024 * f);
+    o.Me = L.add((size_t)nt * 1024 * i4);
+    o.Gh = L.add((size_t)nb * 1024 * f);
+    o.Gl = L.add((size_t)nb * 1024 * f);
+    o.Ge = L.add((size_t)nb * 1024 * i4);
+    o.Qh = L.add((size_t)nb * 1024 * f);
+    o.Ql = L.add((size_t)nb * 1024 * f);
+    o.Qe = L.add((size_t)nb * 1024 * i4);
+    o.Ph = L.add((size_t)nb * 1024 * f);
+    o.Pl = L.add((size_t)nb * 1024 * f);
+    o.Pe = L.add((size_t)nb * 1024 * i4);
+    o.yh = L.add(np * f);
+    o.yl = L.add(np * f);
+    o.ye = L.add(np * i4);
+    o.ch = L.add(np * f);
+    o.cl = L.add(np * f);
+    o.ce = L.add(np * i4);
+    o.parth = L.add((size_t)2 * nb * S * 32 * 4 * f);
+    o.partl = L.add((size_t)2 * nb * S * 32 * 4 * f);
+    o.parte = L.add((size_t)2 * nb * S * 32 * i4);
+    o.bandh = L.add((size_t)2 * nb * 32 * 4 * f);
+    o.bandl = L.add((size_t)2 * nb * 32 * 4 * f);
+    o.bande = L.add((size_t)2 * nb * 32 * i4);
+    o.flags = L.add((size_t)(2 * nb + 2 * nb * S) * i4);
+    o.err = L.add(4 * i4);
+    o.lsum = L.add((size_t)xdf_prep_blocks(np) * 2 * sizeof(double));
+    o.lam = L.add(4 * sizeof(double));
+}
+
+XView xdf_view(char* base, const XLayout& o, int N, int P, int d, double beta, double xi, int S, int W, int store,
+               const double* a, const double* b, int lda, int ldb, int spin_limit, int n_help)
+{
+    XView v;
+    memset(&v, 0, sizeof v);
+    v.N = N;
+    v.nb = (N + 1 + 31) / 32;
+    v.npad = v.nb * 32;
+    v.d = d;
+    v.S = S;
+    v.W = W;
+    v.store = store;
+    v.xi_zero = (xi == 0.0);
+    v.kappa = P / (2.0 * beta);
+    v.ks = P / (beta * beta);
+    v.beta = beta;
+    v.log_xi = (xi > 0.0) ? log(xi) : 0.0;
+    v.kap_h = (float)v.kappa;
+    v.kap_l = (float)(v.kappa - (double)v.kap_h);
+    v.a = a;
+    v.b = b;
+    v.lda = lda;
+    v.ldb = ldb;
+#define XP(name, T) v.name = (T*)(base + o.name)
+    XP(ah, float); XP(al, float); XP(bh, float); XP(bl, float); XP(crh, float); XP(crl, float);
+    v.tab = (const float2*)(base + o.tab);
+    XP(Mh, float); XP(Ml, float); XP(Me, int); XP(Gh, float); XP(Gl, float); XP(Ge, int);
+    XP(Qh, float); XP(Ql, float); XP(Qe, int); XP(Ph, float); XP(Pl, float); XP(Pe, int);
+    XP(yh, float); XP(yl, float); XP(ye, int); XP(ch, float); XP(cl, float); XP(ce, int);
+    XP(parth, float); XP(partl, float); XP(parte, int); XP(bandh, float); XP(bandl, float); XP(bande, int);
+    XP(flags, int); XP(err, int); XP(lsum, double); XP(lam, double);
+#undef XP
+    v.spin_limit = spin_limit > 0 ? spin_limit : (1 << 24);
+    if (n_help < 2) n_help = 2;
+    v.n_help_f = n_help / 2;
+    v.n_help_b = n_help - v.n_help_f;
+    return v;
+}
+
+int cfg_band(const pimd_config& c) { return c.exch_band > 0 ? c.exch_band : 4; }
+
 }  // namespace
 
 struct pimd_ctx {
@@ -131,9 +221,12 @@ struct pimd_ctx {
     long long steps = 0;
     Layout L;
     ExchLayout ex;
+    XLayout xl;
+    bool use_df = true;
     size_t off_spr, off_pair, off_fin, off_md, off_sc, off_flag;
     int n_help;
     ExchView xv;
+    XView xd;
     BeadView bv;
     ForceParams fp;
     MDParams mp;
@@ -175,6 +268,8 @@ extern "C" void pimd_default_config(pimd_config* cfg)
     cfg->thermostat = 1;
     cfg->helper_ctas = 0;
     cfg->spin_limit = 0;
+    cfg->exchange_arith = PIMD_XARITH_DF;
+    cfg->exch_band = 0;
 }
 
 extern "C" pimd_status pimd_create(int N, int P, int d, double beta, double omega, double g, double s, double xi,
@@ -219,6 +314,10 @@ extern "C" pimd_status pimd_configure(pimd_t c, const pimd_config* cfg)
     if (cfg->table_mode != PIMD_TABLE_STORE && cfg->table_mode != PIMD_TABLE_RECOMPUTE)
         return fail(c, PIMD_EINVAL, "pimd_configure: unknown table_mode");
     if (cfg->helper_ctas < 0 || cfg->spin_limit < 0) return fail(c, PIMD_EINVAL, "pimd_configure: negative count");
+    if (cfg->exchange_arith != PIMD_XARITH_DF && cfg->exchange_arith != PIMD_XARITH_FP64)
+        return fail(c, PIMD_EINVAL, "pimd_configure: unknown exchange_arith");
+    if (cfg->exch_band != 0 && (cfg->exch_band < 2 || cfg->exch_band > XDF_MAXW))
+        return fail(c, PIMD_EINVAL, "pimd_configure: exch_band must be 0 or in [2, 8]");
     c->cfg = *cfg;
     c->A = (cfg->amp_convention == PIMD_AMP_PAPER) ? c->g / (M_PI * c->s * c->s) : c->g;
     return PIMD_OK;
@@ -227,7 +326,9 @@ extern "C" pimd_status pimd_configure(pimd_t c, const pimd_config* cfg)
 static void ctx_layout(pimd_ctx* c)
 {
     c->L = Layout();
-    exch_layout(c->L, c->ex, c->N, EX_STREAMS, c->cfg.table_mode == PIMD_TABLE_STORE);
+    c->use_df = c->cfg.exchange_arith == PIMD_XARITH_DF;
+    if (c->use_df) xdf_layout(c->L, c->xl, c->N, EX_STREAMS, cfg_band(c->cfg), c->cfg.table_mode == PIMD_TABLE_STORE);
+    else exch_layout(c->L, c->ex, c->N, EX_STREAMS, c->cfg.table_mode == PIMD_TABLE_STORE);
     c->off_spr = c->L.add((size_t)springs_grid_x(c->N) * c->P * sizeof(double));
     c->off_pair = c->L.add((size_t)pair_grid_x(c->N) * c->P * 2 * sizeof(double));
     c->off_fin = c->L.add((size_t)exch_finalize_blocks(c->N) * sizeof(double));
@@ -270,15 +371,21 @@ static pimd_status enqueue_forces(pimd_ctx* c, cudaStream_t st, double* f, bool 
         if (e != cudaSuccess) return cuda_fail(c, e, "zero kernel");
     }
     if (exch) {
-        e = exch_launch_forward(c->xv, st, 1, pm);
-        if (e != cudaSuccess) return cuda_fail(c, e, "exchange recursion");
         FinalizeOut o;
         memset(&o, 0, sizeof(o));
         o.f = f;
         o.ldf = c->buf.n_pad;
         o.P = c->P;
         o.part = (double*)(base + c->off_fin);
-        e = exch_launch_adjoint(c->xv, o, exch_finalize_blocks(c->N), st, pm);
+        if (c->use_df) {
+            e = xdf_launch_forward(c->xd, st, pm);
+            if (e != cudaSuccess) return cuda_fail(c, e, "exchange recursion");
+            e = xdf_launch_adjoint(c->xd, o, st, pm);
+        } else {
+            e = exch_launch_forward(c->xv, st, 1, pm);
+            if (e != cudaSuccess) return cuda_fail(c, e, "exchange recursion");
+            e = exch_launch_adjoint(c->xv, o, exch_finalize_blocks(c->N), st, pm);
+        }
         if (e != cudaSuccess) return cuda_fail(c, e, "exchange forces");
     }
     return PIMD_OK;
@@ -293,12 +400,13 @@ static pimd_status enqueue_scalars(pimd_ctx* c, cudaStream_t st)
     memset(&s, 0, sizeof(s));
     s.springs = (double*)(base + c->off_spr);
     s.n_springs = springs_grid_x(c->N) * c->P;
-    s.lsum = c->xv.lsum;
-    s.n_lsum = exch_prep_blocks(c->N);
+    s.lsum = c->use_df ? c->xd.lsum : c->xv.lsum;
+    s.n_lsum = c->use_df ? xdf_prep_blocks(c->xd.npad) : exch_prep_blocks(c->N);
+    s.n_fin = c->use_df ? xdf_finalize_blocks(c->N) : exch_finalize_blocks(c->N);
+    s.lam = c->use_df ? c->xd.lam : nullptr;
     s.pair = (double*)(base + c->off_pair);
     s.n_pair = pair_grid_x(c->N) * c->P;
     s.fin = (double*)(base + c->off_fin);
-    s.n_fin = exch_finalize_blocks(c->N);
     s.md = (double*)(base + c->off_md);
     s.n_md = md_blocks(c->N, c->P, c->d);
     s.y_m = c->xv.y_m;
@@ -306,8 +414,8 @@ static pimd_status enqueue_scalars(pimd_ctx* c, cudaStream_t st)
     s.c_m = c->xv.c_m;
     s.c_e = c->xv.c_e;
     s.N = c->N;
-    s.xi_zero = c->xv.xi_zero;
-    s.log_xi = c->xv.log_xi;
+    s.xi_zero = (c->xi == 0.0);
+    s.log_xi = (c->xi > 0.0) ? log(c->xi) : 0.0;
     s.out = (double*)(base + c->off_sc);
     e = launch_scalars(s, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "scalar reduction");
@@ -333,12 +441,13 @@ static pimd_status check_device_error(pimd_ctx* c)
     char* base = (char*)c->buf.work;
     cudaError_t e = cudaStreamSynchronize(c->st);
     if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
-    e = cudaMemcpy(&h[0], c->xv.err, sizeof(int), cudaMemcpyDeviceToHost);
+    int* errp = c->use_df ? c->xd.err : c->xv.err;
+    e = cudaMemcpy(&h[0], errp, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(c, e, "error word read");
     e = cudaMemcpy(&h[1], base + c->off_flag, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(c, e, "flag read");
     if (h[0] != 0) {
-        cudaMemsetAsync(c->xv.err, 0, sizeof(int), c->st);
+        cudaMemsetAsync(errp, 0, sizeof(int), c->st);
         cudaStreamSynchronize(c->st);
         char msg[160];
         snprintf(msg, sizeof msg, "device wait gave up (code 0x%08x); increase spin_limit or check co-residency", h[0]);
@@ -365,9 +474,14 @@ extern "C" pimd_status pimd_bind(pimd_t c, const pimd_buffers* b, void* stream)
     c->st = (cudaStream_t)stream;
     c->n_help = default_helpers(c->cfg);
     const int np = b->n_pad;
-    c->xv = exch_view((char*)b->work, c->ex, c->N, c->P, c->d, c->beta, c->xi, EX_STREAMS,
-                      c->cfg.table_mode == PIMD_TABLE_STORE, b->r + (size_t)(c->P - 1) * c->d * np, b->r, np, np,
-                      c->cfg.spin_limit, c->n_help);
+    if (c->use_df)
+        c->xd = xdf_view((char*)b->work, c->xl, c->N, c->P, c->d, c->beta, c->xi, EX_STREAMS, cfg_band(c->cfg),
+                         c->cfg.table_mode == PIMD_TABLE_STORE, b->r + (size_t)(c->P - 1) * c->d * np, b->r, np, np,
+                         c->cfg.spin_limit, c->n_help);
+    else
+        c->xv = exch_view((char*)b->work, c->ex, c->N, c->P, c->d, c->beta, c->xi, EX_STREAMS,
+                          c->cfg.table_mode == PIMD_TABLE_STORE, b->r + (size_t)(c->P - 1) * c->d * np, b->r, np,
+                          np, c->cfg.spin_limit, c->n_help);
     c->bv.N = c->N;
     c->bv.P = c->P;
     c->bv.d = c->d;
@@ -396,8 +510,12 @@ extern "C" pimd_status pimd_bind(pimd_t c, const pimd_buffers* b, void* stream)
         if (e == cudaSuccess) e = cudaMemsetAsync(b->peta, 0, n * sizeof(double), c->st);
         if (e != cudaSuccess) return cuda_fail(c, e, "pimd_bind: thermostat reset");
     }
-    e = cudaMemsetAsync(c->xv.err, 0, 4 * sizeof(int), c->st);
+    e = cudaMemsetAsync(c->use_df ? c->xd.err : c->xv.err, 0, 4 * sizeof(int), c->st);
     if (e != cudaSuccess) return cuda_fail(c, e, "pimd_bind: error word reset");
+    if (c->use_df) {
+        e = xdf_upload_table((float2*)c->xd.tab, c->st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "pimd_bind: exp table upload");
+    }
     e = cudaMemsetAsync((char*)b->work + c->off_flag, 0, 4 * sizeof(int), c->st);
     if (e != cudaSuccess) return cuda_fail(c, e, "pimd_bind: flag reset");
     c->bound = true;

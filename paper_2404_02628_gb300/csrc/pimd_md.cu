@@ -287,6 +287,9 @@ __global__ void scalars_kernel(ScalarSources s)
     if (s.xi_zero) {
         t[SC_LAMBDA] = t[SC_L0];
         t[SC_LAMBDA_B] = t[SC_L0];
+    } else if (s.lam) {
+        t[SC_LAMBDA] = s.lam[0];
+        t[SC_LAMBDA_B] = s.lam[1];
     } else {
         t[SC_LAMBDA] = s.N * s.log_xi + wef_log(Wef{s.y_m[s.N], s.y_e[s.N]});
         t[SC_LAMBDA_B] = s.N * s.log_xi + wef_log(Wef{s.c_m[0], s.c_e[0]});

@@ -52,6 +52,7 @@ struct ScalarSources {
     const double* c_m; const int* c_e;      // backward Z at index 0
     int N, xi_zero;
     double log_xi;
+    const double* lam;                      // if set: [2] ln W_N forward/backward (double-float path)
     double* out;                            // [SC_COUNT]
 };
 

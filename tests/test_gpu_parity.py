@@ -23,13 +23,15 @@ EXCH_CASES = [(1, 4, 2, 1.0, 1.0), (2, 3, 2, 1.0, 0.5), (5, 8, 2, 2.0, 1.0), (31
               (257, 4, 2, 2.0, 0.3), (300, 6, 2, 1.0, 1.0), (130, 4, 2, 2.0, 0.0), (200, 4, 2, 1.0, 1e-3)]
 
 
+@pytest.mark.parametrize("arith", ["df", "fp64"])
 @pytest.mark.parametrize("table", ["store", "recompute"])
 @pytest.mark.parametrize("N,P,d,beta,xi", EXCH_CASES)
-def test_exchange_forces_and_potential(N, P, d, beta, xi, table):
+def test_exchange_forces_and_potential(N, P, d, beta, xi, table, arith):
     import paper_2404_02628_gb300 as pkg
     r = beads(N, P, d, 100 + N)
     mode = pkg.TABLE_STORE if table == "store" else pkg.TABLE_RECOMPUTE
-    S = make_system(N, P, d, beta, 0.0, 0.0, 0.5, xi, r, table_mode=mode)
+    ar = pkg.XARITH_DF if arith == "df" else pkg.XARITH_FP64
+    S = make_system(N, P, d, beta, 0.0, 0.0, 0.5, xi, r, table_mode=mode, exchange_arith=ar)
     F, V = S.exchange_forces()
     Fo, info = oracle.forces(r, beta, xi, 0.0, 0.0, 0.5)
     assert rel_inf(F, Fo) < TOL64
@@ -37,6 +39,20 @@ def test_exchange_forces_and_potential(N, P, d, beta, xi, table):
     est = S.estimators()
     assert abs(est["V_xi_bwd"] - info["V_xi_bwd"]) < TOL64 * abs(info["V_xi"])
     assert abs(est["spring"] - info["spring"]) < TOL64 * abs(info["spring"])
+    S.close()
+
+
+@pytest.mark.parametrize("W", [2, 3, 5, 8])
+@pytest.mark.parametrize("N,xi", [(700, 1.0), (450, 0.5)])
+def test_exchange_band_widths(N, xi, W):
+    """The double-float recursion gives the same forces for every look-ahead width."""
+    P, d, beta = 4, 2, 2.0
+    r = beads(N, P, d, 150 + N)
+    S = make_system(N, P, d, beta, 0.0, 0.0, 0.5, xi, r, exch_band=W)
+    F, V = S.exchange_forces()
+    Fo, info = oracle.forces(r, beta, xi, 0.0, 0.0, 0.5)
+    assert rel_inf(F, Fo) < TOL64
+    assert abs(V - info["V_xi"]) < TOL64 * abs(info["V_xi"])
     S.close()
 
 
