@@ -80,7 +80,7 @@ typedef struct {
     int exchange_arith; /* PIMD_XARITH_DF (default): exchange recursion, probabilities and
                            endpoint forces in double-float (FP32 pairs, ~48-bit mantissa, int32
                            exponent) on the FP32 pipe; PIMD_XARITH_FP64: native FP64 throughout */
-    int exch_band;      /* look-ahead band width W of the double-float recursion, 2..8
+    int exch_band;      /* look-ahead band width W of the double-float recursion, 2..5
                            (0 = default 4): the chain block adds the W-2 tiles next to the
                            diagonal itself, helper blocks the rest */
 } pimd_config;

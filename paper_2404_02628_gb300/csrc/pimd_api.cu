@@ -117,7 +117,8 @@ constexpr int EX_STREAMS = 4;
 
 // Workspace regions of the double-float exchange path.
 struct XLayout {
-    size_t ah, al, bh, bl, crh, crl, tab, Mh, Ml, Me, Gh, Gl, Ge, Qh, Ql, Qe, Ph, Pl, Pe, yh, yl, ye, ch, cl, ce,
+    size_t ah, al, bh, bl, crh, crl, tab, Mh, Ml, Me, Gh, Gl, Ge, Qh, Ql, Qe, Ph, Pl, Pe, yh, yl, ye, ch, cl, ce, uh, ul,
+        wh, wl,
         parth, partl, parte, bandh, bandl, bande, flags, err, lsum, lam;
 };
 
@@ -151,6 +152,10 @@ void xdf_layout(Layout& L, XLayout& o, int N, int S, int W, int store)
     o.ch = L.add(np * f);
     o.cl = L.add(np * f);
     o.ce = L.add(np * i4);
+    o.uh = L.add(3 * np * f);
+    o.ul = L.add(3 * np * f);
+    o.wh = L.add(3 * np * f);
+    o.wl = L.add(3 * np * f);
     o.parth = L.add((size_t)2 * nb * S * 32 * 4 * f);
     o.partl = L.add((size_t)2 * nb * S * 32 * 4 * f);
     o.parte = L.add((size_t)2 * nb * S * 32 * i4);
@@ -192,6 +197,7 @@ XView xdf_view(char* base, const XLayout& o, int N, int P, int d, double beta, d
     XP(Mh, float); XP(Ml, float); XP(Me, int); XP(Gh, float); XP(Gl, float); XP(Ge, int);
     XP(Qh, float); XP(Ql, float); XP(Qe, int); XP(Ph, float); XP(Pl, float); XP(Pe, int);
     XP(yh, float); XP(yl, float); XP(ye, int); XP(ch, float); XP(cl, float); XP(ce, int);
+    XP(uh, float); XP(ul, float); XP(wh, float); XP(wl, float);
     XP(parth, float); XP(partl, float); XP(parte, int); XP(bandh, float); XP(bandl, float); XP(bande, int);
     XP(flags, int); XP(err, int); XP(lsum, double); XP(lam, double);
 #undef XP
@@ -317,7 +323,7 @@ extern "C" pimd_status pimd_configure(pimd_t c, const pimd_config* cfg)
     if (cfg->exchange_arith != PIMD_XARITH_DF && cfg->exchange_arith != PIMD_XARITH_FP64)
         return fail(c, PIMD_EINVAL, "pimd_configure: unknown exchange_arith");
     if (cfg->exch_band != 0 && (cfg->exch_band < 2 || cfg->exch_band > XDF_MAXW))
-        return fail(c, PIMD_EINVAL, "pimd_configure: exch_band must be 0 or in [2, 8]");
+        return fail(c, PIMD_EINVAL, "pimd_configure: exch_band must be 0 or in [2, 5]");
     c->cfg = *cfg;
     c->A = (cfg->amp_convention == PIMD_AMP_PAPER) ? c->g / (M_PI * c->s * c->s) : c->g;
     return PIMD_OK;

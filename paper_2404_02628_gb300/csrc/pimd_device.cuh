@@ -123,6 +123,15 @@ __device__ __forceinline__ bool wait_flag(const int* flag, int want, int* err, i
     return false;
 }
 
+// Block-wide barrier for code where lanes of a warp may have taken different
+// paths just before (e.g. lane-0-only stores or waits): bar.sync is
+// warp-aligned, so the warp is reconverged first.
+__device__ __forceinline__ void block_sync()
+{
+    __syncwarp();
+    __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
 // Deterministic block reduction of NV doubles (blockDim.x a multiple of 32,
 // at most 1024).  Result valid in thread 0.
@@ -134,11 +143,11 @@ __device__ __forceinline__ void block_reduce(double (&v)[NV], double* smem /* 32
 #pragma unroll
     for (int q = 0; q < NV; ++q)
         for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
-    __syncthreads();
+    block_sync();
     if (lane == 0)
 #pragma unroll
         for (int q = 0; q < NV; ++q) smem[w * NV + q] = v[q];
-    __syncthreads();
+    block_sync();
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
@@ -147,5 +156,5 @@ __device__ __forceinline__ void block_reduce(double (&v)[NV], double* smem /* 32
             v[q] = s;
         }
     }
-    __syncthreads();
+    block_sync();
 }

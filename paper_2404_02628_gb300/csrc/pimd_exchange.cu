@@ -246,7 +246,7 @@ __device__ void chain_forward(const ExchView& v, ExSlot* slots, ChainSmem* cs)
     for (int J = 0; J < v.nb; ++J) {
         stage_tile_block(v, sd, J, J);
         if (J > 0) stage_tile_block(v, ss, J, J - 1);
-        __syncthreads();
+        block_sync();
         if (J > 0) {
             int Em = WEF_ZERO_E;
             for (int q = 0; q < 4; ++q) {
@@ -263,7 +263,7 @@ __device__ void chain_forward(const ExchView& v, ExSlot* slots, ChainSmem* cs)
             cs->red_m[w][lane] = s;
             cs->red_e[w][lane] = Em;
         }
-        __syncthreads();
+        block_sync();
         if (w == 0) {
             Wef acc = wef_zero();
             const int ns = min(v.S, J - 1);
@@ -311,7 +311,7 @@ __device__ void chain_forward(const ExchView& v, ExSlot* slots, ChainSmem* cs)
                 if (lane == 0) st_release(&flag_chain[J], 1);
             }
         }
-        __syncthreads();
+        block_sync();
         if (cs->abort) return;
     }
 }
@@ -334,7 +334,7 @@ __device__ void chain_backward(const ExchView& v, ExSlot* slots, ChainSmem* cs)
     for (int I = v.nb - 1; I >= 0; --I) {
         stage_tile_block(v, sd, I, I);
         if (I + 1 < v.nb) stage_tile_block(v, ss, I + 1, I);
-        __syncthreads();
+        block_sync();
         if (I + 1 < v.nb) {
             int Em = WEF_ZERO_E;
             for (int q = 0; q < 4; ++q) {
@@ -351,7 +351,7 @@ __device__ void chain_backward(const ExchView& v, ExSlot* slots, ChainSmem* cs)
             cs->red_m[w][lane] = s;
             cs->red_e[w][lane] = Em;
         }
-        __syncthreads();
+        block_sync();
         if (w == 0) {
             Wef acc = wef_zero();
             const int ns = min(v.S, v.nb - 2 - I);
@@ -400,7 +400,7 @@ __device__ void chain_backward(const ExchView& v, ExSlot* slots, ChainSmem* cs)
                 if (lane == 0) st_release(&flag_chain[I], 1);
             }
         }
-        __syncthreads();
+        block_sync();
         if (cs->abort) return;
     }
 }
@@ -413,7 +413,7 @@ __device__ void helper_forward(const ExchView& v, ExSlot* slots, ChainSmem* cs, 
     int* flag_part = v.flags + 2 * v.nb;
     ExSlot* s = &slots[w];
     if (tid == 0) cs->abort = 0;
-    __syncthreads();
+    block_sync();
     long long q = 0;
     for (int J = 2; J < v.nb; ++J) {
         const int ns = min(v.S, J - 1);
@@ -444,7 +444,7 @@ __device__ void helper_forward(const ExchView& v, ExSlot* slots, ChainSmem* cs, 
             cs->hm[w][lane][2] = acc.v[1];
             cs->hm[w][lane][3] = acc.v[2];
             cs->he[w][lane] = acc.e;
-            __syncthreads();
+            block_sync();
             if (cs->abort) return;
             if (w == 0) {
                 VAcc t = vacc_zero();
@@ -454,7 +454,7 @@ __device__ void helper_forward(const ExchView& v, ExSlot* slots, ChainSmem* cs, 
                 __syncwarp();
                 if (lane == 0) st_release(&flag_part[J * v.S + si], 1);
             }
-            __syncthreads();
+            block_sync();
         }
     }
 }
@@ -467,7 +467,7 @@ __device__ void helper_backward(const ExchView& v, ExSlot* slots, ChainSmem* cs,
     int* flag_part = v.flags + 2 * v.nb + v.nb * v.S;
     ExSlot* s = &slots[w];
     if (tid == 0) cs->abort = 0;
-    __syncthreads();
+    block_sync();
     long long q = 0;
     for (int I = v.nb - 3; I >= 0; --I) {
         const int ns = min(v.S, v.nb - 2 - I);
@@ -499,7 +499,7 @@ __device__ void helper_backward(const ExchView& v, ExSlot* slots, ChainSmem* cs,
             cs->hm[w][lane][2] = acc.v[1];
             cs->hm[w][lane][3] = acc.v[2];
             cs->he[w][lane] = acc.e;
-            __syncthreads();
+            block_sync();
             if (cs->abort) return;
             if (w == 0) {
                 VAcc t = vacc_zero();
@@ -509,7 +509,7 @@ __device__ void helper_backward(const ExchView& v, ExSlot* slots, ChainSmem* cs,
                 __syncwarp();
                 if (lane == 0) st_release(&flag_part[I * v.S + si], 1);
             }
-            __syncthreads();
+            block_sync();
         }
     }
 }

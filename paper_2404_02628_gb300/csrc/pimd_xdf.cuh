@@ -30,7 +30,7 @@
 #define XDF_THREADS 256
 #define XDF_WARPS 8
 #define XDF_LD 33
-#define XDF_MAXW 8
+#define XDF_MAXW 5
 
 struct XView {
     int N, nb, npad, d, S, W;
@@ -51,6 +51,8 @@ struct XView {
     float* Ph; float* Pl; int* Pe;   // [nb][1024]
     float* yh; float* yl; int* ye;   // [npad] forward solution y
     float* ch; float* cl; int* ce;   // [npad] backward solution c
+    float* uh; float* ul;            // [3][npad] y[k] b_k (mantissa of y times b_k), published with y
+    float* wh; float* wl;            // [3][npad] c[n] a_{n-1}, published with c
     float* parth; float* partl; int* parte;  // helper partials [2][nb][S][32] x 4 / x 1
     float* bandh; float* bandl; int* bande;  // band sums [2][nb][32] x 4 / x 1
     int* flags;                  // [2][nb] chain flags, then [2][nb][S] partial flags

@@ -42,7 +42,7 @@ def test_exchange_forces_and_potential(N, P, d, beta, xi, table, arith):
     S.close()
 
 
-@pytest.mark.parametrize("W", [2, 3, 5, 8])
+@pytest.mark.parametrize("W", [2, 3, 4, 5])
 @pytest.mark.parametrize("N,xi", [(700, 1.0), (450, 0.5)])
 def test_exchange_band_widths(N, xi, W):
     """The double-float recursion gives the same forces for every look-ahead width."""
