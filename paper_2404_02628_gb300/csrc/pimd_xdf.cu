@@ -557,11 +557,46 @@ struct ChainS {
     int abort;
     int ready;
     int y_ready, published, parts_ready, done;  // chain-block progress counters
+    unsigned long long mb_all;                  // compute-warp barrier (6 arrivals)
+    unsigned long long mb_pair[3];              // band warp-pair barriers (2 arrivals)
 };
 
-__device__ __forceinline__ void named_sync(int id, int nthreads)
+// Barrier for a subset of the warps of a block, on a shared-memory mbarrier:
+// each warp reconverges, one lane arrives for it, and every lane waits for
+// the phase to complete (bounded; a timeout records the error and raises the
+// block's abort word).  `phase` is the warp's local count of completed uses.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* mb, int count)
 {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mb)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_sync(unsigned long long* mb, unsigned& phase, int lane, int limit, int* err,
+                                          int* abort_word, int code)
+{
+    __syncwarp();
+    if (lane == 0)
+        asm volatile("{ .reg .b64 st; mbarrier.arrive.shared::cta.b64 st, [%0]; }" ::"r"(smem_u32(mb)) : "memory");
+    bool ok = false;
+    for (int it = 0; it < limit; ++it) {
+        unsigned done;
+        asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                     : "=r"(done)
+                     : "r"(smem_u32(mb)), "r"(phase & 1)
+                     : "memory");
+        if (done) {
+            ok = true;
+            break;
+        }
+    }
+    phase += 1;
+    if (!ok && lane == 0) {
+        atomicCAS(err, 0, (PIMD_DEVERR_TIMEOUT << 24) | (code & 0xFFFFFF));
+        *(volatile int*)abort_word = 1;
+    }
+    __syncwarp();
+    return ok;
 }
 
 __device__ __forceinline__ dfw cget(const float (*h)[32], const float (*l)[32], const int (*e)[32], int i, int j)
@@ -654,6 +689,8 @@ __device__ void xchain(const XView& v, DfwTile* Tall, ChainS* cs)
         cs->published = -1;
         cs->parts_ready = 0;
         cs->done = -1;
+        mbar_init(&cs->mb_all, 6);
+        for (int q = 0; q < 3; ++q) mbar_init(&cs->mb_pair[q], 2);
     }
     if (tid < 32) {
         for (int m = 0; m < W; ++m) {
@@ -726,9 +763,11 @@ __device__ void xchain(const XView& v, DfwTile* Tall, ChainS* cs)
     // abort raised) they run to the end without waiting, so every named
     // barrier is met by all six warps.
     const int NCT = 6 * 32;
+    unsigned ph_all = 0, ph_pair = 0;
+    auto sync_all = [&](int code) { mbar_sync(&cs->mb_all, ph_all, lane, lim, v.err, &cs->abort, code); };
     fetch_set_c<DIR>(v, Tall, 0, tid, NCT);
     cp_wait<0>();
-    named_sync(1, NCT);
+    sync_all(0x5a0000);
     for (int it = 0; it < nb; ++it) {
         const int J = chain_block<DIR>(v, it);
         DfwTile* T = Tall + (it & 1) * W;
@@ -760,8 +799,7 @@ __device__ void xchain(const XView& v, DfwTile* Tall, ChainS* cs)
             cput(C.rh, C.rl, C.re, w, lane, p);
         }
         (void)ok;
-        __syncwarp();
-        named_sync(1, NCT);
+        sync_all(0x5b0000 + it);
         // phase B
         if (w == 0) {
             // the slot x[xb] was last published two iterations ago
@@ -787,7 +825,7 @@ __device__ void xchain(const XView& v, DfwTile* Tall, ChainS* cs)
             cput(C.hh, C.hl, C.he, s1, lane, dfw_zero());
             cput(C.ph, C.pl, C.pe, s1, lane, dfw_zero());
         }
-        named_sync(1, NCT);
+        sync_all(0x5c0000 + it);
         // phase C: band tiles (pairs of warps, one half of the columns each)
         if (w < 2 * (W - 2)) {
             const int m = 2 + (w >> 1), half = w & 1;
@@ -798,7 +836,7 @@ __device__ void xchain(const XView& v, DfwTile* Tall, ChainS* cs)
                                        : dot_col_vec(&T[m], lane, C.xh[xb], C.xl[xb], C.xe[xb], 16 * half, 16 * half + 16);
                 cput(C.rh, C.rl, C.re, w, lane, p);
             }
-            named_sync(2 + (w >> 1), 64);
+            mbar_sync(&cs->mb_pair[w >> 1], ph_pair, lane, lim, v.err, &cs->abort, 0x5d0000 + it);
             if (on && half == 0) {
                 const int sl = Jt % W;
                 dfw t[3] = {cget(C.hh, C.hl, C.he, sl, lane), cget(C.rh, C.rl, C.re, w, lane), cget(C.rh, C.rl, C.re, w + 1, lane)};
@@ -806,8 +844,7 @@ __device__ void xchain(const XView& v, DfwTile* Tall, ChainS* cs)
             }
         }
         if (more) cp_wait<0>();
-        __syncwarp();
-        named_sync(1, NCT);
+        sync_all(0x5e0000 + it);
         if (tid == 0) {
             __threadfence_block();
             vstore(&cs->done, it);
