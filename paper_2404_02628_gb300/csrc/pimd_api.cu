@@ -117,7 +117,7 @@ constexpr int EX_STREAMS = 4;
 
 // Workspace regions of the double-float exchange path.
 struct XLayout {
-    size_t ah, al, bh, bl, crh, crl, tab, Mh, Ml, Me, Gh, Gl, Ge, Qh, Ql, Qe, Ph, Pl, Pe, yh, yl, ye, ch, cl, ce, uh, ul,
+    size_t ah, al, bh, bl, crh, crl, tab, M, G, Q, P, yh, yl, ye, ch, cl, ce, uh, ul,
         wh, wl,
         parth, partl, parte, bandh, bandl, bande, flags, err, lsum, lam;
 };
@@ -134,18 +134,10 @@ void xdf_layout(Layout& L, XLayout& o, int N, int S, int W, int store)
     o.crh = L.add(np * f);
     o.crl = L.add(np * f);
     o.tab = L.add(256 * sizeof(float2));
-    o.Mh = L.add((size_t)nt * 1024 * f);
-    o.Ml = L.add((size_t)nt * 1024 * f);
-    o.Me = L.add((size_t)nt * 1024 * i4);
-    o.Gh = L.add((size_t)nb * 1024 * f);
-    o.Gl = L.add((size_t)nb * 1024 * f);
-    o.Ge = L.add((size_t)nb * 1024 * i4);
-    o.Qh = L.add((size_t)nb * 1024 * f);
-    o.Ql = L.add((size_t)nb * 1024 * f);
-    o.Qe = L.add((size_t)nb * 1024 * i4);
-    o.Ph = L.add((size_t)nb * 1024 * f);
-    o.Pl = L.add((size_t)nb * 1024 * f);
-    o.Pe = L.add((size_t)nb * 1024 * i4);
+    o.M = L.add((size_t)nt * sizeof(XTile));
+    o.G = L.add((size_t)nb * sizeof(XTile));
+    o.Q = L.add((size_t)nb * sizeof(XTile));
+    o.P = L.add((size_t)nb * sizeof(XTile));
     o.yh = L.add(np * f);
     o.yl = L.add(np * f);
     o.ye = L.add(np * i4);
@@ -194,8 +186,7 @@ XView xdf_view(char* base, const XLayout& o, int N, int P, int d, double beta, d
 #define XP(name, T) v.name = (T*)(base + o.name)
     XP(ah, float); XP(al, float); XP(bh, float); XP(bl, float); XP(crh, float); XP(crl, float);
     v.tab = (const float2*)(base + o.tab);
-    XP(Mh, float); XP(Ml, float); XP(Me, int); XP(Gh, float); XP(Gl, float); XP(Ge, int);
-    XP(Qh, float); XP(Ql, float); XP(Qe, int); XP(Ph, float); XP(Pl, float); XP(Pe, int);
+    XP(M, XTile); XP(G, XTile); XP(Q, XTile); XP(P, XTile);
     XP(yh, float); XP(yl, float); XP(ye, int); XP(ch, float); XP(cl, float); XP(ce, int);
     XP(uh, float); XP(ul, float); XP(wh, float); XP(wl, float);
     XP(parth, float); XP(partl, float); XP(parte, int); XP(bandh, float); XP(bandl, float); XP(bande, int);

@@ -8,17 +8,10 @@
 
 namespace {
 
-// 32x32 dfw matrix.  Element (r, c) sits at RIDX(r, c): row r is rotated by
-// r, so both row walks (lane = r) and column walks (lane = c) of a tile in
-// shared memory hit 32 distinct banks, and a tile is one contiguous 4 KB run
-// per component that cp.async copies verbatim.  Global tiles use the same order.
+// Element (r, c) of an XTile (see pimd_xdf.cuh).
 #define RIDX(r, c) (((r) << 5) + (((c) + (r)) & 31))
-#define XDF_TILES 16  // tile slots per recursion block: 2 per helper warp, 2 x W for a chain block
-struct DfwTile {
-    float h[1024];
-    float l[1024];
-    int e[1024];
-};
+#define XDF_TILES 16  // tile slots per recursion block: 2 per helper, a ring of 16 / W sets of W for a chain block
+typedef XTile DfwTile;
 
 __device__ __forceinline__ void cp16(void* dst, const void* src)
 {
@@ -33,13 +26,11 @@ __device__ __forceinline__ void cp_wait()
 }
 
 // Asynchronous copy of a global tile into shared memory by `nthr` threads.
-__device__ __forceinline__ void tile_copy(DfwTile* s, const float* h, const float* l, const int* e, int tid, int nthr)
+__device__ __forceinline__ void tile_copy(DfwTile* s, const XTile* g, int tid, int nthr)
 {
-    for (int q = tid; q < 256; q += nthr) {
-        cp16(&s->h[4 * q], h + 4 * q);
-        cp16(&s->l[4 * q], l + 4 * q);
-        cp16(&s->e[4 * q], e + 4 * q);
-    }
+    const float4* src = reinterpret_cast<const float4*>(g);
+    float4* dst = reinterpret_cast<float4*>(s);
+    for (int q = tid; q < (int)(sizeof(XTile) / 16); q += nthr) cp16(dst + q, src + q);
 }
 
 struct DVAcc {  // non-negative scalar s and signed vector v sharing exponent e
@@ -136,77 +127,70 @@ __device__ __forceinline__ void acc_term(df& s, float ah, float al, float bh, fl
     s.l = __fadd_rn(s.l, __fadd_rn(t.l, __fadd_rn(pe, cross)));
 }
 
-// sum_{t in [t0,t1)} A[r][t] * x[t]  (x given as per-t dfw in shared arrays)
-__device__ __forceinline__ dfw dot_row_vec(const DfwTile* A, int r, const float* xh, const float* xl, const int* xe,
-                                           int t0, int t1)
+// Packed dfw for vectors in shared memory: {h, l, exponent bits, 0}, read
+// by one 16-byte (broadcast) load.
+__device__ __forceinline__ float4 dfw_pack(dfw x) { return make_float4(x.h, x.l, __int_as_float(x.e), 0.f); }
+__device__ __forceinline__ dfw dfw_unpack(float4 x) { return dfw{x.x, x.y, __float_as_int(x.z)}; }
+
+// sum over t in [c0, c1) of A[lane][t] x[t] (COL = false) or A[t][lane] x[t]
+// (COL = true); c1 - c0 is a positive multiple of 8.  One pass: each 8-term
+// chunk is loaded, its largest exponent taken, the running sum rescaled to
+// the new largest exponent (a power of two: exact, or negligible when it
+// underflows) and the chunk's terms added with the compensated acc_term.
+template <bool COL>
+__device__ __forceinline__ dfw dot_seg(const DfwTile* A, int lane, const float4* x, int c0, int c1)
 {
     int E = WEF_ZERO_E;
-    for (int t = t0; t < t1; ++t) E = max(E, A->e[RIDX(r, t)] + xe[t]);
-    if (E <= WEF_ZERO_E / 2) return dfw_zero();
     df s = df{0.f, 0.f};
-    for (int t = t0; t < t1; ++t) {
-        const int q = RIDX(r, t);
-        acc_term(s, A->h[q], A->l[q], xh[t], xl[t], pow2f(A->e[q] + xe[t] - E));
+    for (int t0 = c0; t0 < c1; t0 += 8) {
+        float ah[8], al[8], xh[8], xl[8];
+        int k[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int t = t0 + u, q = COL ? RIDX(t, lane) : RIDX(lane, t);
+            const float4 xv = x[t];
+            ah[u] = A->h[q];
+            al[u] = A->l[q];
+            xh[u] = xv.x;
+            xl[u] = xv.y;
+            k[u] = A->e[q] + __float_as_int(xv.z);
+        }
+        int Ec = k[0];
+#pragma unroll
+        for (int u = 1; u < 8; ++u) Ec = max(Ec, k[u]);
+        const int En = max(E, Ec);
+        const float g = pow2f(E - En);
+        s.h = __fmul_rn(s.h, g);
+        s.l = __fmul_rn(s.l, g);
+        E = En;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc_term(s, ah[u], al[u], xh[u], xl[u], pow2f(k[u] - E));
     }
+    if (E <= WEF_ZERO_E / 2) return dfw_zero();
     return dfw_norm(fast_two_sum(s.h, s.l), E);
 }
 
-// sum over t in [t0,t1) of A[r][t] * (x[t] + y[t])
-__device__ __forceinline__ dfw dot_row_vec2(const DfwTile* A, int r, const float* xh, const float* xl, const int* xe,
-                                            const float* yh, const float* yl, const int* ye, int t0, int t1)
+// sum of t[0..K) (max-exponent aligned compensated sum; zero entries add nothing)
+template <int K>
+__device__ __forceinline__ dfw dfw_sum_k(const dfw* t)
 {
     int E = WEF_ZERO_E;
-    for (int t = t0; t < t1; ++t) E = max(E, A->e[RIDX(r, t)] + max(xe[t], ye[t]));
+#pragma unroll
+    for (int i = 0; i < K; ++i) E = max(E, t[i].e);
     if (E <= WEF_ZERO_E / 2) return dfw_zero();
     df s = df{0.f, 0.f};
-    for (int t = t0; t < t1; ++t) {
-        const int q = RIDX(r, t);
-        acc_term(s, A->h[q], A->l[q], xh[t], xl[t], pow2f(A->e[q] + xe[t] - E));
-        acc_term(s, A->h[q], A->l[q], yh[t], yl[t], pow2f(A->e[q] + ye[t] - E));
-    }
+#pragma unroll
+    for (int i = 0; i < K; ++i) acc_term(s, t[i].h, t[i].l, 1.0f, 0.0f, pow2f(t[i].e - E));
     return dfw_norm(fast_two_sum(s.h, s.l), E);
 }
 
-// sum over t in [t0,t1) of A[t][c] * (x[t] + y[t])
-__device__ __forceinline__ dfw dot_col_vec2(const DfwTile* A, int c, const float* xh, const float* xl, const int* xe,
-                                            const float* yh, const float* yl, const int* ye, int t0, int t1)
+// sum of t[0..n), n <= 8, with t[n..8) zero: the smallest fixed size that covers n
+__device__ __forceinline__ dfw dfw_sum8(const dfw (&t)[8], int n)
 {
-    int E = WEF_ZERO_E;
-    for (int t = t0; t < t1; ++t) E = max(E, A->e[RIDX(t, c)] + max(xe[t], ye[t]));
-    if (E <= WEF_ZERO_E / 2) return dfw_zero();
-    df s = df{0.f, 0.f};
-    for (int t = t0; t < t1; ++t) {
-        const int q = RIDX(t, c);
-        acc_term(s, A->h[q], A->l[q], xh[t], xl[t], pow2f(A->e[q] + xe[t] - E));
-        acc_term(s, A->h[q], A->l[q], yh[t], yl[t], pow2f(A->e[q] + ye[t] - E));
-    }
-    return dfw_norm(fast_two_sum(s.h, s.l), E);
-}
-
-// sum of n dfw values (max-exponent aligned compensated sum)
-__device__ __forceinline__ dfw dfw_sum(const dfw* v, int n)
-{
-    int E = WEF_ZERO_E;
-    for (int i = 0; i < n; ++i) E = max(E, v[i].e);
-    if (E <= WEF_ZERO_E / 2) return dfw_zero();
-    df s = df{0.f, 0.f};
-    for (int i = 0; i < n; ++i) acc_term(s, v[i].h, v[i].l, 1.0f, 0.0f, pow2f(v[i].e - E));
-    return dfw_norm(fast_two_sum(s.h, s.l), E);
-}
-
-// sum_{t in [t0,t1)} A[t][c] * x[t]  (transposed)
-__device__ __forceinline__ dfw dot_col_vec(const DfwTile* A, int c, const float* xh, const float* xl, const int* xe,
-                                           int t0, int t1)
-{
-    int E = WEF_ZERO_E;
-    for (int t = t0; t < t1; ++t) E = max(E, A->e[RIDX(t, c)] + xe[t]);
-    if (E <= WEF_ZERO_E / 2) return dfw_zero();
-    df s = df{0.f, 0.f};
-    for (int t = t0; t < t1; ++t) {
-        const int q = RIDX(t, c);
-        acc_term(s, A->h[q], A->l[q], xh[t], xl[t], pow2f(A->e[q] + xe[t] - E));
-    }
-    return dfw_norm(fast_two_sum(s.h, s.l), E);
+    if (n <= 2) return dfw_sum_k<2>(t);
+    if (n <= 4) return dfw_sum_k<4>(t);
+    if (n <= 6) return dfw_sum_k<6>(t);
+    return dfw_sum_k<8>(t);
 }
 
 // (A B)[r][c] over t in [t0, t1)
@@ -345,7 +329,7 @@ __device__ __forceinline__ void fetch_tile_warp(const XView& v, DfwTile* s, int 
 {
     if (!tile_stored(v, J, I)) return;
     const long long t = xdf_tile_index(v, J, I);
-    tile_copy(s, v.Mh + t * 1024, v.Ml + t * 1024, v.Me + t * 1024, lane, 32);
+    tile_copy(s, v.M + t, lane, 32);
 }
 
 __device__ __forceinline__ size_t xpart_index(const XView& v, int dir, int blk, int s, int lane)
@@ -459,16 +443,14 @@ __global__ void __launch_bounds__(256) xdf_table_kernel(XView v, long long ntile
             J = (int)(t / v.W);
             I = J - (int)(t % v.W);
         }
-        float* Mh = v.Mh + t * 1024;
-        float* Ml = v.Ml + t * 1024;
-        int* Me = v.Me + t * 1024;
+        XTile* Mt = v.M + t;
         for (int q = threadIdx.x; q < 1024; q += blockDim.x) {
             const int r = q >> 5, c = q & 31;
             const dfw m = (I >= 0) ? xM(v, 32 * J + r, 32 * I + c, tab) : dfw_zero();
             const int o = RIDX(r, c);
-            Mh[o] = m.h;
-            Ml[o] = m.l;
-            Me[o] = m.e;
+            Mt->h[o] = m.h;
+            Mt->l[o] = m.l;
+            Mt->e[o] = m.e;
         }
     }
 }
@@ -487,14 +469,14 @@ __global__ void __launch_bounds__(256) xdf_blockops_kernel(XView v)
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     {
         const long long t = xdf_tile_index(v, J, J);
-        tile_copy(L, v.Mh + t * 1024, v.Ml + t * 1024, v.Me + t * 1024, threadIdx.x, blockDim.x);
+        tile_copy(L, v.M + t, threadIdx.x, blockDim.x);
         if (J >= 1) {
             const long long ts = xdf_tile_index(v, J, J - 1);
-            tile_copy(Ms, v.Mh + ts * 1024, v.Ml + ts * 1024, v.Me + ts * 1024, threadIdx.x, blockDim.x);
+            tile_copy(Ms, v.M + ts, threadIdx.x, blockDim.x);
         }
         if (J + 1 < v.nb) {
             const long long tp = xdf_tile_index(v, J + 1, J);
-            tile_copy(Mp, v.Mh + tp * 1024, v.Ml + tp * 1024, v.Me + tp * 1024, threadIdx.x, blockDim.x);
+            tile_copy(Mp, v.M + tp, threadIdx.x, blockDim.x);
         }
         cp_commit();
         cp_wait<0>();
@@ -515,38 +497,39 @@ __global__ void __launch_bounds__(256) xdf_blockops_kernel(XView v)
         tile_put(G, lane, c, (lane >= c) ? acc : dfw_zero());
     }
     block_sync();
-    const size_t base = (size_t)J * 1024;
     for (int q = threadIdx.x; q < 1024; q += blockDim.x) {
         const int r = q >> 5, c = q & 31, o = RIDX(r, c);
-        v.Gh[base + o] = G->h[o];
-        v.Gl[base + o] = G->l[o];
-        v.Ge[base + o] = G->e[o];
+        v.G[J].h[o] = G->h[o];
+        v.G[J].l[o] = G->l[o];
+        v.G[J].e[o] = G->e[o];
         dfw Q = dfw_zero(), Pm = dfw_zero();
         if (J >= 1) Q = dot_mat(G, Ms, r, c, 0, r + 1);
         if (J + 1 < v.nb) Pm = dot_mat(Mp, G, r, c, c, 32);
-        v.Qh[base + o] = Q.h;
-        v.Ql[base + o] = Q.l;
-        v.Qe[base + o] = Q.e;
-        v.Ph[base + o] = Pm.h;
-        v.Pl[base + o] = Pm.l;
-        v.Pe[base + o] = Pm.e;
+        v.Q[J].h[o] = Q.h;
+        v.Q[J].l[o] = Q.l;
+        v.Q[J].e[o] = Q.e;
+        v.P[J].h[o] = Pm.h;
+        v.P[J].l[o] = Pm.l;
+        v.P[J].e[o] = Pm.e;
     }
 }
 
 // ------------------------------------------------------------------------
 // recursion: chain blocks and helpers
 
+#define XDF_XR 4        // solution blocks kept in shared memory (ring, slot = iteration mod XDF_XR)
+#define XDF_NSETS 8     // most tile sets in flight (XDF_TILES / W)
+#define XDF_NSEG 12     // phase-1 segments: two per compute warp
+#define XDF_MAXS 8      // most helper partial streams per block
+
 struct ChainArrays {
-    float xh[2][32], xl[2][32];   // solution blocks, x[J & 1] = block J (forward) / iteration parity (backward)
-    int xe[2][32];
-    float ghh[2][32], ghl[2][32]; // G h of the next block, double-buffered the same way
-    int ghe[2][32];
-    float hh[XDF_MAXW][32], hl[XDF_MAXW][32];  // band accumulators (ring, slot = block mod W)
+    float4 xv[XDF_XR + 1][32];                   // solution blocks (ring); slot XDF_XR: s = h + p of
+                                                 // the block, the vector G acts on
+    float hh[XDF_MAXW][32], hl[XDF_MAXW][32];    // band accumulators (ring, slot = block mod W)
     int he[XDF_MAXW][32];
-    float ph[XDF_MAXW][32], pl[XDF_MAXW][32];  // helper partial sums (ring)
+    float ph[XDF_MAXW][32], pl[XDF_MAXW][32];    // helper partial sums (ring)
     int pe[XDF_MAXW][32];
-    float rh[XDF_WARPS][32], rl[XDF_WARPS][32];  // per-warp partial results
-    int re[XDF_WARPS][32];
+    float4 r[XDF_NSEG][32];                      // phase-1 partial products, slot 2 w + j
 };
 
 struct ChainS {
@@ -557,14 +540,11 @@ struct ChainS {
     int abort;
     int ready;
     int y_ready, published, parts_ready, done;  // chain-block progress counters
-    unsigned long long mb_all;                  // compute-warp barrier (6 arrivals)
-    unsigned long long mb_pair[3];              // band warp-pair barriers (2 arrivals)
+    int seg_m[XDF_NSEG], seg_c0[XDF_NSEG], seg_c1[XDF_NSEG];  // phase-1 segments (m < 0: none)
+    int red_idx[4][6], red_n[4];                // phase-2 sums: partial slots of warps 0-3
+    unsigned long long mb_set[XDF_NSETS];       // tile-set arrival (bulk copies)
 };
 
-// Barrier for a subset of the warps of a block, on a shared-memory mbarrier:
-// each warp reconverges, one lane arrives for it, and every lane waits for
-// the phase to complete (bounded; a timeout records the error and raises the
-// block's abort word).  `phase` is the warp's local count of completed uses.
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void mbar_init(unsigned long long* mb, int count)
@@ -572,31 +552,44 @@ __device__ __forceinline__ void mbar_init(unsigned long long* mb, int count)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mb)), "r"(count) : "memory");
 }
 
-__device__ __forceinline__ bool mbar_sync(unsigned long long* mb, unsigned& phase, int lane, int limit, int* err,
-                                          int* abort_word, int code)
+__device__ __forceinline__ bool mbar_test(unsigned long long* mb, unsigned parity)
 {
-    __syncwarp();
-    if (lane == 0)
-        asm volatile("{ .reg .b64 st; mbarrier.arrive.shared::cta.b64 st, [%0]; }" ::"r"(smem_u32(mb)) : "memory");
-    bool ok = false;
+    unsigned done;
+    asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                 : "=r"(done)
+                 : "r"(smem_u32(mb)), "r"(parity & 1)
+                 : "memory");
+    return done != 0;
+}
+
+// Bounded wait for the completion of phase `parity` of a transaction
+// barrier; gives up early once the block has aborted (unless `drain`, used
+// to let every bulk copy land before the block exits).
+__device__ __forceinline__ bool mbar_wait(unsigned long long* mb, unsigned parity, int limit, int* err, int* abort_word,
+                                          int code, bool drain)
+{
     for (int it = 0; it < limit; ++it) {
-        unsigned done;
-        asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-                     : "=r"(done)
-                     : "r"(smem_u32(mb)), "r"(phase & 1)
-                     : "memory");
-        if (done) {
-            ok = true;
-            break;
-        }
+        if (mbar_test(mb, parity)) return true;
+        if (!drain && (it & 63) == 63 && *(volatile int*)abort_word) return false;
     }
-    phase += 1;
-    if (!ok && lane == 0) {
-        atomicCAS(err, 0, (PIMD_DEVERR_TIMEOUT << 24) | (code & 0xFFFFFF));
-        *(volatile int*)abort_word = 1;
-    }
-    __syncwarp();
-    return ok;
+    atomicCAS(err, 0, (PIMD_DEVERR_TIMEOUT << 24) | (code & 0xFFFFFF));
+    *(volatile int*)abort_word = 1;
+    return false;
+}
+
+// Bulk (TMA, non-tensor) copy global -> shared, completing on an mbarrier.
+// Both addresses 16-byte aligned, size a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* mb)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(mb))
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* mb, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mb)), "r"(bytes) : "memory");
 }
 
 __device__ __forceinline__ dfw cget(const float (*h)[32], const float (*l)[32], const int (*e)[32], int i, int j)
@@ -608,32 +601,6 @@ __device__ __forceinline__ void cput(float (*h)[32], float (*l)[32], int (*e)[32
     h[i][j] = x.h;
     l[i][j] = x.l;
     e[i][j] = x.e;
-}
-
-// Tiles of iteration `it` by threads [0, nthr): forward T[0] = Q_J (G_0 first),
-// T[1] = G_{J+1}, T[m] = M_{J+m,J}; backward T[0] = P_J (G_J first),
-// T[1] = G_{J-1}, T[m] = M_{J,J-m}.
-template <int DIR>
-__device__ __forceinline__ void fetch_set_c(const XView& v, DfwTile* T, int it, int tid, int nthr)
-{
-    const int J = DIR == 0 ? it : v.nb - 1 - it;
-    const size_t o = (size_t)J * 1024;
-    if (it == 0) tile_copy(&T[0], v.Gh + o, v.Gl + o, v.Ge + o, tid, nthr);
-    else if (DIR == 0) tile_copy(&T[0], v.Qh + o, v.Ql + o, v.Qe + o, tid, nthr);
-    else tile_copy(&T[0], v.Ph + o, v.Pl + o, v.Pe + o, tid, nthr);
-    const int Jn = DIR == 0 ? J + 1 : J - 1;
-    if (Jn >= 0 && Jn < v.nb) {
-        const size_t on = (size_t)Jn * 1024;
-        tile_copy(&T[1], v.Gh + on, v.Gl + on, v.Ge + on, tid, nthr);
-    }
-    for (int m = 2; m < v.W; ++m) {
-        const int Ja = DIR == 0 ? J + m : J, Ia = DIR == 0 ? J : J - m;
-        if (DIR == 0 ? Ja < v.nb : Ia >= 0) {
-            const long long t = xdf_tile_index(v, Ja, Ia);
-            tile_copy(&T[m], v.Mh + t * 1024, v.Ml + t * 1024, v.Me + t * 1024, tid, nthr);
-        }
-    }
-    cp_commit();
 }
 
 // Shared-memory progress counters between the roles of a chain block.
@@ -665,20 +632,103 @@ __device__ __forceinline__ int chain_nparts(const XView& v, int B)
     return DIR == 0 ? min(v.S, B - v.W + 1) : min(v.S, v.nb - B - v.W);
 }
 
-// One chain block per direction.  Warps 0-5 compute; warp 6 fetches helper
-// partials ahead of need; warp 7 publishes each solution block (values,
-// weight products, release flag).  Compute iteration `it` (block J):
-//   A: warps 0-3 critical partials of Q_J y_{J-1} (forward) / P_J^T c_{J+1}
-//      (backward); warps 4-5 partials of G h (or G^T h) for the next block
-//   B: warp 0 forms the block's solution; warp 4 forms the next G h;
-//      warp 5 clears the consumed ring slots
-//   C: warp pairs add the band tiles into the ring (W-2 tiles)
-// The next iteration's tiles are copied during the current one.
+// Tile m of iteration it (block J):
+//   m = 0  Q_J (forward) / P_J (backward), times the previous solution block;
+//   m = 1  G_J, times s_J = h_J + p_J;
+//   m >= 2 band tile M_{J-1+m, J-1} (forward) / M_{J+1, J+1-m} (backward), times
+//          the previous solution block, added into h of block J-1+m / J+1-m.
+template <int DIR>
+__device__ __forceinline__ bool chain_tile_on(const XView& v, int it, int m)
+{
+    if (m == 1) return true;
+    if (it == 0) return false;
+    if (m == 0) return true;
+    const int J = chain_block<DIR>(v, it);
+    return DIR == 0 ? J - 1 + m < v.nb : J + 1 - m >= 0;
+}
+
+// Phase-1 work split: the W tiles of an iteration are cut into 4W units of 8
+// columns (rows), dealt in tile order to compute warps 0,4,1,5,2,3 in shares
+// W/2, W-W/2, W/2, W-W/2, W, W, so that each of the four SM sub-partitions
+// (warps w and w+4 share sub-partition w mod 4; warps 6 and 7 mostly wait)
+// issues W units.  A share of at most 5 units spans at most two tiles.
+__device__ __forceinline__ void chain_segments(int W, int* seg_m, int* seg_c0, int* seg_c1)
+{
+    const int order[6] = {0, 4, 1, 5, 2, 3};
+    int u0 = 0;
+    for (int k = 0; k < XDF_NSEG; ++k) seg_m[k] = -1;
+    for (int q = 0; q < 6; ++q) {
+        const int w = order[q];
+        const int cnt = (q < 4) ? ((q & 1) ? W - W / 2 : W / 2) : W;
+        const int u1 = u0 + cnt;
+        int j = 0;
+        for (int m = u0 >> 2; 4 * m < u1 && j < 2; ++m) {
+            const int a = max(u0, 4 * m), b = min(u1, 4 * m + 4);
+            if (a < b) {
+                seg_m[2 * w + j] = m;
+                seg_c0[2 * w + j] = 8 * (a - 4 * m);
+                seg_c1[2 * w + j] = 8 * (b - 4 * m);
+                ++j;
+            }
+        }
+        u0 = u1;
+    }
+}
+
+// Global source of tile m of iteration it (null if the tile is absent).
+template <int DIR>
+__device__ __forceinline__ const XTile* chain_tile_src(const XView& v, int it, int m)
+{
+    if (!chain_tile_on<DIR>(v, it, m)) return nullptr;
+    const int J = chain_block<DIR>(v, it);
+    if (m == 0) return (DIR == 0 ? v.Q : v.P) + J;
+    if (m == 1) return v.G + J;
+    return v.M + (DIR == 0 ? xdf_tile_index(v, J - 1 + m, J - 1) : xdf_tile_index(v, J + 1, J + 1 - m));
+}
+
+// Issue the bulk copies of the tile set of iteration `it` into its ring slot
+// (one thread, one 12 KB copy per tile).
+template <int DIR>
+__device__ void chain_issue_set(const XView& v, DfwTile* Tall, ChainS* cs, int it, int NS)
+{
+    const int slot = it % NS;
+    DfwTile* T = Tall + slot * v.W;
+    unsigned n = 0;
+    for (int m = 0; m < v.W; ++m) n += chain_tile_on<DIR>(v, it, m) ? 1u : 0u;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(&cs->mb_set[slot], n * (unsigned)sizeof(XTile));
+    for (int m = 0; m < v.W; ++m) {
+        const XTile* src = chain_tile_src<DIR>(v, it, m);
+        if (src) bulk_g2s(&T[m], src, (unsigned)sizeof(XTile), &cs->mb_set[slot]);
+    }
+}
+
+// Barrier of the six compute warps of a chain block (named barrier 1).
+// bar.sync is warp-aligned, so each warp reconverges first.
+__device__ __forceinline__ void compute_sync()
+{
+    __syncwarp();
+    asm volatile("bar.sync 1, 192;" ::: "memory");
+}
+
+// One chain block per direction.  Warps 0-5 compute in two phases per
+// iteration `it` (block J), separated by a barrier on those six warps:
+//   1: every tile of the iteration's set times its vector (the previous
+//      solution block, or s_J for G_J), split into segments (chain_segments);
+//   2: warp 0 sums the partials of Q_J y_{J-1} (P_J^T c_{J+1}) and G_J s_J into
+//      the solution block; warp 1 forms s of the next block from its band
+//      sum, the new band partials and the helper partials; warps 2-3 add band
+//      partials into the other band accumulators; warp 5 issues the bulk copy
+//      of a later tile set into the slot just consumed.
+// Only phase 2 of warp 0 and phase 1 of the Q (P) segments lie on the
+// dependent chain; the G s and band products for later blocks ride along.
+// Warp 6 fetches helper partials ahead of need; warp 7 publishes each
+// solution block (values, weight products, release flag).
 template <int DIR>
 __device__ void xchain(const XView& v, DfwTile* Tall, ChainS* cs)
 {
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const int W = v.W, nb = v.nb;
+    const int W = v.W, nb = v.nb, NS = XDF_TILES / W;
     ChainArrays& C = cs->u.c;
     int* flag_chain = v.flags + DIR * nb;
     const int* flag_part = v.flags + 2 * nb + DIR * nb * v.S;
@@ -689,49 +739,70 @@ __device__ void xchain(const XView& v, DfwTile* Tall, ChainS* cs)
         cs->published = -1;
         cs->parts_ready = 0;
         cs->done = -1;
-        mbar_init(&cs->mb_all, 6);
-        for (int q = 0; q < 3; ++q) mbar_init(&cs->mb_pair[q], 2);
+        chain_segments(W, cs->seg_m, cs->seg_c0, cs->seg_c1);
+        // warp 0 sums tiles 0-1 (its block), warp r = 1..3 tile r+1 (band)
+        for (int r = 0; r < 4; ++r) {
+            const int mlo = r == 0 ? 0 : r + 1, mhi = r + 1;
+            int n = 0;
+            for (int k = 0; k < XDF_NSEG; ++k)
+                if (cs->seg_m[k] >= mlo && cs->seg_m[k] <= mhi && n < 6) cs->red_idx[r][n++] = k;
+            cs->red_n[r] = n;
+        }
+        for (int q = 0; q < NS; ++q) mbar_init(&cs->mb_set[q], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (tid < 32) {
         for (int m = 0; m < W; ++m) {
             cput(C.hh, C.hl, C.he, m, tid, dfw_zero());
             cput(C.ph, C.pl, C.pe, m, tid, dfw_zero());
         }
-        cput(C.ghh, C.ghl, C.ghe, 0, tid, dfw_zero());
-        cput(C.ghh, C.ghl, C.ghe, 1, tid, dfw_zero());
+        C.xv[XDF_XR][tid] = dfw_pack(dfw_zero());
     }
     block_sync();
 
     if (w == XDF_WARPS - 1) {
-        // ---- publisher
+        // ---- publisher.  The endpoint coordinates of the next block are
+        // loaded while the current one is awaited.
+        df e[3];
+        auto load_e = [&](int it) {
+            const int n = 32 * chain_block<DIR>(v, it) + lane;
+            for (int c = 0; c < 3; ++c) {
+                e[c] = df{0.f, 0.f};
+                if (c >= v.d) continue;
+                if (DIR == 0) e[c] = df{v.bh[(size_t)c * v.npad + n], v.bl[(size_t)c * v.npad + n]};
+                else if (n >= 1 && n <= v.N) e[c] = df{v.ah[(size_t)c * v.npad + n - 1], v.al[(size_t)c * v.npad + n - 1]};
+            }
+        };
+        load_e(0);
         for (int it = 0; it < nb; ++it) {
             if (!smem_wait_ge(&cs->y_ready, it, cs, lim, v.err, 0x560000 + it)) break;
-            const int J = chain_block<DIR>(v, it), xb = it & 1, n = 32 * J + lane;
-            const df xm = df{C.xh[xb][lane], C.xl[xb][lane]};
+            const int J = chain_block<DIR>(v, it), xs = it % XDF_XR, n = 32 * J + lane;
+            const dfw xw = dfw_unpack(C.xv[xs][lane]);
+            const df xm = df{xw.h, xw.l};
             (DIR == 0 ? v.yh : v.ch)[n] = xm.h;
             (DIR == 0 ? v.yl : v.cl)[n] = xm.l;
-            (DIR == 0 ? v.ye : v.ce)[n] = C.xe[xb][lane];
+            (DIR == 0 ? v.ye : v.ce)[n] = xw.e;
             for (int c = 0; c < v.d; ++c) {
-                df u = df{0.f, 0.f};
-                if (DIR == 0) u = df_mul(xm, df{v.bh[(size_t)c * v.npad + n], v.bl[(size_t)c * v.npad + n]});
-                else if (n >= 1 && n <= v.N) u = df_mul(xm, df{v.ah[(size_t)c * v.npad + n - 1], v.al[(size_t)c * v.npad + n - 1]});
+                const df u = df_mul(xm, e[c]);
                 (DIR == 0 ? v.uh : v.wh)[(size_t)c * v.npad + n] = u.h;
                 (DIR == 0 ? v.ul : v.wl)[(size_t)c * v.npad + n] = u.l;
             }
-            __threadfence();
+            asm volatile("fence.acq_rel.gpu;" ::: "memory");
             __syncwarp();
             if (lane == 0) {
                 st_release(&flag_chain[J], 1);
                 vstore(&cs->published, it);
             }
             __syncwarp();
+            if (it + 1 < nb) load_e(it + 1);
         }
         return;
     }
     if (w == XDF_WARPS - 2) {
-        // ---- helper-partial fetcher: the block of iteration it is needed for
-        // the G h formed in iteration it-1; its ring slot is free once
-        // iteration it-W-1 has finished.
+        // ---- helper-partial fetcher: the partials of the block of iteration
+        // it are consumed in phase 2 of iteration it-1; its ring slot is free
+        // once iteration it-W-1 has finished.
         for (int it = 1; it < nb; ++it) {
             const int B = chain_block<DIR>(v, it), ns = chain_nparts<DIR>(v, B);
             if (ns > 0) {
@@ -744,12 +815,15 @@ __device__ void xchain(const XView& v, DfwTile* Tall, ChainS* cs)
                     break;
                 }
                 dfw t[8];
-                for (int s = 0; s < ns; ++s) {
-                    const size_t idx = xpart_index(v, DIR, B, s, lane);
-                    t[s] = dfw{__ldcg(&v.parth[idx * 4]), __ldcg(&v.partl[idx * 4]), __ldcg(&v.parte[idx])};
+#pragma unroll
+                for (int s = 0; s < 8; ++s) {
+                    t[s] = dfw_zero();
+                    if (s < ns) {
+                        const size_t idx = xpart_index(v, DIR, B, s, lane);
+                        t[s] = dfw_norm(df{__ldcg(&v.parth[idx * 4]), __ldcg(&v.partl[idx * 4])}, __ldcg(&v.parte[idx]));
+                    }
                 }
-                for (int s = 0; s < ns; ++s) t[s] = dfw_norm(df{t[s].h, t[s].l}, t[s].e);
-                cput(C.ph, C.pl, C.pe, B % W, lane, dfw_sum(t, ns));
+                cput(C.ph, C.pl, C.pe, B % W, lane, dfw_sum8(t, ns));
             }
             __threadfence_block();
             __syncwarp();
@@ -758,100 +832,109 @@ __device__ void xchain(const XView& v, DfwTile* Tall, ChainS* cs)
         }
         return;
     }
-    // ---- compute warps 0-5 (192 threads, named barrier 1; pairs use 2-4).
-    // They never leave the loop early: after a failed wait (error recorded,
-    // abort raised) they run to the end without waiting, so every named
-    // barrier is met by all six warps.
-    const int NCT = 6 * 32;
-    unsigned ph_all = 0, ph_pair = 0;
-    auto sync_all = [&](int code) { mbar_sync(&cs->mb_all, ph_all, lane, lim, v.err, &cs->abort, code); };
-    fetch_set_c<DIR>(v, Tall, 0, tid, NCT);
-    cp_wait<0>();
-    sync_all(0x5a0000);
+    // ---- compute warps 0-5.  They never leave the loop early: after a
+    // failed wait (error recorded, abort raised) they run to the end with
+    // every further wait cut short, so the block always finishes.
+    int issued = -1;  // warp 5, lane 0: last tile set issued
+    if (w == 5 && lane == 0) {
+        for (int i = 0; i < min(NS, nb); ++i) chain_issue_set<DIR>(v, Tall, cs, i, NS);
+        issued = min(NS, nb) - 1;
+    }
+    int sm[2], sc0[2], sc1[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        sm[j] = cs->seg_m[2 * w + j];
+        sc0[j] = cs->seg_c0[2 * w + j];
+        sc1[j] = cs->seg_c1[2 * w + j];
+    }
+    // phase-2 sums: partial slots of this warp's tiles
+    int ridx[6], rn = 0;
+    if (w <= 3) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) ridx[i] = cs->red_idx[w][i];
+        rn = cs->red_n[w];
+    }
     for (int it = 0; it < nb; ++it) {
-        const int J = chain_block<DIR>(v, it);
-        DfwTile* T = Tall + (it & 1) * W;
+        const int J = chain_block<DIR>(v, it), slot = it % NS;
+        DfwTile* T = Tall + slot * W;
         const bool more = it + 1 < nb;
-        const int Jn1 = more ? chain_block<DIR>(v, it + 1) : 0;
-        if (more) fetch_set_c<DIR>(v, Tall + ((it + 1) & 1) * W, it + 1, tid, NCT);
-        const int xb = it & 1, pb = xb ^ 1;
-        bool ok = true;
-        // phase A
-        if (w < 4) {
-            if (it >= 1) {
-                const dfw p = DIR == 0 ? dot_row_vec(&T[0], lane, C.xh[pb], C.xl[pb], C.xe[pb], 8 * w, 8 * w + 8)
-                                       : dot_col_vec(&T[0], lane, C.xh[pb], C.xl[pb], C.xe[pb], 8 * w, 8 * w + 8);
-                cput(C.rh, C.rl, C.re, w, lane, p);
-            }
-        } else if (more) {
-            ok = smem_wait_ge(&cs->parts_ready, it + 1, cs, lim, v.err, 0x580000 + it);
-            const int k = w - 4, s1 = Jn1 % W;
-            dfw p = dfw_zero();
-            if (ok) {
-                if (DIR == 0) {
-                    const int t0 = 16 * k, t1 = min(16 * k + 16, lane + 1);
-                    if (t0 < t1) p = dot_row_vec2(&T[1], lane, C.hh[s1], C.hl[s1], C.he[s1], C.ph[s1], C.pl[s1], C.pe[s1], t0, t1);
-                } else {
-                    const int t0 = max(16 * k, lane), t1 = 16 * k + 16;
-                    if (t0 < t1) p = dot_col_vec2(&T[1], lane, C.hh[s1], C.hl[s1], C.he[s1], C.ph[s1], C.pl[s1], C.pe[s1], t0, t1);
+        mbar_wait(&cs->mb_set[slot], (unsigned)(it / NS), lim, v.err, &cs->abort, 0x5f0000 + it, false);
+        // phase 1 (at it = 0 only warp 0 reads its block from G, before warp 5
+        // may overwrite the slot in phase 2)
+        dfw x0 = dfw_zero();
+        if (it == 0 && w == 0) x0 = DIR == 0 ? tile_get(&T[1], lane, 0) : tile_get(&T[1], v.N - 32 * J, lane);
+        if (it >= 1) {
+            const int xp = (it - 1) % XDF_XR;
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int m = sm[j];
+                if (m < 0) continue;
+                dfw p = dfw_zero();
+                if (chain_tile_on<DIR>(v, it, m)) {
+                    const float4* xv = C.xv[m == 1 ? XDF_XR : xp];
+                    p = DIR == 0 ? dot_seg<false>(&T[m], lane, xv, sc0[j], sc1[j])
+                                 : dot_seg<true>(&T[m], lane, xv, sc0[j], sc1[j]);
                 }
+                C.r[2 * w + j][lane] = dfw_pack(p);
             }
-            cput(C.rh, C.rl, C.re, w, lane, p);
         }
-        (void)ok;
-        sync_all(0x5b0000 + it);
-        // phase B
+        compute_sync();
+        // phase 2
         if (w == 0) {
-            // the slot x[xb] was last published two iterations ago
-            ok = smem_wait_ge(&cs->published, it - 2, cs, lim, v.err, 0x590000 + it);
-            dfw x;
-            if (it == 0) {
-                x = DIR == 0 ? tile_get(&T[0], lane, 0) : tile_get(&T[0], v.N - 32 * J, lane);
-            } else {
-                dfw t[5] = {cget(C.ghh, C.ghl, C.ghe, xb, lane), cget(C.rh, C.rl, C.re, 0, lane), cget(C.rh, C.rl, C.re, 1, lane),
-                            cget(C.rh, C.rl, C.re, 2, lane), cget(C.rh, C.rl, C.re, 3, lane)};
-                x = dfw_sum(t, 5);
+            // ring slot it % XDF_XR was last published XDF_XR iterations ago
+            smem_wait_ge(&cs->published, it - XDF_XR, cs, lim, v.err, 0x590000 + it);
+            dfw x = x0;
+            if (it >= 1) {
+                dfw t[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) t[i] = i < rn ? dfw_unpack(C.r[ridx[i < 6 ? i : 0]][lane]) : dfw_zero();
+                x = dfw_sum8(t, rn);
             }
-            cput(C.xh, C.xl, C.xe, xb, lane, x);
+            C.xv[it % XDF_XR][lane] = dfw_pack(x);
             __threadfence_block();
             __syncwarp();
             if (lane == 0) vstore(&cs->y_ready, it);
             __syncwarp();
-        } else if (w == 4 && more) {
-            dfw t[2] = {cget(C.rh, C.rl, C.re, 4, lane), cget(C.rh, C.rl, C.re, 5, lane)};
-            cput(C.ghh, C.ghl, C.ghe, pb, lane, dfw_sum(t, 2));
-        } else if (w == 5 && more) {
-            const int s1 = Jn1 % W;
-            cput(C.hh, C.hl, C.he, s1, lane, dfw_zero());
-            cput(C.ph, C.pl, C.pe, s1, lane, dfw_zero());
-        }
-        sync_all(0x5c0000 + it);
-        // phase C: band tiles (pairs of warps, one half of the columns each)
-        if (w < 2 * (W - 2)) {
-            const int m = 2 + (w >> 1), half = w & 1;
-            const int Jt = DIR == 0 ? J + m : J - m;
-            const bool on = DIR == 0 ? Jt < nb : Jt >= 0;
-            if (on) {
-                const dfw p = DIR == 0 ? dot_row_vec(&T[m], lane, C.xh[xb], C.xl[xb], C.xe[xb], 16 * half, 16 * half + 16)
-                                       : dot_col_vec(&T[m], lane, C.xh[xb], C.xl[xb], C.xe[xb], 16 * half, 16 * half + 16);
-                cput(C.rh, C.rl, C.re, w, lane, p);
+        } else if (w == 1) {
+            if (more && smem_wait_ge(&cs->parts_ready, it + 1, cs, lim, v.err, 0x580000 + it)) {
+                const int sl = chain_block<DIR>(v, it + 1) % W;
+                const int np = it >= 1 ? rn : 0;
+                dfw t[8];
+                t[0] = cget(C.hh, C.hl, C.he, sl, lane);
+                t[1] = cget(C.ph, C.pl, C.pe, sl, lane);
+#pragma unroll
+                for (int i = 0; i < 6; ++i) t[2 + i] = i < np ? dfw_unpack(C.r[ridx[i]][lane]) : dfw_zero();
+                C.xv[XDF_XR][lane] = dfw_pack(dfw_sum8(t, 2 + np));
+                cput(C.hh, C.hl, C.he, sl, lane, dfw_zero());
+                cput(C.ph, C.pl, C.pe, sl, lane, dfw_zero());
             }
-            mbar_sync(&cs->mb_pair[w >> 1], ph_pair, lane, lim, v.err, &cs->abort, 0x5d0000 + it);
-            if (on && half == 0) {
-                const int sl = Jt % W;
-                dfw t[3] = {cget(C.hh, C.hl, C.he, sl, lane), cget(C.rh, C.rl, C.re, w, lane), cget(C.rh, C.rl, C.re, w + 1, lane)};
-                cput(C.hh, C.hl, C.he, sl, lane, dfw_sum(t, 3));
+        } else if (w <= 3) {
+            const int m = w + 1;
+            if (m < W && it >= 1 && chain_tile_on<DIR>(v, it, m)) {
+                const int sl = (DIR == 0 ? J - 1 + m : J + 1 - m) % W;
+                dfw t[8];
+                t[0] = cget(C.hh, C.hl, C.he, sl, lane);
+#pragma unroll
+                for (int i = 0; i < 7; ++i) t[1 + i] = i < rn ? dfw_unpack(C.r[ridx[i < 6 ? i : 0]][lane]) : dfw_zero();
+                cput(C.hh, C.hl, C.he, sl, lane, dfw_sum8(t, 1 + rn));
             }
+        } else if (w == 5 && lane == 0 && it + NS < nb && !vload(&cs->abort)) {
+            chain_issue_set<DIR>(v, Tall, cs, it + NS, NS);
+            issued = it + NS;
         }
-        if (more) cp_wait<0>();
-        sync_all(0x5e0000 + it);
+        compute_sync();
         if (tid == 0) {
             __threadfence_block();
             vstore(&cs->done, it);
         }
         __syncwarp();
     }
-    cp_wait<0>();
+    // every issued bulk copy lands before the block's shared memory is released
+    if (w == 5 && lane == 0)
+        for (int s = 0; s < NS && s <= issued; ++s) {
+            const int last = s + ((issued - s) / NS) * NS;
+            mbar_wait(&cs->mb_set[s], (unsigned)(last / NS), lim, v.err, &cs->abort, 0x5f8000 + s, true);
+        }
 }
 
 // Helper loop shared by both directions.  dir 0: items (B, s) = row block B,
@@ -890,7 +973,7 @@ __device__ void xhelper(const XView& v, DfwTile* T, WeightSmem* Ws, ChainS* cs, 
                 const int o0 = other(0);
                 if (tile_stored(v, tJ(o0), tI(o0))) {
                     const long long t = xdf_tile_index(v, tJ(o0), tI(o0));
-                    tile_copy(&T[0], v.Mh + t * 1024, v.Ml + t * 1024, v.Me + t * 1024, tid, XDF_THREADS);
+                    tile_copy(&T[0], v.M + t, tid, XDF_THREADS);
                 }
             }
             block_sync();
@@ -906,7 +989,7 @@ __device__ void xhelper(const XView& v, DfwTile* T, WeightSmem* Ws, ChainS* cs, 
                     const int on = other(k + 1);
                     if (tile_stored(v, tJ(on), tI(on))) {
                         const long long t = xdf_tile_index(v, tJ(on), tI(on));
-                        tile_copy(&T[cur ^ 1], v.Mh + t * 1024, v.Ml + t * 1024, v.Me + t * 1024, tid, XDF_THREADS);
+                        tile_copy(&T[cur ^ 1], v.M + t, tid, XDF_THREADS);
                     }
                     if (all_ready && w == 0) fetch_weights_warp(v, &Ws[cur ^ 1], DIR, on, lane);
                 }

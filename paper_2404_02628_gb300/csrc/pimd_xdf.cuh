@@ -32,6 +32,17 @@
 #define XDF_LD 33
 #define XDF_MAXW 5
 
+// A 32x32 dfw tile, in global and in shared memory alike: three contiguous
+// 4 KB runs (high parts, low parts, exponents), element (r, c) at
+// (r << 5) + ((c + r) & 31).  The rotation makes both row walks (lane = r)
+// and column walks (lane = c) hit 32 distinct shared-memory banks; the
+// contiguity lets one 12 KB bulk copy move a tile.
+struct XTile {
+    float h[1024];
+    float l[1024];
+    int e[1024];
+};
+
 struct XView {
     int N, nb, npad, d, S, W;
     int store;
@@ -45,10 +56,10 @@ struct XView {
     float* bh; float* bl;        // [3][npad] b_k in double-float
     float* crh; float* crl;      // [npad] row constants c_n
     const float2* tab;           // [256] 2^(j/256) as double-floats
-    float* Mh; float* Ml; int* Me;   // tiles [t][32 r][32 c]
-    float* Gh; float* Gl; int* Ge;   // [nb][1024]
-    float* Qh; float* Ql; int* Qe;   // [nb][1024]
-    float* Ph; float* Pl; int* Pe;   // [nb][1024]
+    XTile* M;                    // factor tiles, index xdf_tile_index
+    XTile* G;                    // [nb] (I - M_JJ)^{-1}
+    XTile* Q;                    // [nb] G_J M_{J,J-1}
+    XTile* P;                    // [nb] M_{J+1,J} G_J
     float* yh; float* yl; int* ye;   // [npad] forward solution y
     float* ch; float* cl; int* ce;   // [npad] backward solution c
     float* uh; float* ul;            // [3][npad] y[k] b_k (mantissa of y times b_k), published with y
