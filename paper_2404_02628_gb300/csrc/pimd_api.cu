@@ -499,6 +499,8 @@ extern "C" pimd_status pimd_bind(pimd_t c, const pimd_buffers* b, void* stream)
     c->mp.mass = c->cfg.mass;
     c->mp.kT = 1.0 / c->beta;
     c->mp.Q = c->cfg.nhc_Q > 0.0 ? c->cfg.nhc_Q : c->beta / c->P;
+    c->mp.inv_mass = 1.0 / c->mp.mass;
+    c->mp.inv_Q = 1.0 / c->mp.Q;
     c->mp.thermostat = c->cfg.thermostat;
     cudaError_t e;
     if (c->cfg.thermostat) {

@@ -116,45 +116,50 @@ __global__ void __launch_bounds__(PAIR_T) pair_kernel_f64(BeadView b, ForceParam
 
 // FP32 pair arithmetic with exp2 on the MUFU unit; coordinates pre-scaled by
 // sqrt(log2(e))/s so that each pair costs one ex2 and no extra multiply.
+// One thread per particle; partners are taken two at a time on the packed
+// FP32x2 pipe, the partner tile sitting in shared memory as negated
+// coordinate pairs {x_k, x_k+1} per component.
 template <int D>
 __global__ void __launch_bounds__(PAIR_T) pair_kernel_f32(BeadView b, ForceParams fp, double* f, double* part)
 {
-    __shared__ float sx[D][PAIR_T];
+    __shared__ float2 sx[D][PAIR_T / 2];
     __shared__ double red[64];
     const int i = blockIdx.x * PAIR_T + threadIdx.x, j = blockIdx.y;
     const double* rs = b.r + (size_t)j * D * b.ld;
     const float sc = (float)sqrt(fp.inv_s2 * 1.4426950408889634);
     double xd[D];
-    float xi[D], g[D];
+    float2 xi[D], g[D];
 #pragma unroll
     for (int c = 0; c < D; ++c) {
         xd[c] = (i < b.N) ? rs[(size_t)c * b.ld + i] : 0.0;
-        xi[c] = (float)xd[c] * sc;
-        g[c] = 0.0f;
+        const float xs = (float)xd[c] * sc;
+        xi[c] = make_float2(xs, xs);
+        g[c] = make_float2(0.f, 0.f);
     }
-    float esum = 0.0f;
+    float2 esum = make_float2(0.f, 0.f);
     if (fp.A != 0.0) {
         for (int k0 = 0; k0 < b.N; k0 += PAIR_T) {
             const int k = k0 + threadIdx.x;
+            float* sxf = reinterpret_cast<float*>(&sx[0][0]);
 #pragma unroll
-            for (int c = 0; c < D; ++c) sx[c][threadIdx.x] = (k < b.N) ? (float)rs[(size_t)c * b.ld + k] * sc : 1.0e18f;
+            for (int c = 0; c < D; ++c)
+                sxf[c * PAIR_T + threadIdx.x] = (k < b.N) ? -(float)rs[(size_t)c * b.ld + k] * sc : -1.0e18f;
             __syncthreads();
-#pragma unroll 8
-            for (int kk = 0; kk < PAIR_T; ++kk) {
-                float dx[D], nq = 0.0f;
+#pragma unroll 4
+            for (int kk = 0; kk < PAIR_T / 2; ++kk) {
+                float2 dx[D];
 #pragma unroll
-                for (int c = 0; c < D; ++c) {
-                    dx[c] = xi[c] - sx[c][kk];
-                    nq = fmaf(-dx[c], dx[c], nq);
-                }
-                const float ee = ex2_approx(nq);
-                esum += ee;
+                for (int c = 0; c < D; ++c) dx[c] = __fadd2_rn(xi[c], sx[c][kk]);
+                float2 q2 = __fmul2_rn(dx[0], dx[0]);
 #pragma unroll
-                for (int c = 0; c < D; ++c) g[c] = fmaf(ee, dx[c], g[c]);
+                for (int c = 1; c < D; ++c) q2 = __ffma2_rn(dx[c], dx[c], q2);
+                const float2 ee = make_float2(ex2_approx(-q2.x), ex2_approx(-q2.y));
+                esum = __fadd2_rn(esum, ee);
+#pragma unroll
+                for (int c = 0; c < D; ++c) g[c] = __ffma2_rn(ee, dx[c], g[c]);
             }
             __syncthreads();
         }
-        if (i < b.N) esum -= 1.0f;  // the k == i term contributed exp(0) = 1 and no force
     }
     double v[2] = {0.0, 0.0};
     if (i < b.N) {
@@ -162,14 +167,16 @@ __global__ void __launch_bounds__(PAIR_T) pair_kernel_f32(BeadView b, ForceParam
         double t2 = 0.0, vir = 0.0;
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-            const double grad = fp.omega2 * xd[c] + cpair * (double)g[c];
+            const double grad = fp.omega2 * xd[c] + cpair * ((double)g[c].x + (double)g[c].y);
             const size_t o = ((size_t)j * D + c) * b.ld + i;
             const double fo = -grad / b.P;
             f[o] = fp.accumulate ? f[o] + fo : fo;
             t2 = fma(xd[c], xd[c], t2);
             vir = fma(xd[c], grad, vir);
         }
-        v[0] = 0.5 * fp.omega2 * t2 + 0.5 * fp.A * (double)esum;
+        // the k == i term contributed exp(0) = 1 and no force
+        const double es = fp.A != 0.0 ? (double)esum.x + (double)esum.y - 1.0 : 0.0;
+        v[0] = 0.5 * fp.omega2 * t2 + 0.5 * fp.A * es;
         v[1] = vir;
     }
     block_reduce<2>(v, red);
@@ -186,30 +193,53 @@ __global__ void __launch_bounds__(PAIR_T) pair_kernel_f32(BeadView b, ForceParam
 // momentum scaled by exp(-tau p_1/Q), positions eta += tau p_eta/Q, then the
 // links again in the opposite order.
 
-__device__ __forceinline__ void nhc_half_step(double& p, double* eta, double* pe, int M, double m, double Q,
-                                              double kT, double tau)
+// e^x in FP64.  The thermostat scalings have |x| of order 1e-3, where the
+// Taylor polynomial of degree 8 (Horner form) truncates below (1/32)^9/9! <
+// 1e-19 relative; larger |x| use the library exp.
+__device__ __forceinline__ double exp_small(double x)
 {
-    double G = ((M >= 2) ? pe[M - 2] * pe[M - 2] / Q : p * p / m) - kT;
-    pe[M - 1] += 0.5 * tau * G;
-    for (int k = M - 2; k >= 0; --k) {
-        const double a = exp(-0.25 * tau * pe[k + 1] / Q);
-        G = ((k == 0) ? p * p / m : pe[k - 1] * pe[k - 1] / Q) - kT;
-        pe[k] = pe[k] * a * a + 0.5 * tau * G * a;
-    }
-    p *= exp(-tau * pe[0] / Q);
-    for (int k = 0; k < M; ++k) eta[k] += tau * pe[k] / Q;
-    for (int k = 0; k <= M - 2; ++k) {
-        const double a = exp(-0.25 * tau * pe[k + 1] / Q);
-        G = ((k == 0) ? p * p / m : pe[k - 1] * pe[k - 1] / Q) - kT;
-        pe[k] = pe[k] * a * a + 0.5 * tau * G * a;
-    }
-    G = ((M >= 2) ? pe[M - 2] * pe[M - 2] / Q : p * p / m) - kT;
-    pe[M - 1] += 0.5 * tau * G;
+    if (!(fabs(x) <= 0.03125)) return exp(x);
+    double s = 1.0 / 40320.0;
+    s = fma(s, x, 1.0 / 5040.0);
+    s = fma(s, x, 1.0 / 720.0);
+    s = fma(s, x, 1.0 / 120.0);
+    s = fma(s, x, 1.0 / 24.0);
+    s = fma(s, x, 1.0 / 6.0);
+    s = fma(s, x, 0.5);
+    s = fma(s, x, 1.0);
+    return fma(s, x, 1.0);
 }
 
-constexpr int MAX_M = 8;
+// One Trotter half step of length tau for the massive chains of one degree of
+// freedom; 1/m and 1/Q come precomputed.  M is a template argument so that
+// the chain stays in registers.
+template <int M>
+__device__ __forceinline__ void nhc_half_step(double& p, double (&eta)[M], double (&pe)[M], double inv_m, double inv_Q,
+                                              double kT, double tau)
+{
+    const double ca = -0.25 * tau * inv_Q, cg = 0.5 * tau, ce = tau * inv_Q;
+    double G = ((M >= 2) ? pe[M - 2] * pe[M - 2] * inv_Q : p * p * inv_m) - kT;
+    pe[M - 1] = fma(cg, G, pe[M - 1]);
+#pragma unroll
+    for (int k = M - 2; k >= 0; --k) {
+        const double a = exp_small(ca * pe[k + 1]);
+        G = ((k == 0) ? p * p * inv_m : pe[k - 1] * pe[k - 1] * inv_Q) - kT;
+        pe[k] = fma(pe[k], a * a, cg * G * a);
+    }
+    p *= exp_small(-tau * inv_Q * pe[0]);
+#pragma unroll
+    for (int k = 0; k < M; ++k) eta[k] = fma(ce, pe[k], eta[k]);
+#pragma unroll
+    for (int k = 0; k <= M - 2; ++k) {
+        const double a = exp_small(ca * pe[k + 1]);
+        G = ((k == 0) ? p * p * inv_m : pe[k - 1] * pe[k - 1] * inv_Q) - kT;
+        pe[k] = fma(pe[k], a * a, cg * G * a);
+    }
+    G = ((M >= 2) ? pe[M - 2] * pe[M - 2] * inv_Q : p * p * inv_m) - kT;
+    pe[M - 1] = fma(cg, G, pe[M - 1]);
+}
 
-template <bool PRE>
+template <bool PRE, int M>
 __global__ void __launch_bounds__(MD_T) md_kernel(BeadView b, MDParams mp)
 {
     const size_t stride = (size_t)b.P * b.d * b.ld;
@@ -217,24 +247,26 @@ __global__ void __launch_bounds__(MD_T) md_kernel(BeadView b, MDParams mp)
         const int l = (int)(o % b.ld);
         if (l >= b.N) continue;
         double p = b.p[o];
-        double eta[MAX_M], pe[MAX_M];
+        double eta[M], pe[M];
         if (mp.thermostat) {
-            for (int k = 0; k < b.M; ++k) {
+#pragma unroll
+            for (int k = 0; k < M; ++k) {
                 eta[k] = b.eta[k * stride + o];
                 pe[k] = b.peta[k * stride + o];
             }
         }
         if (PRE) {
-            if (mp.thermostat) nhc_half_step(p, eta, pe, b.M, mp.mass, mp.Q, mp.kT, 0.5 * mp.dt);
+            if (mp.thermostat) nhc_half_step<M>(p, eta, pe, mp.inv_mass, mp.inv_Q, mp.kT, 0.5 * mp.dt);
             p += 0.5 * mp.dt * b.f[o];
-            b.r[o] += mp.dt * p / mp.mass;
+            b.r[o] = fma(mp.dt * mp.inv_mass, p, b.r[o]);
         } else {
             p += 0.5 * mp.dt * b.f[o];
-            if (mp.thermostat) nhc_half_step(p, eta, pe, b.M, mp.mass, mp.Q, mp.kT, 0.5 * mp.dt);
+            if (mp.thermostat) nhc_half_step<M>(p, eta, pe, mp.inv_mass, mp.inv_Q, mp.kT, 0.5 * mp.dt);
         }
         b.p[o] = p;
         if (mp.thermostat) {
-            for (int k = 0; k < b.M; ++k) {
+#pragma unroll
+            for (int k = 0; k < M; ++k) {
                 b.eta[k * stride + o] = eta[k];
                 b.peta[k * stride + o] = pe[k];
             }
@@ -341,17 +373,27 @@ cudaError_t launch_pair(const BeadView& b, const ForceParams& fp, double* f_out,
     return cudaGetLastError();
 }
 
-cudaError_t launch_md_pre(const BeadView& b, const MDParams& mp, cudaStream_t st)
+template <bool PRE>
+static cudaError_t launch_md(const BeadView& b, const MDParams& mp, cudaStream_t st)
 {
-    md_kernel<true><<<md_blocks(b.N, b.P, b.d), MD_T, 0, st>>>(b, mp);
+    const int g = md_blocks(b.N, b.P, b.d);
+    switch (b.M) {
+    case 1: md_kernel<PRE, 1><<<g, MD_T, 0, st>>>(b, mp); break;
+    case 2: md_kernel<PRE, 2><<<g, MD_T, 0, st>>>(b, mp); break;
+    case 3: md_kernel<PRE, 3><<<g, MD_T, 0, st>>>(b, mp); break;
+    case 4: md_kernel<PRE, 4><<<g, MD_T, 0, st>>>(b, mp); break;
+    case 5: md_kernel<PRE, 5><<<g, MD_T, 0, st>>>(b, mp); break;
+    case 6: md_kernel<PRE, 6><<<g, MD_T, 0, st>>>(b, mp); break;
+    case 7: md_kernel<PRE, 7><<<g, MD_T, 0, st>>>(b, mp); break;
+    case 8: md_kernel<PRE, 8><<<g, MD_T, 0, st>>>(b, mp); break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
-cudaError_t launch_md_post(const BeadView& b, const MDParams& mp, cudaStream_t st)
-{
-    md_kernel<false><<<md_blocks(b.N, b.P, b.d), MD_T, 0, st>>>(b, mp);
-    return cudaGetLastError();
-}
+cudaError_t launch_md_pre(const BeadView& b, const MDParams& mp, cudaStream_t st) { return launch_md<true>(b, mp, st); }
+
+cudaError_t launch_md_post(const BeadView& b, const MDParams& mp, cudaStream_t st) { return launch_md<false>(b, mp, st); }
 
 cudaError_t launch_md_energy(const BeadView& b, const MDParams& mp, double* part, cudaStream_t st)
 {

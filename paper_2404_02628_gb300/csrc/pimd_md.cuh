@@ -24,6 +24,7 @@ struct ForceParams {
 
 struct MDParams {
     double dt, mass, Q, kT;
+    double inv_mass, inv_Q;   // 1/mass and 1/Q, formed on the host
     int thermostat;
 };
 
