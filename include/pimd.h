@@ -187,6 +187,57 @@ const char* pimd_last_error(pimd_t ctx);
 const char* pimd_global_error(void);
 void pimd_destroy(pimd_t ctx);
 
+/* ---- batched replicas ----------------------------------------------------- */
+/*
+ * R independent systems of uneven particle number N_r <= 2047, inverse
+ * temperature beta_r and exchange parameter xi_r (for instance the xi and
+ * temperature scans of Sec. II's fictitious-particle method), sharing P, d,
+ * omega, g, s and one pimd_config.  Each step runs every replica with one
+ * launch per kernel (the exchange recursion one block per replica and
+ * direction, no cross-block waits), replayed as one CUDA graph.
+ * table_mode, exchange_arith, exch_band and helper_ctas are ignored: the
+ * batch always stores the factor table and uses the double-float recursion.
+ * nhc_Q <= 0 selects beta_r/P per replica.
+ */
+typedef struct pimd_batch* pimd_batch_t;
+
+typedef struct {
+    double* r;          /* device: replica r's [P][d][n_pad_r] block starts at element
+                           offsets[r] (pimd_batch_layout), n_pad_r = N_r rounded up to 32 */
+    double* p;          /* device, momenta, same layout                                      */
+    double* f;          /* device, forces, same layout (written here)                        */
+    double* eta;        /* device, thermostat positions: replica r's [M][P][d][n_pad_r]
+                           block at M * offsets[r]                                           */
+    double* peta;       /* device, thermostat momenta, same layout as eta                    */
+    void* work;         /* device workspace, 256-byte aligned                                */
+    size_t work_bytes;  /* its size, at least pimd_batch_workspace_bytes()                   */
+} pimd_batch_buffers;
+
+/* N, beta, xi: host arrays of R entries (N_r in [1, 2047], beta_r > 0,
+ * xi_r in [0,1]).  Host only. */
+pimd_status pimd_batch_create(int R, const int* N, int P, int d, const double* beta, const double* xi,
+                              double omega, double g, double s, pimd_batch_t* out);
+pimd_status pimd_batch_configure(pimd_batch_t b, const pimd_config* cfg);
+/* offsets: host array of R + 1 entries; offsets[R] = total elements per bead array. */
+pimd_status pimd_batch_layout(pimd_batch_t b, size_t* offsets);
+pimd_status pimd_batch_workspace_bytes(pimd_batch_t b, size_t* bytes);
+/* As pimd_bind: zeroes the thermostats and the step counter and computes the
+ * forces of r; r and p must hold the initial state. */
+pimd_status pimd_batch_bind(pimd_batch_t b, const pimd_batch_buffers* bufs, void* stream);
+pimd_status pimd_batch_forces(pimd_batch_t b);
+/* Captures one batched step as a CUDA graph on a private stream (done by the
+ * first pimd_batch_step otherwise). */
+pimd_status pimd_batch_capture_graph(pimd_batch_t b);
+pimd_status pimd_batch_step(pimd_batch_t b, int nsteps);
+pimd_status pimd_batch_step_eager(pimd_batch_t b, int nsteps);
+pimd_status pimd_batch_step_profiled(pimd_batch_t b, int nsteps, double* ms_out, int max_slots, int* n_slots);
+const char* pimd_batch_profile_slot_name(pimd_batch_t b, int slot);
+/* out: host array of R estimates (synchronises). */
+pimd_status pimd_batch_estimators(pimd_batch_t b, pimd_estimates* out);
+pimd_status pimd_batch_sync(pimd_batch_t b);
+const char* pimd_batch_last_error(pimd_batch_t b);
+void pimd_batch_destroy(pimd_batch_t b);
+
 /* ---- exchange potential alone (for autograd) --------------------------- */
 /*
  * V_ends(r^1, r^P) = V_xi^[1,N] - sum_l E_int^(l): the part of the exchange

@@ -14,13 +14,17 @@ import os
 from . import build as _build
 
 __all__ = [
-    "PIMD_OK", "PimdError", "Config", "Buffers", "Estimates", "lib", "load", "symbols",
+    "PIMD_OK", "PimdError", "Config", "Buffers", "BatchBuffers", "Estimates", "lib", "load", "symbols", "Batch",
     "pimd_create", "pimd_default_config", "pimd_configure", "pimd_workspace_bytes", "pimd_bind",
     "pimd_forces", "pimd_exchange_forces", "pimd_interaction_forces", "pimd_step", "pimd_step_eager",
     "pimd_estimators", "pimd_state_bytes", "pimd_get_state", "pimd_set_state", "pimd_sync",
     "pimd_last_error", "pimd_global_error", "pimd_destroy", "pimd_vb_create", "pimd_vb_workspace_bytes",
     "pimd_vb_forward", "pimd_vb_backward", "pimd_vb_destroy", "pimd_step_profiled",
     "pimd_profile_slot_name", "pimd_vb_forward_noalloc", "System",
+    "pimd_batch_create", "pimd_batch_configure", "pimd_batch_layout", "pimd_batch_workspace_bytes",
+    "pimd_batch_bind", "pimd_batch_forces", "pimd_batch_capture_graph", "pimd_batch_step",
+    "pimd_batch_step_eager", "pimd_batch_step_profiled", "pimd_batch_profile_slot_name",
+    "pimd_batch_estimators", "pimd_batch_sync", "pimd_batch_last_error", "pimd_batch_destroy",
 ]
 
 PIMD_OK, PIMD_EINVAL, PIMD_ENOMEM, PIMD_ECUDA, PIMD_ETIMEOUT, PIMD_ENONFINITE, PIMD_ESTATE = range(7)
@@ -51,6 +55,12 @@ class Buffers(ctypes.Structure):
     _fields_ = [("r", ctypes.c_void_p), ("p", ctypes.c_void_p), ("f", ctypes.c_void_p),
                 ("eta", ctypes.c_void_p), ("peta", ctypes.c_void_p), ("work", ctypes.c_void_p),
                 ("work_bytes", ctypes.c_size_t), ("n_pad", ctypes.c_int)]
+
+
+class BatchBuffers(ctypes.Structure):
+    _fields_ = [("r", ctypes.c_void_p), ("p", ctypes.c_void_p), ("f", ctypes.c_void_p),
+                ("eta", ctypes.c_void_p), ("peta", ctypes.c_void_p), ("work", ctypes.c_void_p),
+                ("work_bytes", ctypes.c_size_t)]
 
 
 class Estimates(ctypes.Structure):
@@ -95,6 +105,22 @@ _SIGS = {
     "pimd_profile_slot_name": ([_vp, ctypes.c_int], ctypes.c_char_p),
     "pimd_vb_forward_noalloc": ([ctypes.c_int] * 3 + [ctypes.c_double] * 2 + [_vp, _vp, ctypes.c_int, _vp, _vp],
                                 ctypes.c_int),
+    "pimd_batch_create": ([ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int, _dp, _dp]
+                          + [ctypes.c_double] * 3 + [ctypes.POINTER(_vp)], ctypes.c_int),
+    "pimd_batch_configure": ([_vp, ctypes.POINTER(Config)], ctypes.c_int),
+    "pimd_batch_layout": ([_vp, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "pimd_batch_workspace_bytes": ([_vp, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "pimd_batch_bind": ([_vp, ctypes.POINTER(BatchBuffers), _vp], ctypes.c_int),
+    "pimd_batch_forces": ([_vp], ctypes.c_int),
+    "pimd_batch_capture_graph": ([_vp], ctypes.c_int),
+    "pimd_batch_step": ([_vp, ctypes.c_int], ctypes.c_int),
+    "pimd_batch_step_eager": ([_vp, ctypes.c_int], ctypes.c_int),
+    "pimd_batch_step_profiled": ([_vp, ctypes.c_int, _dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "pimd_batch_profile_slot_name": ([_vp, ctypes.c_int], ctypes.c_char_p),
+    "pimd_batch_estimators": ([_vp, ctypes.POINTER(Estimates)], ctypes.c_int),
+    "pimd_batch_sync": ([_vp], ctypes.c_int),
+    "pimd_batch_last_error": ([_vp], ctypes.c_char_p),
+    "pimd_batch_destroy": ([_vp], None),
 }
 
 
@@ -127,6 +153,14 @@ def _check(status, handle=None):
     if status != PIMD_OK:
         L = lib()
         msg = L.pimd_last_error(handle) if handle else L.pimd_global_error()
+        raise PimdError(status, (msg or b"").decode())
+    return status
+
+
+def _bcheck(status, handle=None):
+    if status != PIMD_OK:
+        L = lib()
+        msg = L.pimd_batch_last_error(handle) if handle else L.pimd_global_error()
         raise PimdError(status, (msg or b"").decode())
     return status
 
@@ -260,6 +294,163 @@ def pimd_vb_destroy(h):
 def pimd_vb_forward_noalloc(N, P, d, beta, xi, r1, rP, ld, V_out, stream):
     """V_ends without a caller workspace (library-owned fixed scratch, N <= 1024)."""
     return _check(lib().pimd_vb_forward_noalloc(N, P, d, beta, xi, r1, rP, ld, V_out, stream))
+
+
+# ---- batched replicas ---------------------------------------------------------
+
+def pimd_batch_create(Ns, P, d, betas, xis, omega, g, s):
+    R = len(Ns)
+    h = _vp()
+    _bcheck(lib().pimd_batch_create(R, (ctypes.c_int * R)(*Ns), P, d, (ctypes.c_double * R)(*betas),
+                                    (ctypes.c_double * R)(*xis), omega, g, s, ctypes.byref(h)))
+    return h
+
+
+def pimd_batch_configure(h, cfg):
+    return _bcheck(lib().pimd_batch_configure(h, ctypes.byref(cfg)), h)
+
+
+def pimd_batch_layout(h, R):
+    off = (ctypes.c_size_t * (R + 1))()
+    _bcheck(lib().pimd_batch_layout(h, off), h)
+    return list(off)
+
+
+def pimd_batch_workspace_bytes(h):
+    n = ctypes.c_size_t()
+    _bcheck(lib().pimd_batch_workspace_bytes(h, ctypes.byref(n)), h)
+    return n.value
+
+
+def pimd_batch_bind(h, bufs, stream):
+    return _bcheck(lib().pimd_batch_bind(h, ctypes.byref(bufs), stream), h)
+
+
+def pimd_batch_forces(h):
+    return _bcheck(lib().pimd_batch_forces(h), h)
+
+
+def pimd_batch_capture_graph(h):
+    return _bcheck(lib().pimd_batch_capture_graph(h), h)
+
+
+def pimd_batch_step(h, nsteps):
+    return _bcheck(lib().pimd_batch_step(h, nsteps), h)
+
+
+def pimd_batch_step_eager(h, nsteps):
+    return _bcheck(lib().pimd_batch_step_eager(h, nsteps), h)
+
+
+def pimd_batch_step_profiled(h, nsteps, max_slots=64):
+    ms = (ctypes.c_double * max_slots)()
+    n = ctypes.c_int()
+    _bcheck(lib().pimd_batch_step_profiled(h, nsteps, ms, max_slots, ctypes.byref(n)), h)
+    return [(lib().pimd_batch_profile_slot_name(h, i).decode(), ms[i]) for i in range(n.value)]
+
+
+def pimd_batch_profile_slot_name(h, slot):
+    return lib().pimd_batch_profile_slot_name(h, slot).decode()
+
+
+def pimd_batch_estimators(h, R):
+    out = (Estimates * R)()
+    _bcheck(lib().pimd_batch_estimators(h, out), h)
+    return [e.as_dict() for e in out]
+
+
+def pimd_batch_sync(h):
+    return _bcheck(lib().pimd_batch_sync(h), h)
+
+
+def pimd_batch_last_error(h):
+    return (lib().pimd_batch_last_error(h) or b"").decode()
+
+
+def pimd_batch_destroy(h):
+    lib().pimd_batch_destroy(h)
+
+
+class Batch:
+    """R replicas of uneven N, beta, xi in one set of torch-owned device arrays.
+
+    ``rs`` and ``ps`` are lists of particle-major (N_r, P, d) arrays.  Replica
+    r's slice-major block [P][d][n_pad_r] sits at element offset offsets[r] of
+    the flat float64 tensors.  All arithmetic happens in the C ABI's kernels.
+    """
+
+    def __init__(self, Ns, P, d, betas, xis, omega=1.0, g=0.0, s=0.5, rs=None, ps=None, device="cuda",
+                 stream=None, **cfg_kw):
+        import torch
+
+        self.torch = torch
+        self.R, self.P, self.d = len(Ns), P, d
+        self.Ns, self.betas, self.xis = list(Ns), list(betas), list(xis)
+        self.h = pimd_batch_create(Ns, P, d, betas, xis, omega, g, s)
+        cfg = pimd_default_config()
+        for k, v in cfg_kw.items():
+            setattr(cfg, k, v)
+        pimd_batch_configure(self.h, cfg)
+        self.cfg = cfg
+        self.offsets = pimd_batch_layout(self.h, self.R)
+        self.n_pad = [(n + 31) // 32 * 32 for n in Ns]
+        dev = torch.device(device)
+        f64 = torch.float64
+        tot = self.offsets[-1]
+        M = cfg.nhc_len
+        self.r = torch.zeros(tot, dtype=f64, device=dev)
+        self.p = torch.zeros_like(self.r)
+        self.f = torch.zeros_like(self.r)
+        self.eta = torch.zeros(M * tot, dtype=f64, device=dev)
+        self.peta = torch.zeros_like(self.eta)
+        nbytes = pimd_batch_workspace_bytes(self.h)
+        self.work = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+        self.work_ptr = (self.work.data_ptr() + 255) // 256 * 256
+        for q in range(self.R):
+            if rs is not None:
+                self._view(self.r, q)[:, :, :Ns[q]] = torch.as_tensor(rs[q], dtype=f64).permute(1, 2, 0).to(dev)
+            if ps is not None:
+                self._view(self.p, q)[:, :, :Ns[q]] = torch.as_tensor(ps[q], dtype=f64).permute(1, 2, 0).to(dev)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        self.bufs = BatchBuffers(self.r.data_ptr(), self.p.data_ptr(), self.f.data_ptr(), self.eta.data_ptr(),
+                                 self.peta.data_ptr(), self.work_ptr, nbytes)
+        pimd_batch_bind(self.h, self.bufs, self.stream.cuda_stream)
+
+    def _view(self, flat, q):
+        a, b = self.offsets[q], self.offsets[q + 1]
+        return flat[a:b].view(self.P, self.d, self.n_pad[q])
+
+    def positions(self, q):
+        return self._view(self.r, q)[:, :, :self.Ns[q]].permute(2, 0, 1).cpu().numpy()
+
+    def momenta(self, q):
+        return self._view(self.p, q)[:, :, :self.Ns[q]].permute(2, 0, 1).cpu().numpy()
+
+    def forces_array(self, q):
+        return self._view(self.f, q)[:, :, :self.Ns[q]].permute(2, 0, 1).cpu().numpy()
+
+    def forces(self):
+        pimd_batch_forces(self.h)
+
+    def step(self, n=1, graph=True):
+        (pimd_batch_step if graph else pimd_batch_step_eager)(self.h, n)
+
+    def estimators(self):
+        return pimd_batch_estimators(self.h, self.R)
+
+    def sync(self):
+        pimd_batch_sync(self.h)
+
+    def close(self):
+        if self.h:
+            pimd_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---- convenience: torch-owned buffers ---------------------------------------

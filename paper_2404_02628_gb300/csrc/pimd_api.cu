@@ -5,11 +5,13 @@
 #include <string.h>
 
 #include <string>
+#include <vector>
+#include <algorithm>
 
 #include "../../include/pimd.h"
 #include "pimd_exchange.cuh"
 #include "pimd_md.cuh"
-#include "pimd_xdf.cuh"
+#include "pimd_batch.cuh"
 
 namespace {
 
@@ -688,6 +690,28 @@ extern "C" const char* pimd_profile_slot_name(pimd_t c, int slot)
     return c->slot_names[slot];
 }
 
+// Estimators of one system from its scalar slots (primitive and virial
+// readings; Sec. III spring terms, Sec. II U).  False if any is non-finite.
+static bool fill_estimates(const double* t, int Pi, int Ni, int di, double beta, int thermostat, long long steps,
+                           pimd_estimates* out)
+{
+    const double P = Pi, N = Ni, d = di;
+    out->V_xi = t[SC_EINT] + (t[SC_GLINK] - t[SC_LAMBDA]) / beta;
+    out->V_xi_bwd = t[SC_EINT] + (t[SC_GLINK] - t[SC_LAMBDA_B]) / beta;
+    out->U_over_P = t[SC_U] / P;
+    out->spring = t[SC_EINT] + t[SC_SPRING_X];
+    out->virial = t[SC_VIRIAL];
+    out->kinetic = t[SC_KIN];
+    out->E_prim = 0.5 * P * d * N / beta - out->spring + out->U_over_P;
+    out->E_vir = out->U_over_P + out->virial / (2.0 * P);
+    out->H_conserved = out->kinetic + out->V_xi + out->U_over_P + (thermostat ? t[SC_THERMO] : 0.0);
+    out->step = steps;
+    const double* q = &out->E_prim;
+    for (int i = 0; i < 9; ++i)
+        if (!isfinite(q[i])) return false;
+    return true;
+}
+
 extern "C" pimd_status pimd_estimators(pimd_t c, pimd_estimates* out)
 {
     if (!c || !out) return fail(c, PIMD_EINVAL, "pimd_estimators: NULL argument");
@@ -706,20 +730,8 @@ extern "C" pimd_status pimd_estimators(pimd_t c, pimd_estimates* out)
     e = cudaMemcpy(t, base + c->off_sc, sizeof t, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemcpy(&flag, base + c->off_flag, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(c, e, "pimd_estimators: read");
-    const double P = c->P, N = c->N, d = c->d, beta = c->beta;
-    out->V_xi = t[SC_EINT] + (t[SC_GLINK] - t[SC_LAMBDA]) / beta;
-    out->V_xi_bwd = t[SC_EINT] + (t[SC_GLINK] - t[SC_LAMBDA_B]) / beta;
-    out->U_over_P = t[SC_U] / P;
-    out->spring = t[SC_EINT] + t[SC_SPRING_X];
-    out->virial = t[SC_VIRIAL];
-    out->kinetic = t[SC_KIN];
-    out->E_prim = 0.5 * P * d * N / beta - out->spring + out->U_over_P;
-    out->E_vir = out->U_over_P + out->virial / (2.0 * P);
-    out->H_conserved = out->kinetic + out->V_xi + out->U_over_P + (c->cfg.thermostat ? t[SC_THERMO] : 0.0);
-    out->step = c->steps;
-    const double* q = &out->E_prim;
-    for (int i = 0; i < 9; ++i)
-        if (!isfinite(q[i])) return fail(c, PIMD_ENONFINITE, "pimd_estimators: non-finite estimate");
+    if (!fill_estimates(t, c->P, c->N, c->d, c->beta, c->cfg.thermostat, c->steps, out))
+        return fail(c, PIMD_ENONFINITE, "pimd_estimators: non-finite estimate");
     if (flag) return fail(c, PIMD_ENONFINITE, "pimd_estimators: non-finite force");
     return PIMD_OK;
 }
@@ -889,6 +901,450 @@ extern "C" pimd_status pimd_vb_backward(pimd_vb_t h, const double* r1, const dou
 }
 
 extern "C" void pimd_vb_destroy(pimd_vb_t h) { delete h; }
+
+// ---------------------------------------------------------------------------
+// Batched replicas (uneven N, beta, xi; shared P, d, omega, g, s and config):
+// every step kernel is one launch over all replicas, the exchange recursion
+// one block per replica and direction (xsolo), the step one CUDA graph.
+
+namespace {
+constexpr int BATCH_NMAX = 2047;  // xsolo keeps h of every block in shared memory
+}
+
+struct pimd_batch {
+    int R, P, d;
+    double omega, g, s, A;
+    std::vector<int> N, npad;
+    std::vector<double> beta, xi;
+    pimd_config cfg;
+    std::string err;
+    bool bound = false;
+    pimd_batch_buffers buf;
+    cudaStream_t st = nullptr, cap = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    bool graph_failed = false;
+    long long steps = 0;
+    std::vector<size_t> off;  // bead element offset of each replica (R + 1 entries)
+    BatchGrid grid;
+    Layout L;
+    size_t off_args = 0, off_err = 0, off_sc = 0, off_tab = 0, off_flag = 0;
+    std::vector<RepArgs> args;
+    const char* slot_names[64] = {};
+};
+
+static pimd_status bfail(pimd_batch_t b, pimd_status s, const std::string& m)
+{
+    if (b) b->err = m;
+    else g_global_error = m;
+    return s;
+}
+
+static pimd_status bcuda(pimd_batch_t b, cudaError_t e, const char* where)
+{
+    return bfail(b, PIMD_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+extern "C" pimd_status pimd_batch_create(int R, const int* N, int P, int d, const double* beta, const double* xi,
+                                         double omega, double g, double s, pimd_batch_t* out)
+{
+    if (!out) return bfail(nullptr, PIMD_EINVAL, "pimd_batch_create: out is NULL");
+    *out = nullptr;
+    if (R < 1 || R > 65535 || !N || !beta || !xi) return bfail(nullptr, PIMD_EINVAL, "pimd_batch_create: R in [1, 65535] and arrays required");
+    if (P < 2 || P > 65535) return bfail(nullptr, PIMD_EINVAL, "pimd_batch_create: P must be in [2, 65535]");
+    if (d < 1 || d > 3) return bfail(nullptr, PIMD_EINVAL, "pimd_batch_create: d must be 1, 2 or 3");
+    if (!(omega >= 0.0) || !isfinite(omega) || !isfinite(g) || !(s > 0.0) || !isfinite(s))
+        return bfail(nullptr, PIMD_EINVAL, "pimd_batch_create: omega >= 0, finite g and s > 0 required");
+    for (int r = 0; r < R; ++r) {
+        if (N[r] < 1 || N[r] > BATCH_NMAX) return bfail(nullptr, PIMD_EINVAL, "pimd_batch_create: each N must be in [1, 2047]");
+        if (!(beta[r] > 0.0) || !isfinite(beta[r])) return bfail(nullptr, PIMD_EINVAL, "pimd_batch_create: each beta must be > 0");
+        if (!(xi[r] >= 0.0 && xi[r] <= 1.0)) return bfail(nullptr, PIMD_EINVAL, "pimd_batch_create: each xi must be in [0, 1]");
+    }
+    pimd_batch* b = new pimd_batch();
+    b->R = R;
+    b->P = P;
+    b->d = d;
+    b->omega = omega;
+    b->g = g;
+    b->s = s;
+    b->N.assign(N, N + R);
+    b->beta.assign(beta, beta + R);
+    b->xi.assign(xi, xi + R);
+    b->npad.resize(R);
+    b->off.resize(R + 1);
+    b->off[0] = 0;
+    for (int r = 0; r < R; ++r) {
+        b->npad[r] = (N[r] + 31) / 32 * 32;
+        b->off[r + 1] = b->off[r] + (size_t)P * d * b->npad[r];
+    }
+    pimd_default_config(&b->cfg);
+    b->A = g / (M_PI * s * s);
+    *out = b;
+    return PIMD_OK;
+}
+
+extern "C" pimd_status pimd_batch_configure(pimd_batch_t b, const pimd_config* cfg)
+{
+    if (!b || !cfg) return bfail(b, PIMD_EINVAL, "pimd_batch_configure: NULL argument");
+    if (b->bound) return bfail(b, PIMD_ESTATE, "pimd_batch_configure: already bound");
+    if (!(cfg->dt > 0.0) || cfg->nhc_len < 1 || cfg->nhc_len > 8 || !(cfg->mass > 0.0))
+        return bfail(b, PIMD_EINVAL, "pimd_batch_configure: dt > 0, nhc_len in [1, 8], mass > 0 required");
+    if (cfg->precision != PIMD_PREC_FP64 && cfg->precision != PIMD_PREC_MIXED)
+        return bfail(b, PIMD_EINVAL, "pimd_batch_configure: unknown precision");
+    if (cfg->amp_convention != PIMD_AMP_PAPER && cfg->amp_convention != PIMD_AMP_RAW)
+        return bfail(b, PIMD_EINVAL, "pimd_batch_configure: unknown amplitude convention");
+    b->cfg = *cfg;
+    b->A = cfg->amp_convention == PIMD_AMP_RAW ? b->g : b->g / (M_PI * b->s * b->s);
+    return PIMD_OK;
+}
+
+extern "C" pimd_status pimd_batch_layout(pimd_batch_t b, size_t* offsets)
+{
+    if (!b || !offsets) return bfail(b, PIMD_EINVAL, "pimd_batch_layout: NULL argument");
+    for (int r = 0; r <= b->R; ++r) offsets[r] = b->off[r];
+    return PIMD_OK;
+}
+
+// Workspace: per replica an exchange layout (store mode, band width nb) and
+// its partial-sum arrays sized by the batch grid; then the RepArgs array, the
+// scalar slots [R][SC_COUNT], one exp table and one error word.
+static void batch_layout(pimd_batch* b, std::vector<XLayout>& xl, std::vector<size_t>& offs)
+{
+    int nmax = 0;
+    for (int n : b->N) nmax = std::max(nmax, n);
+    const int npmax = (nmax + 1 + 31) / 32 * 32, nbmax = npmax / 32;
+    BatchGrid& g = b->grid;
+    g.R = b->R;
+    g.P = b->P;
+    g.d = b->d;
+    g.M = b->cfg.nhc_len;
+    g.mixed = b->cfg.precision == PIMD_PREC_MIXED;
+    g.gx_spr = springs_grid_x(nmax);
+    g.gx_pair = pair_grid_x(nmax);
+    g.gx_md = batch_md_blocks((nmax + 31) / 32 * 32, b->P, b->d);
+    g.gx_prep = xdf_prep_blocks(npmax);
+    g.gx_fin = xdf_finalize_blocks(nmax);
+    g.gx_table = (int)xdf_ntiles(nbmax, nbmax, 1);
+    g.nb_max = nbmax;
+    b->L = Layout();
+    xl.resize(b->R);
+    offs.resize((size_t)b->R * 5);
+    for (int r = 0; r < b->R; ++r) {
+        const int nb = (b->N[r] + 1 + 31) / 32;
+        xdf_layout(b->L, xl[r], b->N[r], 1, nb, 1);
+        offs[5 * r + 0] = b->L.add((size_t)g.gx_spr * b->P * sizeof(double));
+        offs[5 * r + 1] = b->L.add((size_t)g.gx_pair * b->P * 2 * sizeof(double));
+        offs[5 * r + 2] = b->L.add((size_t)g.gx_fin * sizeof(double));
+        offs[5 * r + 3] = b->L.add((size_t)g.gx_md * 2 * sizeof(double));
+        offs[5 * r + 4] = b->L.add((size_t)g.gx_prep * 2 * sizeof(double));
+    }
+    b->off_args = b->L.add((size_t)b->R * sizeof(RepArgs));
+    b->off_sc = b->L.add((size_t)b->R * SC_COUNT * sizeof(double));
+    b->off_tab = b->L.add(256 * sizeof(float2));
+    b->off_err = b->L.add(4 * sizeof(int));
+    b->off_flag = b->L.add(4 * sizeof(int));
+}
+
+extern "C" pimd_status pimd_batch_workspace_bytes(pimd_batch_t b, size_t* bytes)
+{
+    if (!b || !bytes) return bfail(b, PIMD_EINVAL, "pimd_batch_workspace_bytes: NULL argument");
+    std::vector<XLayout> xl;
+    std::vector<size_t> offs;
+    batch_layout(b, xl, offs);
+    *bytes = b->L.total;
+    return PIMD_OK;
+}
+
+static pimd_status batch_enqueue_forces(pimd_batch* b, cudaStream_t st, ProfMarks* pm = nullptr)
+{
+    const RepArgs* ra = (const RepArgs*)((char*)b->buf.work + b->off_args);
+    cudaError_t e = batch_launch_forces(ra, b->grid, st);
+    prof_mark(pm, "batch_springs_pair", st);
+    if (e != cudaSuccess) return bcuda(b, e, "batch springs/pair kernels");
+    e = batch_launch_exchange(ra, b->grid, st);
+    prof_mark(pm, "batch_exchange", st);
+    if (e != cudaSuccess) return bcuda(b, e, "batch exchange kernels");
+    return PIMD_OK;
+}
+
+static pimd_status batch_enqueue_step(pimd_batch* b, cudaStream_t st, ProfMarks* pm = nullptr)
+{
+    const RepArgs* ra = (const RepArgs*)((char*)b->buf.work + b->off_args);
+    cudaError_t e = batch_launch_md(ra, b->grid, true, st);
+    prof_mark(pm, "batch_md_pre", st);
+    if (e != cudaSuccess) return bcuda(b, e, "batch md pre kernel");
+    pimd_status s = batch_enqueue_forces(b, st, pm);
+    if (s != PIMD_OK) return s;
+    e = batch_launch_md(ra, b->grid, false, st);
+    prof_mark(pm, "batch_md_post", st);
+    if (e != cudaSuccess) return bcuda(b, e, "batch md post kernel");
+    return PIMD_OK;
+}
+
+static pimd_status batch_check_device(pimd_batch* b)
+{
+    cudaError_t e = cudaStreamSynchronize(b->st);
+    if (e != cudaSuccess) return bcuda(b, e, "stream synchronize");
+    int h = 0;
+    int* errp = (int*)((char*)b->buf.work + b->off_err);
+    e = cudaMemcpy(&h, errp, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return bcuda(b, e, "error word read");
+    if (h != 0) {
+        cudaMemsetAsync(errp, 0, sizeof(int), b->st);
+        cudaStreamSynchronize(b->st);
+        char msg[160];
+        snprintf(msg, sizeof msg, "device wait gave up (code 0x%08x)", h);
+        return bfail(b, PIMD_ETIMEOUT, msg);
+    }
+    return PIMD_OK;
+}
+
+extern "C" pimd_status pimd_batch_bind(pimd_batch_t b, const pimd_batch_buffers* bf, void* stream)
+{
+    if (!b || !bf) return bfail(b, PIMD_EINVAL, "pimd_batch_bind: NULL argument");
+    if (b->bound) return bfail(b, PIMD_ESTATE, "pimd_batch_bind: already bound");
+    if (!bf->r || !bf->p || !bf->f || !bf->work) return bfail(b, PIMD_EINVAL, "pimd_batch_bind: NULL buffer");
+    if (b->cfg.thermostat && (!bf->eta || !bf->peta)) return bfail(b, PIMD_EINVAL, "pimd_batch_bind: thermostat buffers missing");
+    if (((uintptr_t)bf->work & 255) != 0) return bfail(b, PIMD_EINVAL, "pimd_batch_bind: workspace must be 256-byte aligned");
+    std::vector<XLayout> xl;
+    std::vector<size_t> offs;
+    batch_layout(b, xl, offs);
+    if (bf->work_bytes < b->L.total) {
+        char msg[160];
+        snprintf(msg, sizeof msg, "pimd_batch_bind: workspace too small (%zu < %zu bytes)", bf->work_bytes, b->L.total);
+        return bfail(b, PIMD_ENOMEM, msg);
+    }
+    b->buf = *bf;
+    b->st = (cudaStream_t)stream;
+    char* base = (char*)bf->work;
+    const int M = b->cfg.nhc_len;
+    b->args.assign(b->R, RepArgs());
+    for (int r = 0; r < b->R; ++r) {
+        RepArgs& a = b->args[r];
+        memset(&a, 0, sizeof a);
+        const int N = b->N[r], np = b->npad[r], P = b->P, d = b->d, nb = (N + 1 + 31) / 32;
+        const double beta = b->beta[r];
+        double* rr = bf->r + b->off[r];
+        a.bv.N = N;
+        a.bv.P = P;
+        a.bv.d = d;
+        a.bv.ld = np;
+        a.bv.r = rr;
+        a.bv.p = bf->p + b->off[r];
+        a.bv.f = bf->f + b->off[r];
+        a.bv.eta = bf->eta ? bf->eta + (size_t)M * b->off[r] : nullptr;
+        a.bv.peta = bf->peta ? bf->peta + (size_t)M * b->off[r] : nullptr;
+        a.bv.M = M;
+        a.fp.ks = P / (beta * beta);
+        a.fp.omega2 = b->omega * b->omega;
+        a.fp.A = b->A;
+        a.fp.inv_s2 = 1.0 / (b->s * b->s);
+        a.fp.mixed = b->cfg.precision == PIMD_PREC_MIXED;
+        a.mp.dt = b->cfg.dt;
+        a.mp.mass = b->cfg.mass;
+        a.mp.kT = 1.0 / beta;
+        a.mp.Q = b->cfg.nhc_Q > 0.0 ? b->cfg.nhc_Q : beta / P;
+        a.mp.inv_mass = 1.0 / a.mp.mass;
+        a.mp.inv_Q = 1.0 / a.mp.Q;
+        a.mp.thermostat = b->cfg.thermostat;
+        a.xv = xdf_view(base, xl[r], N, P, d, beta, b->xi[r], 1, nb, 1, rr + (size_t)(P - 1) * d * np, rr, np, np,
+                        b->cfg.spin_limit, 0);
+        a.xv.err = (int*)(base + b->off_err);
+        a.xv.tab = (const float2*)(base + b->off_tab);
+        a.xv.lsum = (double*)(base + offs[5 * r + 4]);
+        a.fo.f = a.bv.f;
+        a.fo.ldf = np;
+        a.fo.P = P;
+        a.fo.part = (double*)(base + offs[5 * r + 2]);
+        a.part_spr = (double*)(base + offs[5 * r + 0]);
+        a.part_pair = (double*)(base + offs[5 * r + 1]);
+        a.part_md = (double*)(base + offs[5 * r + 3]);
+        ScalarSources& ss = a.ss;
+        ss.springs = a.part_spr;
+        ss.n_springs = b->grid.gx_spr * P;
+        ss.lsum = a.xv.lsum;
+        ss.n_lsum = b->grid.gx_prep;
+        ss.pair = a.part_pair;
+        ss.n_pair = b->grid.gx_pair * P;
+        ss.fin = a.fo.part;
+        ss.n_fin = b->grid.gx_fin;
+        ss.md = a.part_md;
+        ss.n_md = b->grid.gx_md;
+        ss.N = N;
+        ss.xi_zero = b->xi[r] == 0.0;
+        ss.log_xi = b->xi[r] > 0.0 ? log(b->xi[r]) : 0.0;
+        ss.lam = a.xv.lam;
+        ss.out = (double*)(base + b->off_sc) + (size_t)r * SC_COUNT;
+    }
+    cudaError_t e = cudaMemcpyAsync(base + b->off_args, b->args.data(), b->args.size() * sizeof(RepArgs),
+                                    cudaMemcpyHostToDevice, b->st);
+    if (e == cudaSuccess && b->cfg.thermostat) {
+        const size_t n = (size_t)M * b->off[b->R];
+        e = cudaMemsetAsync(bf->eta, 0, n * sizeof(double), b->st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(bf->peta, 0, n * sizeof(double), b->st);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + b->off_err, 0, 8 * sizeof(int), b->st);
+    if (e == cudaSuccess) e = xdf_upload_table((float2*)(base + b->off_tab), b->st);
+    if (e != cudaSuccess) return bcuda(b, e, "pimd_batch_bind: setup");
+    b->bound = true;
+    b->steps = 0;
+    pimd_status s = batch_enqueue_forces(b, b->st);
+    if (s != PIMD_OK) {
+        b->bound = false;
+        return s;
+    }
+    return PIMD_OK;
+}
+
+extern "C" pimd_status pimd_batch_forces(pimd_batch_t b)
+{
+    if (!b) return bfail(b, PIMD_EINVAL, "pimd_batch_forces: NULL handle");
+    if (!b->bound) return bfail(b, PIMD_ESTATE, "pimd_batch_forces: not bound");
+    return batch_enqueue_forces(b, b->st);
+}
+
+extern "C" pimd_status pimd_batch_step_eager(pimd_batch_t b, int nsteps)
+{
+    if (!b) return bfail(b, PIMD_EINVAL, "pimd_batch_step_eager: NULL handle");
+    if (!b->bound) return bfail(b, PIMD_ESTATE, "pimd_batch_step_eager: not bound");
+    if (nsteps < 0) return bfail(b, PIMD_EINVAL, "pimd_batch_step_eager: nsteps < 0");
+    for (int n = 0; n < nsteps; ++n) {
+        pimd_status s = batch_enqueue_step(b, b->st);
+        if (s != PIMD_OK) return s;
+    }
+    b->steps += nsteps;
+    return PIMD_OK;
+}
+
+extern "C" pimd_status pimd_batch_capture_graph(pimd_batch_t b)
+{
+    if (!b) return bfail(b, PIMD_EINVAL, "pimd_batch_capture_graph: NULL handle");
+    if (!b->bound) return bfail(b, PIMD_ESTATE, "pimd_batch_capture_graph: not bound");
+    if (b->graph) return PIMD_OK;
+    cudaError_t e;
+    if (!b->cap) {
+        e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return bcuda(b, e, "graph stream");
+    }
+    e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return bcuda(b, e, "begin capture");
+    pimd_status s = batch_enqueue_step(b, b->cap);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(b->cap, &g);
+    if (s != PIMD_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+    }
+    if (e != cudaSuccess) return bcuda(b, e, "end capture");
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        b->graph = nullptr;
+        return bcuda(b, e, "graph instantiate");
+    }
+    return PIMD_OK;
+}
+
+extern "C" pimd_status pimd_batch_step(pimd_batch_t b, int nsteps)
+{
+    if (!b) return bfail(b, PIMD_EINVAL, "pimd_batch_step: NULL handle");
+    if (!b->bound) return bfail(b, PIMD_ESTATE, "pimd_batch_step: not bound");
+    if (nsteps < 0) return bfail(b, PIMD_EINVAL, "pimd_batch_step: nsteps < 0");
+    if (!b->graph && !b->graph_failed) {
+        if (pimd_batch_capture_graph(b) != PIMD_OK) {
+            b->graph_failed = true;
+            cudaGetLastError();
+        }
+    }
+    if (!b->graph) return pimd_batch_step_eager(b, nsteps);
+    for (int n = 0; n < nsteps; ++n) {
+        cudaError_t e = cudaGraphLaunch(b->graph, b->st);
+        if (e != cudaSuccess) return bcuda(b, e, "graph launch");
+    }
+    b->steps += nsteps;
+    return PIMD_OK;
+}
+
+extern "C" pimd_status pimd_batch_step_profiled(pimd_batch_t b, int nsteps, double* ms_out, int max_slots, int* n_slots)
+{
+    if (!b || !ms_out || !n_slots || max_slots < 1) return bfail(b, PIMD_EINVAL, "pimd_batch_step_profiled: bad argument");
+    if (!b->bound) return bfail(b, PIMD_ESTATE, "pimd_batch_step_profiled: not bound");
+    ProfMarks pm;
+    memset(&pm, 0, sizeof pm);
+    for (int i = 0; i < 64; ++i)
+        if (cudaEventCreate(&pm.ev[i]) != cudaSuccess) return bfail(b, PIMD_ECUDA, "event create");
+    for (int i = 0; i < max_slots; ++i) ms_out[i] = 0.0;
+    int slots = 0;
+    pimd_status s = PIMD_OK;
+    for (int n = 0; n < nsteps && s == PIMD_OK; ++n) {
+        pm.n = 0;
+        prof_mark(&pm, "start", b->st);
+        s = batch_enqueue_step(b, b->st, &pm);
+        cudaEventSynchronize(pm.ev[pm.n - 1]);
+        slots = std::min(pm.n - 1, max_slots);
+        for (int i = 0; i < slots; ++i) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, pm.ev[i], pm.ev[i + 1]);
+            ms_out[i] += ms;
+            b->slot_names[i] = pm.name[i + 1];
+        }
+    }
+    for (int i = 0; i < 64; ++i) cudaEventDestroy(pm.ev[i]);
+    b->steps += nsteps;
+    *n_slots = slots;
+    return s;
+}
+
+extern "C" const char* pimd_batch_profile_slot_name(pimd_batch_t b, int slot)
+{
+    if (!b || slot < 0 || slot >= 64 || !b->slot_names[slot]) return "";
+    return b->slot_names[slot];
+}
+
+extern "C" pimd_status pimd_batch_estimators(pimd_batch_t b, pimd_estimates* out)
+{
+    if (!b || !out) return bfail(b, PIMD_EINVAL, "pimd_batch_estimators: NULL argument");
+    if (!b->bound) return bfail(b, PIMD_ESTATE, "pimd_batch_estimators: not bound");
+    char* base = (char*)b->buf.work;
+    const RepArgs* ra = (const RepArgs*)(base + b->off_args);
+    cudaError_t e = batch_launch_scalars(ra, b->grid, b->st);
+    if (e != cudaSuccess) return bcuda(b, e, "batch scalar reduction");
+    int* flag = (int*)(base + b->off_flag);
+    e = cudaMemsetAsync(flag, 0, sizeof(int), b->st);
+    for (int r = 0; r < b->R && e == cudaSuccess; ++r)
+        e = launch_nonfinite_scan(b->buf.f + b->off[r], b->N[r], b->P, b->d, b->npad[r], flag, b->st);
+    if (e != cudaSuccess) return bcuda(b, e, "pimd_batch_estimators: scan");
+    pimd_status s = batch_check_device(b);
+    if (s != PIMD_OK) return s;
+    std::vector<double> t((size_t)b->R * SC_COUNT);
+    int hflag = 0;
+    e = cudaMemcpy(t.data(), base + b->off_sc, t.size() * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return bcuda(b, e, "pimd_batch_estimators: read");
+    bool finite = true;
+    for (int r = 0; r < b->R; ++r)
+        finite &= fill_estimates(&t[(size_t)r * SC_COUNT], b->P, b->N[r], b->d, b->beta[r], b->cfg.thermostat, b->steps,
+                                 &out[r]);
+    if (!finite) return bfail(b, PIMD_ENONFINITE, "pimd_batch_estimators: non-finite estimate");
+    if (hflag) return bfail(b, PIMD_ENONFINITE, "pimd_batch_estimators: non-finite force");
+    return PIMD_OK;
+}
+
+extern "C" pimd_status pimd_batch_sync(pimd_batch_t b)
+{
+    if (!b) return bfail(b, PIMD_EINVAL, "pimd_batch_sync: NULL handle");
+    if (!b->bound) return bfail(b, PIMD_ESTATE, "pimd_batch_sync: not bound");
+    return batch_check_device(b);
+}
+
+extern "C" const char* pimd_batch_last_error(pimd_batch_t b) { return b ? b->err.c_str() : g_global_error.c_str(); }
+
+extern "C" void pimd_batch_destroy(pimd_batch_t b)
+{
+    if (!b) return;
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
+}
 
 // ---------------------------------------------------------------------------
 // Exchange potential with library-owned scratch, for callers that cannot

@@ -2,7 +2,7 @@
 // reductions for sm_103a.
 #include <math.h>
 
-#include "pimd_md.cuh"
+#include "pimd_batch.cuh"
 
 namespace {
 
@@ -22,7 +22,7 @@ __device__ __forceinline__ float ex2_approx(float x)
 // within-particle half of the exterior-bead formulas): F_l^j = -k (2 r^j -
 // r^{j+1} - r^{j-1}), with the missing neighbour of beads 1 and P dropped.
 // Also sum_l E_int^(l) (always FP64).
-__global__ void __launch_bounds__(SPR_T) springs_kernel(BeadView b, ForceParams fp, double* f, double* part)
+__device__ __forceinline__ void springs_body(const BeadView& b, const ForceParams& fp, double* f, double* part)
 {
     __shared__ double red[32];
     const int l = blockIdx.x * SPR_T + threadIdx.x, j = blockIdx.y;
@@ -49,6 +49,11 @@ __global__ void __launch_bounds__(SPR_T) springs_kernel(BeadView b, ForceParams 
     if (threadIdx.x == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = v[0];
 }
 
+__global__ void __launch_bounds__(SPR_T) springs_kernel(BeadView b, ForceParams fp, double* f, double* part)
+{
+    springs_body(b, fp, f, part);
+}
+
 // ---------------------------------------------------------------------------
 // (a4) Trap + Gaussian pairs in each bead slice (Sec. II U, Sec. IV B):
 // V_slice = sum_l 1/2 omega^2 r_l^2 + 1/2 sum_{i!=k} A exp(-|r_i - r_k|^2/s^2),
@@ -56,10 +61,17 @@ __global__ void __launch_bounds__(SPR_T) springs_kernel(BeadView b, ForceParams 
 // shared memory 128 particles at a time.  Writes per-block (energy, virial).
 
 template <int D>
-__global__ void __launch_bounds__(PAIR_T) pair_kernel_f64(BeadView b, ForceParams fp, double* f, double* part)
+__device__ __forceinline__ void pair_body_f64(const BeadView& b, const ForceParams& fp, double* f, double* part)
 {
     __shared__ double sx[D][PAIR_T];
     __shared__ double red[64];
+    if (blockIdx.x * PAIR_T >= b.N) {  // a block past this replica's particles
+        if (threadIdx.x == 0) {
+            part[2 * (blockIdx.y * gridDim.x + blockIdx.x) + 0] = 0.0;
+            part[2 * (blockIdx.y * gridDim.x + blockIdx.x) + 1] = 0.0;
+        }
+        return;
+    }
     const int i = blockIdx.x * PAIR_T + threadIdx.x, j = blockIdx.y;
     const double* rs = b.r + (size_t)j * D * b.ld;
     double xi[D], g[D];
@@ -120,10 +132,17 @@ __global__ void __launch_bounds__(PAIR_T) pair_kernel_f64(BeadView b, ForceParam
 // FP32x2 pipe, the partner tile sitting in shared memory as negated
 // coordinate pairs {x_k, x_k+1} per component.
 template <int D>
-__global__ void __launch_bounds__(PAIR_T) pair_kernel_f32(BeadView b, ForceParams fp, double* f, double* part)
+__device__ __forceinline__ void pair_body_f32(const BeadView& b, const ForceParams& fp, double* f, double* part)
 {
     __shared__ float2 sx[D][PAIR_T / 2];
     __shared__ double red[64];
+    if (blockIdx.x * PAIR_T >= b.N) {  // a block past this replica's particles
+        if (threadIdx.x == 0) {
+            part[2 * (blockIdx.y * gridDim.x + blockIdx.x) + 0] = 0.0;
+            part[2 * (blockIdx.y * gridDim.x + blockIdx.x) + 1] = 0.0;
+        }
+        return;
+    }
     const int i = blockIdx.x * PAIR_T + threadIdx.x, j = blockIdx.y;
     const double* rs = b.r + (size_t)j * D * b.ld;
     const float sc = (float)sqrt(fp.inv_s2 * 1.4426950408889634);
@@ -186,6 +205,18 @@ __global__ void __launch_bounds__(PAIR_T) pair_kernel_f32(BeadView b, ForceParam
     }
 }
 
+template <int D>
+__global__ void __launch_bounds__(PAIR_T) pair_kernel_f64(BeadView b, ForceParams fp, double* f, double* part)
+{
+    pair_body_f64<D>(b, fp, f, part);
+}
+
+template <int D>
+__global__ void __launch_bounds__(PAIR_T) pair_kernel_f32(BeadView b, ForceParams fp, double* f, double* part)
+{
+    pair_body_f32<D>(b, fp, f, part);
+}
+
 // ---------------------------------------------------------------------------
 // (a5) Massive Nose-Hoover chains (one chain of M thermostats of mass Q per
 // degree of freedom) with the reversible Trotter half step of length tau:
@@ -240,7 +271,7 @@ __device__ __forceinline__ void nhc_half_step(double& p, double (&eta)[M], doubl
 }
 
 template <bool PRE, int M>
-__global__ void __launch_bounds__(MD_T) md_kernel(BeadView b, MDParams mp)
+__device__ __forceinline__ void md_body(const BeadView& b, const MDParams& mp)
 {
     const size_t stride = (size_t)b.P * b.d * b.ld;
     for (size_t o = (size_t)blockIdx.x * MD_T + threadIdx.x; o < stride; o += (size_t)gridDim.x * MD_T) {
@@ -274,7 +305,13 @@ __global__ void __launch_bounds__(MD_T) md_kernel(BeadView b, MDParams mp)
     }
 }
 
-__global__ void __launch_bounds__(MD_T) md_energy_kernel(BeadView b, MDParams mp, double* part)
+template <bool PRE, int M>
+__global__ void __launch_bounds__(MD_T) md_kernel(BeadView b, MDParams mp)
+{
+    md_body<PRE, M>(b, mp);
+}
+
+__device__ __forceinline__ void md_energy_body(const BeadView& b, const MDParams& mp, double* part)
 {
     __shared__ double red[64];
     const size_t stride = (size_t)b.P * b.d * b.ld;
@@ -296,10 +333,14 @@ __global__ void __launch_bounds__(MD_T) md_energy_kernel(BeadView b, MDParams mp
     }
 }
 
-// Fixed-order reduction of every per-block partial into the scalar slots.
-__global__ void scalars_kernel(ScalarSources s)
+__global__ void __launch_bounds__(MD_T) md_energy_kernel(BeadView b, MDParams mp, double* part)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    md_energy_body(b, mp, part);
+}
+
+// Fixed-order reduction of every per-block partial into the scalar slots.
+__device__ __forceinline__ void scalars_body(const ScalarSources& s)
+{
     double t[SC_COUNT];
     for (int q = 0; q < SC_COUNT; ++q) t[q] = 0.0;
     for (int i = 0; i < s.n_springs; ++i) t[SC_EINT] += s.springs[i];
@@ -327,6 +368,52 @@ __global__ void scalars_kernel(ScalarSources s)
         t[SC_LAMBDA_B] = s.N * s.log_xi + wef_log(Wef{s.c_m[0], s.c_e[0]});
     }
     for (int q = 0; q < SC_COUNT; ++q) s.out[q] = t[q];
+}
+
+__global__ void scalars_kernel(ScalarSources s)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    scalars_body(s);
+}
+
+// ---------------------------------------------------------------------------
+// Batched wrappers: replica blockIdx.z, arguments from its RepArgs.
+
+__global__ void __launch_bounds__(SPR_T) springs_batch(const RepArgs* ra)
+{
+    const RepArgs& a = ra[blockIdx.z];
+    ForceParams fp = a.fp;
+    fp.accumulate = 0;
+    springs_body(a.bv, fp, a.bv.f, a.part_spr);
+}
+
+template <int D, bool MIXED>
+__global__ void __launch_bounds__(PAIR_T) pair_batch(const RepArgs* ra)
+{
+    const RepArgs& a = ra[blockIdx.z];
+    ForceParams fp = a.fp;
+    fp.accumulate = 1;
+    if (MIXED) pair_body_f32<D>(a.bv, fp, a.bv.f, a.part_pair);
+    else pair_body_f64<D>(a.bv, fp, a.bv.f, a.part_pair);
+}
+
+template <bool PRE, int M>
+__global__ void __launch_bounds__(MD_T) md_batch(const RepArgs* ra)
+{
+    const RepArgs& a = ra[blockIdx.z];
+    md_body<PRE, M>(a.bv, a.mp);
+}
+
+__global__ void __launch_bounds__(MD_T) md_energy_batch(const RepArgs* ra)
+{
+    const RepArgs& a = ra[blockIdx.z];
+    md_energy_body(a.bv, a.mp, a.part_md);
+}
+
+__global__ void scalars_batch(const RepArgs* ra)
+{
+    if (threadIdx.x != 0) return;
+    scalars_body(ra[blockIdx.x].ss);
 }
 
 __global__ void zero_kernel(double* x, size_t n)
@@ -416,5 +503,52 @@ cudaError_t launch_zero(double* x, size_t n, cudaStream_t st)
 cudaError_t launch_nonfinite_scan(const double* x, int N, int P, int d, int ld, int* flag, cudaStream_t st)
 {
     nonfinite_kernel<<<152, 256, 0, st>>>(x, N, P, d, ld, flag);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// batched launchers
+
+int batch_md_blocks(int nmax, int P, int d) { return (int)(((long long)nmax * P * d + MD_T - 1) / MD_T); }
+
+cudaError_t batch_launch_md(const RepArgs* ra, const BatchGrid& g, bool pre, cudaStream_t st)
+{
+    const int M = g.M;
+    const dim3 grid(g.gx_md, 1, g.R);
+#define PIMD_MDB(m)                                                         \
+    case m:                                                                 \
+        if (pre) md_batch<true, m><<<grid, MD_T, 0, st>>>(ra);              \
+        else md_batch<false, m><<<grid, MD_T, 0, st>>>(ra);                 \
+        break;
+    switch (M) {
+        PIMD_MDB(1) PIMD_MDB(2) PIMD_MDB(3) PIMD_MDB(4) PIMD_MDB(5) PIMD_MDB(6) PIMD_MDB(7) PIMD_MDB(8)
+    default: return cudaErrorInvalidValue;
+    }
+#undef PIMD_MDB
+    return cudaGetLastError();
+}
+
+cudaError_t batch_launch_forces(const RepArgs* ra, const BatchGrid& g, cudaStream_t st)
+{
+    const int P = g.P, d = g.d;
+    const bool mixed = g.mixed != 0;
+    springs_batch<<<dim3(g.gx_spr, P, g.R), SPR_T, 0, st>>>(ra);
+    const dim3 grid(g.gx_pair, P, g.R);
+    if (mixed) {
+        if (d == 1) pair_batch<1, true><<<grid, PAIR_T, 0, st>>>(ra);
+        else if (d == 2) pair_batch<2, true><<<grid, PAIR_T, 0, st>>>(ra);
+        else pair_batch<3, true><<<grid, PAIR_T, 0, st>>>(ra);
+    } else {
+        if (d == 1) pair_batch<1, false><<<grid, PAIR_T, 0, st>>>(ra);
+        else if (d == 2) pair_batch<2, false><<<grid, PAIR_T, 0, st>>>(ra);
+        else pair_batch<3, false><<<grid, PAIR_T, 0, st>>>(ra);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t batch_launch_scalars(const RepArgs* ra, const BatchGrid& g, cudaStream_t st)
+{
+    md_energy_batch<<<dim3(g.gx_md, 1, g.R), MD_T, 0, st>>>(ra);
+    scalars_batch<<<g.R, 32, 0, st>>>(ra);
     return cudaGetLastError();
 }

@@ -4,7 +4,7 @@
 #include <math.h>
 #include <stdio.h>
 
-#include "pimd_xdf.cuh"
+#include "pimd_batch.cuh"
 
 namespace {
 
@@ -369,7 +369,7 @@ __device__ __forceinline__ void load_tab_smem(float2* tab_s, const float2* tab)
 // ------------------------------------------------------------------------
 // prep: double-float endpoints, row constants, link energy, flags
 
-__global__ void __launch_bounds__(256) xdf_prep_kernel(XView v)
+__device__ __forceinline__ void prep_body(const XView& v)
 {
     __shared__ double red[64];
     double acc[2] = {0.0, 0.0};
@@ -424,10 +424,12 @@ __global__ void __launch_bounds__(256) xdf_prep_kernel(XView v)
     }
 }
 
+__global__ void __launch_bounds__(256) xdf_prep_kernel(XView v) { prep_body(v); }
+
 // ------------------------------------------------------------------------
 // factor table: M tiles (all in store mode, band |J-I| < W otherwise)
 
-__global__ void __launch_bounds__(256) xdf_table_kernel(XView v, long long ntiles)
+__device__ __forceinline__ void table_body(const XView& v, long long ntiles)
 {
     __shared__ float2 tab[256];
     load_tab_smem(tab, v.tab);
@@ -455,10 +457,12 @@ __global__ void __launch_bounds__(256) xdf_table_kernel(XView v, long long ntile
     }
 }
 
+__global__ void __launch_bounds__(256) xdf_table_kernel(XView v, long long ntiles) { table_body(v, ntiles); }
+
 // ------------------------------------------------------------------------
 // block operators: G_J = (I - M_JJ)^{-1}, Q_J = G_J M_{J,J-1}, P_J = M_{J+1,J} G_J
 
-__global__ void __launch_bounds__(256) xdf_blockops_kernel(XView v)
+__device__ __forceinline__ void blockops_body(const XView& v)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     DfwTile* L = reinterpret_cast<DfwTile*>(smem_raw);
@@ -466,6 +470,7 @@ __global__ void __launch_bounds__(256) xdf_blockops_kernel(XView v)
     DfwTile* Ms = L + 2;
     DfwTile* Mp = L + 3;
     const int J = blockIdx.x;
+    if (J >= v.nb) return;  // a block past this replica's blocks
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     {
         const long long t = xdf_tile_index(v, J, J);
@@ -513,6 +518,8 @@ __global__ void __launch_bounds__(256) xdf_blockops_kernel(XView v)
         v.P[J].e[o] = Pm.e;
     }
 }
+
+__global__ void __launch_bounds__(256) xdf_blockops_kernel(XView v) { blockops_body(v); }
 
 // ------------------------------------------------------------------------
 // recursion: chain blocks and helpers
@@ -609,19 +616,23 @@ __device__ __forceinline__ void vstore(int* p, int x) { *(volatile int*)p = x; }
 
 // Bounded spin on a shared-memory counter; false if it gave up (recorded in
 // the error word) or another role of the block has aborted.
-__device__ __forceinline__ bool smem_wait_ge(const int* ctr, int want, ChainS* cs, int limit, int* err, int code)
+__device__ __forceinline__ bool smem_wait_ge(const int* ctr, int want, int* abort_word, int limit, int* err, int code)
 {
     for (int it = 0; it < limit; ++it) {
         if (vload(ctr) >= want) {
             __threadfence_block();
             return true;
         }
-        if (vload(&cs->abort)) return false;
+        if (vload(abort_word)) return false;
         __nanosleep(32);
     }
     atomicCAS(err, 0, (PIMD_DEVERR_TIMEOUT << 24) | (code & 0xFFFFFF));
-    vstore(&cs->abort, 1);
+    vstore(abort_word, 1);
     return false;
+}
+__device__ __forceinline__ bool smem_wait_ge(const int* ctr, int want, ChainS* cs, int limit, int* err, int code)
+{
+    return smem_wait_ge(ctr, want, &cs->abort, limit, err, code);
 }
 
 template <int DIR>
@@ -1056,37 +1067,41 @@ __global__ void __launch_bounds__(XDF_THREADS, 1) xdf_recursion_kernel(XView v)
 }
 
 // Band sums: forward row block J over tiles I in [J-W+1, J]; backward column
-// block I over row blocks [I, I+W-1].  One warp per tile, merged in order.
-__global__ void __launch_bounds__(XDF_MAXW * 32) xdf_band_kernel(XView v)
+// block I over row blocks [I, I+W-1].  Warp w takes tiles m = w, w + nw, ...
+// (nw = warps of the block) and the warps' sums are merged in warp order.
+__device__ __forceinline__ void band_body(const XView& v)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nw = blockDim.x >> 5;
     DfwTile* T = reinterpret_cast<DfwTile*>(smem_raw);
-    WeightSmem* Ws = reinterpret_cast<WeightSmem*>(smem_raw + v.W * sizeof(DfwTile));
-    DVAcc* hm = reinterpret_cast<DVAcc*>(smem_raw + v.W * (sizeof(DfwTile) + sizeof(WeightSmem)));
-    __shared__ float2 tab[256];
-    load_tab_smem(tab, v.tab);
-    block_sync();
+    WeightSmem* Ws = reinterpret_cast<WeightSmem*>(smem_raw + nw * sizeof(DfwTile));
+    DVAcc* hm = reinterpret_cast<DVAcc*>(smem_raw + nw * (sizeof(DfwTile) + sizeof(WeightSmem)));
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int blk = blockIdx.x, dir = blockIdx.y;
+    if (blk >= v.nb) return;  // a block past this replica's blocks
     DVAcc a = dv_zero();
-    const int J = dir == 0 ? blk : blk + w, I = dir == 0 ? blk - w : blk;
-    if (I >= 0 && J < v.nb) {
+    for (int m = w; m < v.W; m += nw) {
+        const int J = dir == 0 ? blk : blk + m, I = dir == 0 ? blk - m : blk;
+        if (I < 0 || J >= v.nb) continue;
         fetch_tile_warp(v, &T[w], J, I, lane);
         cp_commit();
         if (dir == 0) load_wf(v, &Ws[w], I, lane);
         else load_wb(v, &Ws[w], J, lane);
         cp_wait<0>();
         __syncwarp();
-        a = dir == 0 ? weighted_rows(&T[w], &Ws[w], lane, v.d) : weighted_cols(&T[w], &Ws[w], lane, v.d);
+        dv_add(a, dir == 0 ? weighted_rows(&T[w], &Ws[w], lane, v.d) : weighted_cols(&T[w], &Ws[w], lane, v.d));
+        __syncwarp();
     }
     hm[w * 32 + lane] = a;
     block_sync();
     if (w == 0) {
         DVAcc t = dv_zero();
-        for (int q = 0; q < v.W; ++q) dv_add(t, hm[q * 32 + lane]);
+        for (int q = 0; q < nw; ++q) dv_add(t, hm[q * 32 + lane]);
         store_dv(v.bandh, v.bandl, v.bande, xband_index(v, dir, blk, lane), t);
     }
 }
+
+__global__ void __launch_bounds__(256) xdf_band_kernel(XView v) { band_body(v); }
 
 __device__ __forceinline__ dfw xget(const float* h, const float* l, const int* e, int i) { return dfw{h[i], l[i], e[i]}; }
 
@@ -1099,7 +1114,7 @@ __device__ __forceinline__ double dv_comp(const DVAcc& a, int c, dfw scale)
 }
 
 // Endpoint forces (Sec. III exterior-bead formulas, factorised form).
-__global__ void __launch_bounds__(256) xdf_finalize_kernel(XView v, FinalizeOut o)
+__device__ __forceinline__ void finalize_body(const XView& v, const FinalizeOut& o)
 {
     __shared__ double red[32];
     double esum[1] = {0.0};
@@ -1177,6 +1192,262 @@ __global__ void __launch_bounds__(256) xdf_finalize_kernel(XView v, FinalizeOut 
     if (threadIdx.x == 0 && o.part) o.part[blockIdx.x] = esum[0];
 }
 
+__global__ void __launch_bounds__(256) xdf_finalize_kernel(XView v, FinalizeOut o) { finalize_body(v, o); }
+
+// ------------------------------------------------------------------------
+// Self-contained recursion for small systems (batched replicas): one block per
+// replica and direction does every product of the solve itself, so it waits
+// on no other block.  Iteration it (block J) multiplies, in chunks of at most
+// XS_CHUNK tiles streamed through shared memory by bulk copies:
+//   list entry 0  Q_J (forward) / P_J (backward) by the previous solution block,
+//   list entry 1  G_J by h_J (every contribution to h_J is in by then),
+//   list entry m  (m >= 2) M_{J-1+m, J-1} (forward) / M_{J+1, J+1-m} (backward)
+//                 by the previous solution block, added into h of block
+//                 J-1+m / J+1-m (right-looking update).
+// Chunk 0 holds entries 0 and 1, so the dependent chain per iteration is one
+// chunk's products and one reduction.  Warps 0-5 compute (work split as in
+// chain_segments, with the chunk's tile count for W); warp 7 publishes.
+
+#define XS_CHUNK 6
+#define XS_SLOTS (2 * XS_CHUNK)
+#define XS_NBMAX 64  // blocks of the largest replica (N <= 2047)
+
+struct SoloS {
+    float4 xv[XDF_XR][32];          // solution blocks (ring)
+    float4 h[XS_NBMAX][32];         // h of every block
+    float4 r[XDF_NSEG][32];         // phase-1 partials, slot 2 w + j
+    int seg_m[XS_CHUNK + 1][XDF_NSEG], seg_c0[XS_CHUNK + 1][XDF_NSEG], seg_c1[XS_CHUNK + 1][XDF_NSEG];
+    int red[XS_CHUNK + 1][XS_CHUNK][4], nred[XS_CHUNK + 1][XS_CHUNK];  // partial slots of each tile
+    int y_ready, published, abort;
+    unsigned long long mb[2];
+};
+
+template <int DIR>
+__device__ __forceinline__ int solo_nband(const XView& v, int it)
+{
+    if (it == 0) return 0;
+    const int J = chain_block<DIR>(v, it);
+    return DIR == 0 ? v.nb - 1 - J : J;
+}
+
+// Global tile of list entry g of iteration it (null if absent).
+template <int DIR>
+__device__ __forceinline__ const XTile* solo_tile(const XView& v, int it, int g)
+{
+    const int J = chain_block<DIR>(v, it);
+    if (g == 1) return v.G + J;
+    if (it == 0) return nullptr;
+    if (g == 0) return (DIR == 0 ? v.Q : v.P) + J;
+    if (g - 2 >= solo_nband<DIR>(v, it)) return nullptr;
+    return v.M + (DIR == 0 ? xdf_tile_index(v, J - 1 + g, J - 1) : xdf_tile_index(v, J + 1, J + 1 - g));
+}
+
+// Bulk copies of chunk ch of iteration it into ring half q & 1 (one thread).
+template <int DIR>
+__device__ void solo_issue(const XView& v, DfwTile* Tall, SoloS* ss, int q, int it, int ch)
+{
+    const int slot = q & 1, L = 2 + solo_nband<DIR>(v, it), n = min(XS_CHUNK, L - XS_CHUNK * ch);
+    DfwTile* T = Tall + slot * XS_CHUNK;
+    unsigned cnt = 0;
+    for (int k = 0; k < n; ++k) cnt += solo_tile<DIR>(v, it, XS_CHUNK * ch + k) ? 1u : 0u;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(&ss->mb[slot], cnt * (unsigned)sizeof(XTile));
+    for (int k = 0; k < n; ++k) {
+        const XTile* src = solo_tile<DIR>(v, it, XS_CHUNK * ch + k);
+        if (src) bulk_g2s(&T[k], src, (unsigned)sizeof(XTile), &ss->mb[slot]);
+    }
+}
+
+// the chunk after (it, ch)
+template <int DIR>
+__device__ __forceinline__ void solo_advance(const XView& v, int& it, int& ch)
+{
+    if (++ch * XS_CHUNK >= 2 + solo_nband<DIR>(v, it)) {
+        ch = 0;
+        ++it;
+    }
+}
+
+template <int DIR>
+__device__ void xsolo(const XView& v, DfwTile* Tall, SoloS* ss)
+{
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nb = v.nb;
+    const int lim = v.spin_limit;
+    if (tid == 0) {
+        ss->y_ready = -1;
+        ss->published = -1;
+        ss->abort = 0;
+        for (int n = 1; n <= XS_CHUNK; ++n) {
+            chain_segments(n, ss->seg_m[n], ss->seg_c0[n], ss->seg_c1[n]);
+            for (int k = 0; k < XS_CHUNK; ++k) {
+                int c = 0;
+                for (int s = 0; s < XDF_NSEG; ++s)
+                    if (ss->seg_m[n][s] == k && c < 4) ss->red[n][k][c++] = s;
+                ss->nred[n][k] = c;
+            }
+        }
+        mbar_init(&ss->mb[0], 1);
+        mbar_init(&ss->mb[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    for (int i = tid; i < nb * 32; i += blockDim.x) ss->h[i >> 5][i & 31] = dfw_pack(dfw_zero());
+    block_sync();
+
+    if (w == XDF_WARPS - 1) {
+        // ---- publisher: solution blocks and weight products to global memory
+        for (int it = 0; it < nb; ++it) {
+            if (!smem_wait_ge(&ss->y_ready, it, &ss->abort, lim, v.err, 0x620000 + it)) break;
+            const int J = chain_block<DIR>(v, it), n = 32 * J + lane;
+            const dfw xw = dfw_unpack(ss->xv[it % XDF_XR][lane]);
+            const df xm = df{xw.h, xw.l};
+            (DIR == 0 ? v.yh : v.ch)[n] = xm.h;
+            (DIR == 0 ? v.yl : v.cl)[n] = xm.l;
+            (DIR == 0 ? v.ye : v.ce)[n] = xw.e;
+            for (int c = 0; c < v.d; ++c) {
+                df e = df{0.f, 0.f};
+                if (DIR == 0) e = df{v.bh[(size_t)c * v.npad + n], v.bl[(size_t)c * v.npad + n]};
+                else if (n >= 1 && n <= v.N) e = df{v.ah[(size_t)c * v.npad + n - 1], v.al[(size_t)c * v.npad + n - 1]};
+                const df u = df_mul(xm, e);
+                (DIR == 0 ? v.uh : v.wh)[(size_t)c * v.npad + n] = u.h;
+                (DIR == 0 ? v.ul : v.wl)[(size_t)c * v.npad + n] = u.l;
+            }
+            __syncwarp();
+            if (lane == 0) vstore(&ss->published, it);
+            __syncwarp();
+        }
+        return;
+    }
+    if (w == XDF_WARPS - 2) return;
+
+    // ---- compute warps 0-5 (never leave the loop early; see xchain)
+    int qi = 0, ich = 0, q_issued = -1;  // warp 5 lane 0: next chunk to issue
+    if (w == 5 && lane == 0) {
+        for (int k = 0; k < 2 && qi < nb; ++k) {
+            solo_issue<DIR>(v, Tall, ss, k, qi, ich);
+            q_issued = k;
+            solo_advance<DIR>(v, qi, ich);
+        }
+    }
+    int q = 0;
+    for (int it = 0; it < nb; ++it) {
+        const int J = chain_block<DIR>(v, it), L = 2 + solo_nband<DIR>(v, it);
+        const int xp = (it + XDF_XR - 1) % XDF_XR;
+        for (int ch = 0; ch * XS_CHUNK < L; ++ch, ++q) {
+            const int slot = q & 1, n = min(XS_CHUNK, L - XS_CHUNK * ch);
+            DfwTile* T = Tall + slot * XS_CHUNK;
+            mbar_wait(&ss->mb[slot], (unsigned)(q >> 1), lim, v.err, &ss->abort, 0x630000 + it, false);
+            // phase 1
+            dfw x0 = dfw_zero();
+            if (it == 0 && w == 0) x0 = DIR == 0 ? tile_get(&T[1], lane, 0) : tile_get(&T[1], v.N - 32 * J, lane);
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int k = ss->seg_m[n][2 * w + j];
+                if (k < 0) continue;
+                const int g = XS_CHUNK * ch + k;
+                dfw p = dfw_zero();
+                if (it >= 1 && solo_tile<DIR>(v, it, g)) {
+                    const float4* xv = g == 1 ? ss->h[J] : ss->xv[xp];
+                    const int c0 = ss->seg_c0[n][2 * w + j], c1 = ss->seg_c1[n][2 * w + j];
+                    p = DIR == 0 ? dot_seg<false>(&T[k], lane, xv, c0, c1) : dot_seg<true>(&T[k], lane, xv, c0, c1);
+                }
+                ss->r[2 * w + j][lane] = dfw_pack(p);
+            }
+            compute_sync();
+            // phase 2: reductions
+            if (ch == 0 && w == 0) {
+                smem_wait_ge(&ss->published, it - XDF_XR, &ss->abort, lim, v.err, 0x640000 + it);
+                dfw x = x0;
+                if (it >= 1) {
+                    dfw t[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) t[i] = dfw_zero();
+                    int c = 0;
+                    for (int k = 0; k < 2; ++k)
+                        for (int i = 0; i < ss->nred[n][k]; ++i) {
+                            const dfw pv = dfw_unpack(ss->r[ss->red[n][k][i]][lane]);
+#pragma unroll
+                            for (int u = 0; u < 8; ++u)
+                                if (u == c) t[u] = pv;
+                            ++c;
+                        }
+                    x = dfw_sum8(t, c);
+                }
+                ss->xv[it % XDF_XR][lane] = dfw_pack(x);
+                __threadfence_block();
+                __syncwarp();
+                if (lane == 0) vstore(&ss->y_ready, it);
+                __syncwarp();
+            }
+            // band tile k of this chunk: reducer warp k - 1 in chunk 0, k otherwise
+            for (int k = (ch == 0 ? 2 : 0); k < n; ++k) {
+                if (w != (ch == 0 ? k - 1 : k)) continue;
+                const int g = XS_CHUNK * ch + k;
+                if (!solo_tile<DIR>(v, it, g)) continue;
+                const int tgt = DIR == 0 ? J - 1 + g : J + 1 - g;
+                dfw t[8];
+                t[0] = dfw_unpack(ss->h[tgt][lane]);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) t[1 + i] = i < ss->nred[n][k] ? dfw_unpack(ss->r[ss->red[n][k][i < 4 ? i : 0]][lane]) : dfw_zero();
+                t[5] = t[6] = t[7] = dfw_zero();
+                ss->h[tgt][lane] = dfw_pack(dfw_sum8(t, 1 + ss->nred[n][k]));
+            }
+            if (w == 5 && lane == 0 && qi < nb && !vload(&ss->abort)) {
+                solo_issue<DIR>(v, Tall, ss, q + 2, qi, ich);
+                q_issued = q + 2;
+                solo_advance<DIR>(v, qi, ich);
+            }
+            compute_sync();
+        }
+    }
+    // every issued bulk copy lands before the block's shared memory is released
+    if (w == 5 && lane == 0)
+        for (int sl = 0; sl < 2 && sl <= q_issued; ++sl) {
+            const int last = sl + ((q_issued - sl) / 2) * 2;
+            mbar_wait(&ss->mb[sl], (unsigned)(last >> 1), lim, v.err, &ss->abort, 0x658000 + sl, true);
+        }
+}
+
+__global__ void __launch_bounds__(XDF_THREADS, 1) xsolo_batch(const RepArgs* ra)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    DfwTile* T = reinterpret_cast<DfwTile*>(smem_raw);
+    SoloS* ss = reinterpret_cast<SoloS*>(smem_raw + XS_SLOTS * sizeof(DfwTile));
+    const XView& v = ra[blockIdx.y].xv;
+    if (v.xi_zero) return;
+    if (blockIdx.x == 0) xsolo<0>(v, T, ss);
+    else xsolo<1>(v, T, ss);
+}
+
+__global__ void __launch_bounds__(256) prep_batch(const RepArgs* ra) { prep_body(ra[blockIdx.z].xv); }
+
+__global__ void __launch_bounds__(256) table_batch(const RepArgs* ra)
+{
+    const XView& v = ra[blockIdx.z].xv;
+    if (v.xi_zero) return;
+    table_body(v, xdf_ntiles(v.nb, v.W, v.store));
+}
+
+__global__ void __launch_bounds__(256) blockops_batch(const RepArgs* ra)
+{
+    const XView& v = ra[blockIdx.z].xv;
+    if (v.xi_zero) return;
+    blockops_body(v);
+}
+
+__global__ void __launch_bounds__(256) band_batch(const RepArgs* ra)
+{
+    const XView& v = ra[blockIdx.z].xv;
+    if (v.xi_zero) return;
+    band_body(v);
+}
+
+__global__ void __launch_bounds__(256) finalize_batch(const RepArgs* ra)
+{
+    const RepArgs& a = ra[blockIdx.z];
+    finalize_body(a.xv, a.fo);
+}
+
 }  // namespace
 
 int xdf_prep_blocks(int npad) { return min(152, (npad + 255) / 256); }
@@ -1189,7 +1460,7 @@ size_t xdf_recursion_smem(int W)
     return tab_off + 256 * sizeof(float2);
 }
 
-static size_t band_smem(int W) { return W * (sizeof(DfwTile) + sizeof(WeightSmem)) + W * 32 * sizeof(DVAcc); }
+static size_t band_smem(int nw) { return nw * (sizeof(DfwTile) + sizeof(WeightSmem) + 32 * sizeof(DVAcc)); }
 static size_t blockops_smem() { return 4 * sizeof(DfwTile); }
 
 cudaError_t xdf_launch_forward(const XView& v, cudaStream_t st, ProfMarks* pm)
@@ -1209,7 +1480,7 @@ cudaError_t xdf_launch_forward(const XView& v, cudaStream_t st, ProfMarks* pm)
             e = cudaFuncSetAttribute(xdf_recursion_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)xdf_recursion_smem(XDF_MAXW));
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(xdf_band_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)band_smem(XDF_MAXW));
+            e = cudaFuncSetAttribute(xdf_band_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)band_smem(8));
         if (e != cudaSuccess) return e;
         attrs = true;
     }
@@ -1259,4 +1530,28 @@ cudaError_t xdf_upload_table(float2* dev_table, cudaStream_t st)
         ready = true;
     }
     return cudaMemcpyAsync(dev_table, host_tab, sizeof(host_tab), cudaMemcpyHostToDevice, st);
+}
+
+size_t xsolo_smem() { return XS_SLOTS * sizeof(DfwTile) + sizeof(SoloS); }
+
+cudaError_t batch_launch_exchange(const RepArgs* ra, const BatchGrid& g, cudaStream_t st)
+{
+    static bool attrs = false;
+    cudaError_t e;
+    if (!attrs) {
+        e = cudaFuncSetAttribute(xsolo_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsolo_smem());
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(band_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)band_smem(8));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(blockops_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)blockops_smem());
+        if (e != cudaSuccess) return e;
+        attrs = true;
+    }
+    prep_batch<<<dim3(g.gx_prep, 1, g.R), 256, 0, st>>>(ra);
+    table_batch<<<dim3(g.gx_table, 1, g.R), 256, 0, st>>>(ra);
+    blockops_batch<<<dim3(g.nb_max, 1, g.R), 256, blockops_smem(), st>>>(ra);
+    xsolo_batch<<<dim3(2, g.R), XDF_THREADS, xsolo_smem(), st>>>(ra);
+    band_batch<<<dim3(g.nb_max, 2, g.R), 256, band_smem(8), st>>>(ra);
+    finalize_batch<<<dim3(g.gx_fin, 1, g.R), 256, 0, st>>>(ra);
+    return cudaGetLastError();
 }

@@ -94,3 +94,38 @@ def test_workspace_scales_quadratically_in_store_mode(pkg):
     assert 14 < b / a < 18
     c, d = ws(10000, pkg.TABLE_RECOMPUTE), ws(40000, pkg.TABLE_RECOMPUTE)
     assert d / c < 5 and d < 0.02 * b
+
+
+def test_batch_create_rejects_bad_arguments(pkg):
+    bad = [([0, 5], [1.0, 1.0], [1.0, 1.0]), ([2048, 5], [1.0, 1.0], [1.0, 1.0]),
+           ([4, 5], [0.0, 1.0], [1.0, 1.0]), ([4, 5], [1.0, 1.0], [1.0, 1.5]),
+           ([4, 5], [1.0, 1.0], [-0.2, 1.0])]
+    for Ns, betas, xis in bad:
+        with pytest.raises(pkg.PimdError) as ei:
+            pkg.pimd_batch_create(Ns, 4, 2, betas, xis, 1.0, 0.0, 0.5)
+        assert ei.value.status == pkg.PIMD_EINVAL
+
+
+def test_batch_layout_and_workspace_host_logic(pkg):
+    Ns = [1, 31, 32, 33, 500]
+    P, d = 8, 2
+    h = pkg.pimd_batch_create(Ns, P, d, [1.0, 2.0, 3.0, 4.0, 1.0], [1.0, 0.0, 0.5, 1.0, 1.0], 1.0, 3.0, 0.5)
+    try:
+        off = pkg.pimd_batch_layout(h, len(Ns))
+        pads = [(n + 31) // 32 * 32 for n in Ns]
+        assert off[0] == 0
+        assert [off[i + 1] - off[i] for i in range(len(Ns))] == [P * d * n for n in pads]
+        small = pkg.pimd_batch_workspace_bytes(h)
+        cfg = pkg.pimd_default_config()
+        cfg.nhc_len = 0
+        with pytest.raises(pkg.PimdError):
+            pkg.pimd_batch_configure(h, cfg)
+    finally:
+        pkg.pimd_batch_destroy(h)
+    h = pkg.pimd_batch_create(Ns + [2047], P, d, [1.0] * 6, [1.0] * 6, 1.0, 3.0, 0.5)
+    try:
+        big = pkg.pimd_batch_workspace_bytes(h)
+        # the stored factor table of the 2047-particle replica alone is ~64*65/2 tiles of 12 KB
+        assert big > small + 64 * 65 // 2 * 12288
+    finally:
+        pkg.pimd_batch_destroy(h)
