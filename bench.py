@@ -35,8 +35,8 @@ FP32_TFLOPS_DERIVED = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FMA/clk x 2
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="gauss1600")
     ap.add_argument("--no-extra", action="store_true", help="skip the N=10000 line item and the CPU baseline")
@@ -102,7 +102,7 @@ class ClockSampler:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -158,7 +158,7 @@ def kernel_work(name, w):
     hbm_src = "of measured" if hbm else "of fallback"
     hbm = hbm or 6800.0
     dof = N * P * d
-    if name == "exch_recursion":
+    if name in ("exch_recursion", "batch_exch_recursion"):
         # forward and backward passes: per term one multiply-add for the
         # recursion and d for the weighted endpoint sums, FP64-accurate
         flops = 2 * T * (1 + d) * 2
@@ -167,17 +167,64 @@ def kernel_work(name, w):
         # per term: d differences, d squares, one scale -> 3d+1 flops, plus one exp
         flops = T * (3 * d + 2)
         return "alu", flops / 1e12, "TFLOP/s", FP64_NOMINAL_TFLOPS, "FP64 nominal (recipe)"
-    if name == "pair":
+    if name in ("pair", "batch_pair"):
         pairs = P * N * N
         flops = pairs * (3 * d + 2 * d + 2)
         return "alu", flops / 1e12, "TFLOP/s", FP32_TFLOPS_DERIVED, "FP32 derived (152 SM x 128 FMA x 2.07 GHz)"
-    if name in ("md_pre", "md_post"):
+    if name in ("md_pre", "md_post", "batch_md_pre", "batch_md_post"):
         M = w["M"]
-        byts = dof * 8 * (3 + 2 * M) * 2 - dof * 8 * (1 if name == "md_post" else 0)
+        byts = dof * 8 * (3 + 2 * M) * 2 - dof * 8 * (1 if name.endswith("md_post") else 0)
         return "hbm", byts / 1e9, "GB/s", hbm, hbm_src
-    if name == "springs":
+    if name in ("springs", "batch_springs"):
         return "hbm", dof * 8 * 2 / 1e9, "GB/s", hbm, hbm_src
     return "hbm", dof * 8 / 1e9, "GB/s", hbm, hbm_src
+
+
+def run_batch(pkg, device, flush, stream, K, warmup):
+    """Batched 64-replica workload (uneven N, beta, xi) against the plain FP64
+    single-system form run replica by replica on the same GPU."""
+    import torch
+
+    from workloads import BATCH64, batch_replicas, beads, momenta
+
+    reps = batch_replicas()
+    cfg = BATCH64
+    P, d = cfg["P"], cfg["d"]
+    rs = [beads(r["N"], P, d, r["seed"]) for r in reps]
+    ps = [momenta(r["N"], P, d, r["beta"], r["seed"]) for r in reps]
+    B = pkg.Batch([r["N"] for r in reps], P, d, [r["beta"] for r in reps], [r["xi"] for r in reps],
+                  cfg["omega"], cfg["g"], cfg["s"], rs=rs, ps=ps, device=device, precision=pkg.PREC_MIXED,
+                  nhc_len=cfg["M"], dt=cfg["dt"], nhc_fp32=1)
+    B.step(max(warmup, 3))
+    torch.cuda.synchronize()
+    ms = timed_steps(B, K, flush, stream)
+    prof = pkg.pimd_batch_step_profiled(B.h, 5)
+    kernels = {n: round(t / 5 * 1e3, 2) for n, t in prof}
+    B.close()
+    R = len(reps)
+    batched = R * K / (ms / 1e3)
+    # plain FP64 single-system form (native FP64 exchange, FP64 everything), replica by replica
+    tot_ms, K1 = 0.0, 5
+    for q, r in enumerate(reps):
+        S = pkg.System(r["N"], P, d, r["beta"], cfg["omega"], cfg["g"], cfg["s"], r["xi"], r=rs[q], p=ps[q],
+                       device=device, precision=pkg.PREC_FP64, exchange_arith=pkg.XARITH_FP64,
+                       nhc_len=cfg["M"], dt=cfg["dt"])
+        S.step(2)
+        torch.cuda.synchronize()
+        tot_ms += timed_steps(S, K1, flush, stream) / K1
+        S.close()
+    plain = R / (tot_ms / 1e3)
+    return {"value": round(batched, 1), "unit": "replica-steps/s", "steps": K, "ms_per_step": round(ms / K, 4),
+            "kernels_us_per_step": kernels,
+            "plain_fp64_single": {"value": round(plain, 1), "unit": "replica-steps/s",
+                                  "ms_per_replica_step": round(tot_ms / R, 4),
+                                  "form": "one System per replica, FP64 pairs/springs/thermostat, "
+                                          "native FP64 exchange, graph-replayed steps"},
+            "batched_over_plain": round(batched / plain, 2),
+            "config": {"R": R, "N": "U{32..512} seed 4", "sum_N": sum(r["N"] for r in reps), "P": P, "d": d,
+                       "beta": "{1,2,3,4}[r mod 4]", "xi": "{0,...,1}[(r div 4) mod 6]", "g": cfg["g"],
+                       "s": cfg["s"], "precision": "fp32 pairs/springs/thermostat, f64-accurate exchange "
+                       "and estimators", "graph": "one CUDA graph per batched step"}}
 
 
 # --------------------------------------------------------------------------
@@ -239,7 +286,8 @@ def run_ours(args):
     value = ws * args.steps / (ms_max / 1e3)
 
     # per-kernel times (eager steps with events between kernels) -> roofline
-    prof = pkg.pimd_step_profiled(S.h, args.steps)
+    K_prof = min(args.steps, 200)
+    prof = pkg.pimd_step_profiled(S.h, K_prof)
     per = {}
     for name, t in prof:
         per.setdefault(name, [0.0, 0])
@@ -247,10 +295,10 @@ def run_ours(args):
         per[name][1] += 1
     n_kernels = len(prof)
     dom = max(per, key=lambda k: per[k][0])
-    avg_ms = per[dom][0] / (per[dom][1] * args.steps)
+    avg_ms = per[dom][0] / (per[dom][1] * K_prof)
     bound, work, unit, peak, peak_src = kernel_work(dom, w)
     achieved = work / (avg_ms / 1e3)
-    kernels = {k: round(v[0] / args.steps * 1e3, 2) for k, v in sorted(per.items(), key=lambda x: -x[1][0])}
+    kernels = {k: round(v[0] / K_prof * 1e3, 2) for k, v in sorted(per.items(), key=lambda x: -x[1][0])}
 
     # end to end through the C ABI with host buffers (pinned), each step:
     # H2D of the full state, one step, D2H of the estimators
@@ -284,6 +332,7 @@ def run_ours(args):
                                "config": {"N": 10000, "P": 32, "d": 2, "beta": 3.0, "xi": 1.0, "g": 0.0,
                                           "precision": "fp64 exchange + fp32 springs"}}
         S2.close()
+        extra["batch64"] = run_batch(pkg, device, flush, stream, max(10, min(args.steps // 4, 50)), args.warmup)
 
     cpu = None
     if not args.no_extra and rank == 0 and ws == 1:

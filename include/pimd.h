@@ -83,6 +83,8 @@ typedef struct {
     int exch_band;      /* look-ahead band width W of the double-float recursion, 2..5
                            (0 = default 4): the chain block adds the W-2 tiles next to the
                            diagonal itself, helper blocks the rest */
+    int nhc_fp32;       /* 1: thermostat chain arithmetic in FP32 (state stays FP64, the
+                           momentum scaling is applied in FP64); 0: FP64 (default)        */
 } pimd_config;
 
 enum { PIMD_XARITH_DF = 0, PIMD_XARITH_FP64 = 1 };

@@ -48,7 +48,8 @@ class Config(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("nhc_len", ctypes.c_int), ("nhc_Q", ctypes.c_double),
                 ("mass", ctypes.c_double), ("precision", ctypes.c_int), ("amp_convention", ctypes.c_int),
                 ("table_mode", ctypes.c_int), ("thermostat", ctypes.c_int), ("helper_ctas", ctypes.c_int),
-                ("spin_limit", ctypes.c_int), ("exchange_arith", ctypes.c_int), ("exch_band", ctypes.c_int)]
+                ("spin_limit", ctypes.c_int), ("exchange_arith", ctypes.c_int), ("exch_band", ctypes.c_int),
+                ("nhc_fp32", ctypes.c_int)]
 
 
 class Buffers(ctypes.Structure):

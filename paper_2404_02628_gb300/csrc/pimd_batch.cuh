@@ -26,7 +26,7 @@ struct BatchGrid {
 
 int batch_md_blocks(int nmax, int P, int d);
 cudaError_t batch_launch_md(const RepArgs* ra, const BatchGrid& g, bool pre, cudaStream_t st);
-cudaError_t batch_launch_forces(const RepArgs* ra, const BatchGrid& g, cudaStream_t st);
-cudaError_t batch_launch_exchange(const RepArgs* ra, const BatchGrid& g, cudaStream_t st);
+cudaError_t batch_launch_forces(const RepArgs* ra, const BatchGrid& g, cudaStream_t st, ProfMarks* pm);
+cudaError_t batch_launch_exchange(const RepArgs* ra, const BatchGrid& g, cudaStream_t st, ProfMarks* pm);
 cudaError_t batch_launch_scalars(const RepArgs* ra, const BatchGrid& g, cudaStream_t st);
 size_t xsolo_smem();

@@ -17,6 +17,22 @@ __device__ __forceinline__ float ex2_approx(float x)
     return y;
 }
 
+// double -> float by truncating the significand (round toward zero) with
+// integer operations: on GB300 the hardware F2F.F32.F64 conversion costs
+// about twice an FP64 FMA, the bit manipulation a few integer-pipe ops.
+// Relative error below 2^-23; values below the float normal range give a
+// signed zero and values above it (and NaN) an infinity of the same sign.
+__device__ __forceinline__ float d2f_trunc(double x)
+{
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const int e = (int)((hi >> 20) & 0x7FFu) - 1023 + 127;
+    const unsigned s = hi & 0x80000000u;
+    unsigned b = s | ((unsigned)e << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+    b = e <= 0 ? s : b;
+    b = e >= 255 ? (s | 0x7F800000u) : b;
+    return __uint_as_float(b);
+}
+
 // ---------------------------------------------------------------------------
 // (a1) Internal ring-polymer springs (Sec. III interior-bead formula and the
 // within-particle half of the exterior-bead formulas): F_l^j = -k (2 r^j -
@@ -35,8 +51,8 @@ __device__ __forceinline__ void springs_body(const BeadView& b, const ForceParam
             const double xp = (j < b.P - 1) ? b.r[o + (size_t)b.d * b.ld] : x;
             double fo;
             if (fp.mixed) {
-                const float xf = (float)x;
-                fo = (double)(-(float)fp.ks * ((xf - (float)xm) + (xf - (float)xp)));
+                const float xf = d2f_trunc(x);
+                fo = (double)(-(float)fp.ks * ((xf - d2f_trunc(xm)) + (xf - d2f_trunc(xp))));
             } else {
                 fo = -fp.ks * ((x - xm) + (x - xp));
             }
@@ -162,7 +178,7 @@ __device__ __forceinline__ void pair_body_f32(const BeadView& b, const ForcePara
             float* sxf = reinterpret_cast<float*>(&sx[0][0]);
 #pragma unroll
             for (int c = 0; c < D; ++c)
-                sxf[c * PAIR_T + threadIdx.x] = (k < b.N) ? -(float)rs[(size_t)c * b.ld + k] * sc : -1.0e18f;
+                sxf[c * PAIR_T + threadIdx.x] = (k < b.N) ? -d2f_trunc(rs[(size_t)c * b.ld + k]) * sc : -1.0e18f;
             __syncthreads();
 #pragma unroll 4
             for (int kk = 0; kk < PAIR_T / 2; ++kk) {
@@ -270,6 +286,50 @@ __device__ __forceinline__ void nhc_half_step(double& p, double (&eta)[M], doubl
     pe[M - 1] = fma(cg, G, pe[M - 1]);
 }
 
+// The same half step with the chain arithmetic in FP32 (mixed precision): the
+// chain state is read and written in FP64, the momentum is scaled in FP64 by
+// the FP32 factor.  e^x by the MUFU exp2 with the argument scaled by log2(e).
+template <int M>
+__device__ __forceinline__ void nhc_half_step_f32(double& p, double (&eta)[M], double (&pe)[M], float inv_m,
+                                                  float inv_Q, float kT, float tau)
+{
+    const float L2E = 1.4426950408889634f;
+    const float ca = -0.25f * tau * inv_Q * L2E, cg = 0.5f * tau, ce = tau * inv_Q;
+    float q[M], e[M];
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        q[k] = d2f_trunc(pe[k]);
+        e[k] = d2f_trunc(eta[k]);
+    }
+    float pf = d2f_trunc(p);
+    float G = ((M >= 2) ? q[M - 2] * q[M - 2] * inv_Q : pf * pf * inv_m) - kT;
+    q[M - 1] = fmaf(cg, G, q[M - 1]);
+#pragma unroll
+    for (int k = M - 2; k >= 0; --k) {
+        const float a = ex2_approx(ca * q[k + 1]);
+        G = ((k == 0) ? pf * pf * inv_m : q[k - 1] * q[k - 1] * inv_Q) - kT;
+        q[k] = fmaf(q[k], a * a, cg * G * a);
+    }
+    const float sp = ex2_approx(-tau * inv_Q * L2E * q[0]);
+    p *= (double)sp;
+    pf = d2f_trunc(p);
+#pragma unroll
+    for (int k = 0; k < M; ++k) e[k] = fmaf(ce, q[k], e[k]);
+#pragma unroll
+    for (int k = 0; k <= M - 2; ++k) {
+        const float a = ex2_approx(ca * q[k + 1]);
+        G = ((k == 0) ? pf * pf * inv_m : q[k - 1] * q[k - 1] * inv_Q) - kT;
+        q[k] = fmaf(q[k], a * a, cg * G * a);
+    }
+    G = ((M >= 2) ? q[M - 2] * q[M - 2] * inv_Q : pf * pf * inv_m) - kT;
+    q[M - 1] = fmaf(cg, G, q[M - 1]);
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        pe[k] = (double)q[k];
+        eta[k] = (double)e[k];
+    }
+}
+
 template <bool PRE, int M>
 __device__ __forceinline__ void md_body(const BeadView& b, const MDParams& mp)
 {
@@ -287,12 +347,22 @@ __device__ __forceinline__ void md_body(const BeadView& b, const MDParams& mp)
             }
         }
         if (PRE) {
-            if (mp.thermostat) nhc_half_step<M>(p, eta, pe, mp.inv_mass, mp.inv_Q, mp.kT, 0.5 * mp.dt);
+            if (mp.thermostat) {
+                if (mp.nhc_fp32)
+                    nhc_half_step_f32<M>(p, eta, pe, mp.f_inv_mass, mp.f_inv_Q, mp.f_kT, mp.f_half_dt);
+                else
+                    nhc_half_step<M>(p, eta, pe, mp.inv_mass, mp.inv_Q, mp.kT, 0.5 * mp.dt);
+            }
             p += 0.5 * mp.dt * b.f[o];
             b.r[o] = fma(mp.dt * mp.inv_mass, p, b.r[o]);
         } else {
             p += 0.5 * mp.dt * b.f[o];
-            if (mp.thermostat) nhc_half_step<M>(p, eta, pe, mp.inv_mass, mp.inv_Q, mp.kT, 0.5 * mp.dt);
+            if (mp.thermostat) {
+                if (mp.nhc_fp32)
+                    nhc_half_step_f32<M>(p, eta, pe, mp.f_inv_mass, mp.f_inv_Q, mp.f_kT, mp.f_half_dt);
+                else
+                    nhc_half_step<M>(p, eta, pe, mp.inv_mass, mp.inv_Q, mp.kT, 0.5 * mp.dt);
+            }
         }
         b.p[o] = p;
         if (mp.thermostat) {
@@ -528,11 +598,12 @@ cudaError_t batch_launch_md(const RepArgs* ra, const BatchGrid& g, bool pre, cud
     return cudaGetLastError();
 }
 
-cudaError_t batch_launch_forces(const RepArgs* ra, const BatchGrid& g, cudaStream_t st)
+cudaError_t batch_launch_forces(const RepArgs* ra, const BatchGrid& g, cudaStream_t st, ProfMarks* pm)
 {
     const int P = g.P, d = g.d;
     const bool mixed = g.mixed != 0;
     springs_batch<<<dim3(g.gx_spr, P, g.R), SPR_T, 0, st>>>(ra);
+    prof_mark(pm, "batch_springs", st);
     const dim3 grid(g.gx_pair, P, g.R);
     if (mixed) {
         if (d == 1) pair_batch<1, true><<<grid, PAIR_T, 0, st>>>(ra);
@@ -543,6 +614,7 @@ cudaError_t batch_launch_forces(const RepArgs* ra, const BatchGrid& g, cudaStrea
         else if (d == 2) pair_batch<2, false><<<grid, PAIR_T, 0, st>>>(ra);
         else pair_batch<3, false><<<grid, PAIR_T, 0, st>>>(ra);
     }
+    prof_mark(pm, "batch_pair", st);
     return cudaGetLastError();
 }
 

@@ -26,6 +26,8 @@ struct MDParams {
     double dt, mass, Q, kT;
     double inv_mass, inv_Q;   // 1/mass and 1/Q, formed on the host
     int thermostat;
+    int nhc_fp32;             // thermostat chain arithmetic in FP32
+    float f_inv_mass, f_inv_Q, f_kT, f_half_dt;  // FP32 copies for that mode
 };
 
 // Scalar slots of the per-step reduction (device array of doubles).

@@ -1534,7 +1534,7 @@ cudaError_t xdf_upload_table(float2* dev_table, cudaStream_t st)
 
 size_t xsolo_smem() { return XS_SLOTS * sizeof(DfwTile) + sizeof(SoloS); }
 
-cudaError_t batch_launch_exchange(const RepArgs* ra, const BatchGrid& g, cudaStream_t st)
+cudaError_t batch_launch_exchange(const RepArgs* ra, const BatchGrid& g, cudaStream_t st, ProfMarks* pm)
 {
     static bool attrs = false;
     cudaError_t e;
@@ -1548,10 +1548,16 @@ cudaError_t batch_launch_exchange(const RepArgs* ra, const BatchGrid& g, cudaStr
         attrs = true;
     }
     prep_batch<<<dim3(g.gx_prep, 1, g.R), 256, 0, st>>>(ra);
+    prof_mark(pm, "batch_exch_prep", st);
     table_batch<<<dim3(g.gx_table, 1, g.R), 256, 0, st>>>(ra);
+    prof_mark(pm, "batch_exch_table", st);
     blockops_batch<<<dim3(g.nb_max, 1, g.R), 256, blockops_smem(), st>>>(ra);
+    prof_mark(pm, "batch_exch_blockops", st);
     xsolo_batch<<<dim3(2, g.R), XDF_THREADS, xsolo_smem(), st>>>(ra);
+    prof_mark(pm, "batch_exch_recursion", st);
     band_batch<<<dim3(g.nb_max, 2, g.R), 256, band_smem(8), st>>>(ra);
+    prof_mark(pm, "batch_exch_band", st);
     finalize_batch<<<dim3(g.gx_fin, 1, g.R), 256, 0, st>>>(ra);
+    prof_mark(pm, "batch_exch_finalize", st);
     return cudaGetLastError();
 }

@@ -115,3 +115,21 @@ def test_batch_mixed_precision():
         Fo, _ = oracle.forces(rs[q], beta, xi, 1.0, amplitude(g, s), s)
         assert rel_inf(B.forces_array(q), Fo) < TOLMIX, q
     B.close()
+
+
+def test_batch_fp32_thermostat_tracks_fp64():
+    """nhc_fp32 (mixed mode): 20 steps stay within 1e-4 of the FP64 thermostat run."""
+    import paper_2404_02628_gb300 as pkg
+    P, d, g, s = 16, 2, 3.0, 0.5
+    reps = [(120, 1.0, 1.0), (60, 3.0, 0.4)]
+    A, _, _ = make_batch(reps, P, d, 1.0, g, s, 1030, precision=pkg.PREC_MIXED)
+    C, _, _ = make_batch(reps, P, d, 1.0, g, s, 1030, precision=pkg.PREC_MIXED, nhc_fp32=1)
+    A.step(20)
+    C.step(20)
+    ea, ec = A.estimators(), C.estimators()
+    for q in range(len(reps)):
+        assert rel_inf(C.momenta(q), A.momenta(q)) < 1e-4, q
+        assert rel_inf(C.positions(q), A.positions(q)) < 1e-6, q
+        assert abs(ec[q]["H_conserved"] - ea[q]["H_conserved"]) < 1e-5 * abs(ea[q]["H_conserved"]), q
+    A.close()
+    C.close()
