@@ -139,6 +139,29 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 # roofline bookkeeping: algorithmic work per launch of each kernel
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
+# ncu capture of the gauss1600 bench command (profiles/xdf_recursion_gauss1600_full.md),
+# valid only while the kernel's source file is unchanged (first 16 hex digits of its
+# SHA-256 at capture time); otherwise the roofline line reports traffic null.
+NCU_TRAFFIC = {
+    "exch_recursion": {"bytes": 17.16352e6 + 0.061696e6, "source": "paper_2404_02628_gb300/csrc/pimd_xdf.cu",
+                       "sha256_16": "34dee3ca47ec38a9"},
+}
+
+
+def ncu_traffic(kernel):
+    import hashlib
+
+    t = NCU_TRAFFIC.get(kernel)
+    if not t:
+        return None
+    try:
+        h = hashlib.sha256(open(os.path.join(ROOT, t["source"]), "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return t["bytes"] if h == t["sha256_16"] else None
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -351,7 +374,8 @@ def run_ours(args):
                        "g": w["g"], "s": w["s"], "amp": "g/(pi s^2)", "parallelism": "replicas x%d" % ws,
                        "l2": "flushed between timed steps (512 MB write)"},
             "roofline": {"kernel": dom, "bound": bound, "achieved": round(achieved, 6), "peak": peak,
-                         "unit": unit, "frac": round(achieved / peak, 6), "traffic": None,
+                         "unit": unit, "frac": round(achieved / peak, 6), "traffic": ncu_traffic(dom),
+                         "traffic_unit": "bytes per launch (ncu capture, same workload)",
                          "peak_source": peak_src, "avg_launch_ms": round(avg_ms, 5)},
             "kernels_us_per_step": kernels,
             "cpu_baseline": cpu,
