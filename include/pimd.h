@@ -249,7 +249,13 @@ void pimd_batch_destroy(pimd_batch_t b);
  */
 typedef struct pimd_vb* pimd_vb_t;
 
+/* The handle computes with the double-float recursion.  Its factor table is
+ * stored up to N = 16383 and recomputed where used above (so N = 40000 needs
+ * O(32 N) workspace instead of 12 N^2 / 2 bytes); pimd_vb_set_table_mode
+ * overrides that (PIMD_TABLE_STORE, PIMD_TABLE_RECOMPUTE, or -1 for the
+ * automatic choice) and changes pimd_vb_workspace_bytes accordingly. */
 pimd_status pimd_vb_create(int N, int P, int d, double beta, double xi, pimd_vb_t* out);
+pimd_status pimd_vb_set_table_mode(pimd_vb_t h, int table_mode);
 pimd_status pimd_vb_workspace_bytes(pimd_vb_t h, size_t* bytes);
 /* V_out: device double.  Saves the recursion state in work for backward. */
 pimd_status pimd_vb_forward(pimd_vb_t h, const double* r1, const double* rP, int ld,

@@ -19,7 +19,7 @@ __all__ = [
     "pimd_forces", "pimd_exchange_forces", "pimd_interaction_forces", "pimd_step", "pimd_step_eager",
     "pimd_estimators", "pimd_state_bytes", "pimd_get_state", "pimd_set_state", "pimd_sync",
     "pimd_last_error", "pimd_global_error", "pimd_destroy", "pimd_vb_create", "pimd_vb_workspace_bytes",
-    "pimd_vb_forward", "pimd_vb_backward", "pimd_vb_destroy", "pimd_step_profiled",
+    "pimd_vb_forward", "pimd_vb_backward", "pimd_vb_destroy", "pimd_vb_set_table_mode", "pimd_step_profiled",
     "pimd_profile_slot_name", "pimd_vb_forward_noalloc", "System",
     "pimd_batch_create", "pimd_batch_configure", "pimd_batch_layout", "pimd_batch_workspace_bytes",
     "pimd_batch_bind", "pimd_batch_forces", "pimd_batch_capture_graph", "pimd_batch_step",
@@ -99,6 +99,7 @@ _SIGS = {
     "pimd_destroy": ([_vp], None),
     "pimd_vb_create": ([ctypes.c_int] * 3 + [ctypes.c_double] * 2 + [ctypes.POINTER(_vp)], ctypes.c_int),
     "pimd_vb_workspace_bytes": ([_vp, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "pimd_vb_set_table_mode": ([_vp, ctypes.c_int], ctypes.c_int),
     "pimd_vb_forward": ([_vp, _vp, _vp, ctypes.c_int, _vp, ctypes.c_size_t, _vp, _vp], ctypes.c_int),
     "pimd_vb_backward": ([_vp, _vp, _vp, ctypes.c_int, _vp, ctypes.c_size_t, _vp, _vp, _vp, _vp], ctypes.c_int),
     "pimd_vb_destroy": ([_vp], None),
@@ -272,6 +273,10 @@ def pimd_vb_create(N, P, d, beta, xi):
     h = _vp()
     _check(lib().pimd_vb_create(N, P, d, beta, xi, ctypes.byref(h)))
     return h
+
+
+def pimd_vb_set_table_mode(h, mode):
+    return _check(lib().pimd_vb_set_table_mode(h, mode))
 
 
 def pimd_vb_workspace_bytes(h):

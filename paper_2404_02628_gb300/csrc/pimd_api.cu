@@ -236,10 +236,22 @@ struct pimd_vb {
     int N, P, d;
     double beta, xi;
     int n_help;
+    int store;       // 1: factor table stored (12 bytes per term), 0: recomputed where used
     Layout L;
-    ExchLayout ex;
+    XLayout xl;
     size_t off_fin;
 };
+
+// Automatic table mode of the exchange-potential handle: store the N(N+1)/2
+// factors up to N = 16383 (about 1.6 GB), recompute them above.
+constexpr int VB_STORE_MAX_N = 16383;
+
+static void vb_layout(pimd_vb* h)
+{
+    h->L = Layout();
+    xdf_layout(h->L, h->xl, h->N, EX_STREAMS, 4, h->store);
+    h->off_fin = h->L.add((size_t)xdf_finalize_blocks(h->N) * sizeof(double));
+}
 
 static pimd_status fail(pimd_t c, pimd_status s, const std::string& m)
 {
@@ -847,9 +859,20 @@ extern "C" pimd_status pimd_vb_create(int N, int P, int d, double beta, double x
     pimd_config cfg;
     pimd_default_config(&cfg);
     h->n_help = default_helpers(cfg);
-    exch_layout(h->L, h->ex, N, EX_STREAMS, 1);
-    h->off_fin = h->L.add((size_t)exch_finalize_blocks(N) * sizeof(double));
+    h->store = N <= VB_STORE_MAX_N;
+    vb_layout(h);
     *out = h;
+    return PIMD_OK;
+}
+
+extern "C" pimd_status pimd_vb_set_table_mode(pimd_vb_t h, int table_mode)
+{
+    if (!h) return fail(nullptr, PIMD_EINVAL, "pimd_vb_set_table_mode: NULL handle");
+    if (table_mode == PIMD_TABLE_STORE) h->store = 1;
+    else if (table_mode == PIMD_TABLE_RECOMPUTE) h->store = 0;
+    else if (table_mode == -1) h->store = h->N <= VB_STORE_MAX_N;
+    else return fail(nullptr, PIMD_EINVAL, "pimd_vb_set_table_mode: unknown mode");
+    vb_layout(h);
     return PIMD_OK;
 }
 
@@ -876,10 +899,12 @@ extern "C" pimd_status pimd_vb_forward(pimd_vb_t h, const double* r1, const doub
     if (s != PIMD_OK) return s;
     if (!V_out) return fail(nullptr, PIMD_EINVAL, "pimd_vb_forward: V_out is NULL");
     cudaStream_t st = (cudaStream_t)stream;
-    ExchView v = exch_view((char*)work, h->ex, h->N, h->P, h->d, h->beta, h->xi, EX_STREAMS, 1, rP, r1, ld, ld, 0, h->n_help);
+    XView v = xdf_view((char*)work, h->xl, h->N, h->P, h->d, h->beta, h->xi, EX_STREAMS, 4, h->store, rP, r1, ld, ld, 0,
+                       h->n_help);
     cudaError_t e = cudaMemsetAsync(v.err, 0, sizeof(int), st);
-    if (e == cudaSuccess) e = exch_launch_forward(v, st, 1);
-    if (e == cudaSuccess) e = exch_launch_vb_value(v, exch_prep_blocks(h->N), V_out, st);
+    if (e == cudaSuccess) e = xdf_upload_table((float2*)v.tab, st);
+    if (e == cudaSuccess) e = xdf_launch_forward(v, st, nullptr);
+    if (e == cudaSuccess) e = xdf_launch_vb_value(v, V_out, st);
     if (e != cudaSuccess) return fail(nullptr, PIMD_ECUDA, std::string("pimd_vb_forward: ") + cudaGetErrorString(e));
     return PIMD_OK;
 }
@@ -891,7 +916,8 @@ extern "C" pimd_status pimd_vb_backward(pimd_vb_t h, const double* r1, const dou
     if (s != PIMD_OK) return s;
     if (!gV || !g_r1 || !g_rP) return fail(nullptr, PIMD_EINVAL, "pimd_vb_backward: NULL output");
     cudaStream_t st = (cudaStream_t)stream;
-    ExchView v = exch_view((char*)work, h->ex, h->N, h->P, h->d, h->beta, h->xi, EX_STREAMS, 1, rP, r1, ld, ld, 0, h->n_help);
+    XView v = xdf_view((char*)work, h->xl, h->N, h->P, h->d, h->beta, h->xi, EX_STREAMS, 4, h->store, rP, r1, ld, ld, 0,
+                       h->n_help);
     FinalizeOut o;
     memset(&o, 0, sizeof(o));
     o.g1 = g_r1;
@@ -900,7 +926,7 @@ extern "C" pimd_status pimd_vb_backward(pimd_vb_t h, const double* r1, const dou
     o.gscale = gV;
     o.P = h->P;
     o.part = (double*)((char*)work + h->off_fin);
-    cudaError_t e = exch_launch_adjoint(v, o, exch_finalize_blocks(h->N), st);
+    cudaError_t e = xdf_launch_adjoint(v, o, st, nullptr);
     if (e != cudaSuccess) return fail(nullptr, PIMD_ECUDA, std::string("pimd_vb_backward: ") + cudaGetErrorString(e));
     return PIMD_OK;
 }

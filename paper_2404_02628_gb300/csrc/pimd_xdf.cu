@@ -1448,6 +1448,21 @@ __global__ void __launch_bounds__(256) finalize_batch(const RepArgs* ra)
     finalize_body(a.xv, a.fo);
 }
 
+// V_ends = V_xi - sum E_int = (sum_l g(l, l+1) - ln W_N)/beta with
+// ln W_N = N ln xi + ln y[N] (xi = 0: the diagonal chain), from the prep
+// partial sums and the forward solution (Sec. III).
+__global__ void xdf_vb_value_kernel(XView v, int nprep, double* V_out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double gl = 0.0, l0 = 0.0;
+    for (int i = 0; i < nprep; ++i) {
+        gl += v.lsum[2 * i];
+        l0 += v.lsum[2 * i + 1];
+    }
+    const double lam = v.xi_zero ? l0 : v.N * v.log_xi + dfw_log(xget(v.yh, v.yl, v.ye, v.N));
+    *V_out = (gl - lam) / v.beta;
+}
+
 }  // namespace
 
 int xdf_prep_blocks(int npad) { return min(152, (npad + 255) / 256); }
@@ -1559,5 +1574,11 @@ cudaError_t batch_launch_exchange(const RepArgs* ra, const BatchGrid& g, cudaStr
     prof_mark(pm, "batch_exch_band", st);
     finalize_batch<<<dim3(g.gx_fin, 1, g.R), 256, 0, st>>>(ra);
     prof_mark(pm, "batch_exch_finalize", st);
+    return cudaGetLastError();
+}
+
+cudaError_t xdf_launch_vb_value(const XView& v, double* V_out, cudaStream_t st)
+{
+    xdf_vb_value_kernel<<<1, 32, 0, st>>>(v, xdf_prep_blocks(v.npad), V_out);
     return cudaGetLastError();
 }

@@ -91,3 +91,4 @@ size_t xdf_recursion_smem(int W);
 cudaError_t xdf_upload_table(float2* dev_table, cudaStream_t st);
 cudaError_t xdf_launch_forward(const XView& v, cudaStream_t st, ProfMarks* pm);
 cudaError_t xdf_launch_adjoint(const XView& v, const FinalizeOut& o, cudaStream_t st, ProfMarks* pm);
+cudaError_t xdf_launch_vb_value(const XView& v, double* V_out, cudaStream_t st);

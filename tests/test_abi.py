@@ -129,3 +129,26 @@ def test_batch_layout_and_workspace_host_logic(pkg):
         assert big > small + 64 * 65 // 2 * 12288
     finally:
         pkg.pimd_batch_destroy(h)
+
+
+def test_vb_table_mode_and_workspace(pkg):
+    """pimd_vb: automatic store up to N = 16383, recompute above (O(N) workspace)."""
+    sizes = {}
+    for N in (10000, 16383, 16384, 20000, 30000, 40000):
+        h = pkg.pimd_vb_create(N, 32, 2, 3.0, 1.0)
+        try:
+            sizes[N] = pkg.pimd_vb_workspace_bytes(h)
+            if N == 10000:
+                pkg.pimd_vb_set_table_mode(h, pkg.TABLE_RECOMPUTE)
+                small = pkg.pimd_vb_workspace_bytes(h)
+                assert small < sizes[N] / 10
+                pkg.pimd_vb_set_table_mode(h, -1)
+                assert pkg.pimd_vb_workspace_bytes(h) == sizes[N]
+                with pytest.raises(pkg.PimdError):
+                    pkg.pimd_vb_set_table_mode(h, 7)
+        finally:
+            pkg.pimd_vb_destroy(h)
+    assert sizes[16383] > 12 * 16383 * 16384 // 2          # stored table
+    assert sizes[16384] < sizes[16383] / 20                 # recomputed
+    assert sizes[40000] < 12 * 40000 * 40001 // 2 // 50     # O(N): 127 MB against the 9.6 GB table
+    assert sizes[20000] < sizes[30000] < sizes[40000]
