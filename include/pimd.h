@@ -182,6 +182,17 @@ pimd_status pimd_set_state(pimd_t ctx, const void* host_blob, size_t bytes);
 pimd_status pimd_step_profiled(pimd_t ctx, int nsteps, double* ms_out, int max_slots, int* n_slots);
 const char* pimd_profile_slot_name(pimd_t ctx, int slot);
 
+/* Autotuner: times the force evaluation (r and p are not advanced) for every
+ * candidate launch shape -- the look-ahead band width W of the double-float
+ * recursion (those whose workspace fits the bound one) and the pair-kernel
+ * block of 64, 128 or 256 particles -- and keeps the fastest.  cache_path
+ * (nullable): a text file of "device problem|choice" lines; a hit skips the
+ * timing, a miss appends the new choice.  The step graph is re-captured on
+ * the next pimd_step.  Synchronises. */
+pimd_status pimd_autotune(pimd_t ctx, const char* cache_path);
+/* The current tuned values (host only). */
+pimd_status pimd_tuning(pimd_t ctx, int* exch_band, int* pair_block);
+
 /* Synchronises the bound stream and reports device-side errors. */
 pimd_status pimd_sync(pimd_t ctx);
 
@@ -236,6 +247,9 @@ pimd_status pimd_batch_step_profiled(pimd_batch_t b, int nsteps, double* ms_out,
 const char* pimd_batch_profile_slot_name(pimd_batch_t b, int slot);
 /* out: host array of R estimates (synchronises). */
 pimd_status pimd_batch_estimators(pimd_batch_t b, pimd_estimates* out);
+/* Autotuner of the batched step (as pimd_autotune): the pair-kernel block of
+ * 64, 128 or 256 particles, cached by device and (R, sum N, sum N^2, P, d). */
+pimd_status pimd_batch_autotune(pimd_batch_t b, const char* cache_path);
 pimd_status pimd_batch_sync(pimd_batch_t b);
 const char* pimd_batch_last_error(pimd_batch_t b);
 void pimd_batch_destroy(pimd_batch_t b);

@@ -25,6 +25,7 @@ __all__ = [
     "pimd_batch_bind", "pimd_batch_forces", "pimd_batch_capture_graph", "pimd_batch_step",
     "pimd_batch_step_eager", "pimd_batch_step_profiled", "pimd_batch_profile_slot_name",
     "pimd_batch_estimators", "pimd_batch_sync", "pimd_batch_last_error", "pimd_batch_destroy",
+    "pimd_batch_autotune", "pimd_autotune", "pimd_tuning",
 ]
 
 PIMD_OK, PIMD_EINVAL, PIMD_ENOMEM, PIMD_ECUDA, PIMD_ETIMEOUT, PIMD_ENONFINITE, PIMD_ESTATE = range(7)
@@ -123,6 +124,9 @@ _SIGS = {
     "pimd_batch_sync": ([_vp], ctypes.c_int),
     "pimd_batch_last_error": ([_vp], ctypes.c_char_p),
     "pimd_batch_destroy": ([_vp], None),
+    "pimd_autotune": ([_vp, ctypes.c_char_p], ctypes.c_int),
+    "pimd_tuning": ([_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "pimd_batch_autotune": ([_vp, ctypes.c_char_p], ctypes.c_int),
 }
 
 
@@ -377,6 +381,21 @@ def pimd_batch_destroy(h):
     lib().pimd_batch_destroy(h)
 
 
+def pimd_batch_autotune(h, cache_path=None):
+    return _bcheck(lib().pimd_batch_autotune(h, cache_path.encode() if cache_path else None), h)
+
+
+def pimd_autotune(h, cache_path=None):
+    return _check(lib().pimd_autotune(h, cache_path.encode() if cache_path else None), h)
+
+
+def pimd_tuning(h):
+    W = ctypes.c_int()
+    T = ctypes.c_int()
+    _check(lib().pimd_tuning(h, ctypes.byref(W), ctypes.byref(T)), h)
+    return {"exch_band": W.value, "pair_block": T.value}
+
+
 class Batch:
     """R replicas of uneven N, beta, xi in one set of torch-owned device arrays.
 
@@ -440,6 +459,9 @@ class Batch:
 
     def step(self, n=1, graph=True):
         (pimd_batch_step if graph else pimd_batch_step_eager)(self.h, n)
+
+    def autotune(self, cache_path=None):
+        pimd_batch_autotune(self.h, cache_path)
 
     def estimators(self):
         return pimd_batch_estimators(self.h, self.R)
@@ -530,6 +552,10 @@ class System:
 
     def step(self, n=1, graph=True):
         (pimd_step if graph else pimd_step_eager)(self.h, n)
+
+    def autotune(self, cache_path=None):
+        pimd_autotune(self.h, cache_path)
+        return pimd_tuning(self.h)
 
     def estimators(self):
         return pimd_estimators(self.h)

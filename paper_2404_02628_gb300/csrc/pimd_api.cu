@@ -224,6 +224,7 @@ struct pimd_ctx {
     bool use_df = true;
     size_t off_spr, off_pair, off_fin, off_md, off_sc, off_flag;
     int n_help;
+    int pair_t = 128;  // pair-kernel block size (pimd_autotune)
     ExchView xv;
     XView xd;
     BeadView bv;
@@ -341,7 +342,7 @@ static void ctx_layout(pimd_ctx* c)
     if (c->use_df) xdf_layout(c->L, c->xl, c->N, EX_STREAMS, cfg_band(c->cfg), c->cfg.table_mode == PIMD_TABLE_STORE);
     else exch_layout(c->L, c->ex, c->N, EX_STREAMS, c->cfg.table_mode == PIMD_TABLE_STORE);
     c->off_spr = c->L.add((size_t)springs_grid_x(c->N) * c->P * sizeof(double));
-    c->off_pair = c->L.add((size_t)pair_grid_x(c->N) * c->P * 2 * sizeof(double));
+    c->off_pair = c->L.add((size_t)pair_grid_x(c->N, PAIR_T_MIN) * c->P * 2 * sizeof(double));
     c->off_fin = c->L.add((size_t)exch_finalize_blocks(c->N) * sizeof(double));
     c->off_md = c->L.add((size_t)md_blocks(c->N, c->P, c->d) * 2 * sizeof(double));
     c->off_sc = c->L.add(SC_COUNT * sizeof(double));
@@ -355,6 +356,21 @@ extern "C" pimd_status pimd_workspace_bytes(pimd_t c, int n_pad, size_t* bytes)
     ctx_layout(c);
     *bytes = c->L.total;
     return PIMD_OK;
+}
+
+// Exchange views of the bound buffers under the current configuration.
+static void ctx_views(pimd_ctx* c)
+{
+    const pimd_buffers* b = &c->buf;
+    const int np = b->n_pad;
+    if (c->use_df)
+        c->xd = xdf_view((char*)b->work, c->xl, c->N, c->P, c->d, c->beta, c->xi, EX_STREAMS, cfg_band(c->cfg),
+                         c->cfg.table_mode == PIMD_TABLE_STORE, b->r + (size_t)(c->P - 1) * c->d * np, b->r, np, np,
+                         c->cfg.spin_limit, c->n_help);
+    else
+        c->xv = exch_view((char*)b->work, c->ex, c->N, c->P, c->d, c->beta, c->xi, EX_STREAMS,
+                          c->cfg.table_mode == PIMD_TABLE_STORE, b->r + (size_t)(c->P - 1) * c->d * np, b->r, np,
+                          np, c->cfg.spin_limit, c->n_help);
 }
 
 static pimd_status enqueue_forces(pimd_ctx* c, cudaStream_t st, double* f, bool exch, bool inter,
@@ -374,11 +390,11 @@ static pimd_status enqueue_forces(pimd_ctx* c, cudaStream_t st, double* f, bool 
         if (e != cudaSuccess) return cuda_fail(c, e, "zero kernel");
     }
     if (inter) {
-        e = launch_pair(c->bv, fp, f, (double*)(base + c->off_pair), st);
+        e = launch_pair(c->bv, fp, f, (double*)(base + c->off_pair), st, c->pair_t);
         prof_mark(pm, "pair", st);
         if (e != cudaSuccess) return cuda_fail(c, e, "pair kernel");
     } else {
-        e = launch_zero((double*)(base + c->off_pair), (size_t)pair_grid_x(c->N) * c->P * 2, st);
+        e = launch_zero((double*)(base + c->off_pair), (size_t)pair_grid_x(c->N, c->pair_t) * c->P * 2, st);
         if (e != cudaSuccess) return cuda_fail(c, e, "zero kernel");
     }
     if (exch) {
@@ -416,7 +432,7 @@ static pimd_status enqueue_scalars(pimd_ctx* c, cudaStream_t st)
     s.n_fin = c->use_df ? xdf_finalize_blocks(c->N) : exch_finalize_blocks(c->N);
     s.lam = c->use_df ? c->xd.lam : nullptr;
     s.pair = (double*)(base + c->off_pair);
-    s.n_pair = pair_grid_x(c->N) * c->P;
+    s.n_pair = pair_grid_x(c->N, c->pair_t) * c->P;
     s.fin = (double*)(base + c->off_fin);
     s.md = (double*)(base + c->off_md);
     s.n_md = md_blocks(c->N, c->P, c->d);
@@ -485,14 +501,7 @@ extern "C" pimd_status pimd_bind(pimd_t c, const pimd_buffers* b, void* stream)
     c->st = (cudaStream_t)stream;
     c->n_help = default_helpers(c->cfg);
     const int np = b->n_pad;
-    if (c->use_df)
-        c->xd = xdf_view((char*)b->work, c->xl, c->N, c->P, c->d, c->beta, c->xi, EX_STREAMS, cfg_band(c->cfg),
-                         c->cfg.table_mode == PIMD_TABLE_STORE, b->r + (size_t)(c->P - 1) * c->d * np, b->r, np, np,
-                         c->cfg.spin_limit, c->n_help);
-    else
-        c->xv = exch_view((char*)b->work, c->ex, c->N, c->P, c->d, c->beta, c->xi, EX_STREAMS,
-                          c->cfg.table_mode == PIMD_TABLE_STORE, b->r + (size_t)(c->P - 1) * c->d * np, b->r, np,
-                          np, c->cfg.spin_limit, c->n_help);
+    ctx_views(c);
     c->bv.N = c->N;
     c->bv.P = c->P;
     c->bv.d = c->d;
@@ -699,6 +708,159 @@ extern "C" pimd_status pimd_step_profiled(pimd_t c, int nsteps, double* ms_out, 
     c->steps += nsteps;
     *n_slots = nk < max_slots ? nk : max_slots;
     return check_device_error(c);
+}
+
+// ---------------------------------------------------------------------------
+// Autotuning: time the force evaluation (which leaves r and p untouched) for
+// each candidate launch shape, keep the fastest, and remember the choice in
+// an optional text cache keyed by device and problem.
+
+static std::string device_key()
+{
+    int dev = 0;
+    cudaDeviceProp pr;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&pr, dev) != cudaSuccess) return "unknown";
+    std::string n = pr.name;
+    for (char& ch : n)
+        if (ch == ' ' || ch == '|') ch = '_';
+    return n + "_sm" + std::to_string(pr.multiProcessorCount);
+}
+
+static bool cache_lookup(const char* path, const std::string& key, std::string& value)
+{
+    if (!path) return false;
+    FILE* f = fopen(path, "r");
+    if (!f) return false;
+    char line[1024];
+    bool found = false;
+    while (fgets(line, sizeof line, f)) {
+        std::string l(line);
+        while (!l.empty() && (l.back() == '\n' || l.back() == '\r')) l.pop_back();
+        const size_t bar = l.find('|');
+        if (bar != std::string::npos && l.substr(0, bar) == key) {
+            value = l.substr(bar + 1);  // the last entry for a key wins
+            found = true;
+        }
+    }
+    fclose(f);
+    return found;
+}
+
+static void cache_store(const char* path, const std::string& key, const std::string& value)
+{
+    if (!path) return;
+    FILE* f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%s|%s\n", key.c_str(), value.c_str());
+    fclose(f);
+}
+
+static int cache_field(const std::string& v, const char* name, int dflt)
+{
+    const std::string k = std::string(name) + "=";
+    const size_t p = v.find(k);
+    return p == std::string::npos ? dflt : atoi(v.c_str() + p + k.size());
+}
+
+template <class F>
+static double time_ms(cudaStream_t st, int reps, F&& enqueue)
+{
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return 1e30;
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return 1e30;
+    }
+    enqueue();  // warm
+    cudaEventRecord(a, st);
+    for (int i = 0; i < reps; ++i) enqueue();
+    cudaEventRecord(b, st);
+    float ms = 1e30f;
+    if (cudaEventSynchronize(b) == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return (double)ms / reps;
+}
+
+static void drop_graph(pimd_ctx* c)
+{
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+    c->graph_failed = false;
+}
+
+extern "C" pimd_status pimd_autotune(pimd_t c, const char* cache_path)
+{
+    if (!c) return fail(c, PIMD_EINVAL, "pimd_autotune: NULL handle");
+    if (!c->bound) return fail(c, PIMD_ESTATE, "pimd_autotune: not bound");
+    char kb[256];
+    snprintf(kb, sizeof kb, "single N=%d P=%d d=%d prec=%d arith=%d table=%d xi0=%d g0=%d", c->N, c->P, c->d,
+             c->cfg.precision, c->cfg.exchange_arith, c->cfg.table_mode, c->xi == 0.0, c->A == 0.0);
+    const std::string key = device_key() + " " + kb;
+    std::string val;
+    int bestW = cfg_band(c->cfg), bestT = c->pair_t;
+    if (cache_lookup(cache_path, key, val)) {
+        bestW = cache_field(val, "W", bestW);
+        bestT = cache_field(val, "pair_t", bestT);
+    } else {
+        std::vector<int> Ws, Ts;
+        if (c->use_df && c->xi != 0.0) {
+            for (int W = 2; W <= XDF_MAXW; ++W) {
+                Layout L;
+                XLayout xl;
+                xdf_layout(L, xl, c->N, EX_STREAMS, W, c->cfg.table_mode == PIMD_TABLE_STORE);
+                if (L.total <= c->L.total) Ws.push_back(W);  // candidate fits the bound workspace
+            }
+        }
+        if (Ws.empty()) Ws.push_back(bestW);
+        if (c->A != 0.0) Ts = {64, 128, 256};
+        else Ts = {c->pair_t};
+        double best = 1e30;
+        const int W0 = c->cfg.exch_band;
+        for (int W : Ws)
+            for (int T : Ts) {
+                c->cfg.exch_band = W;
+                c->pair_t = T;
+                ctx_views(c);
+                pimd_status st = PIMD_OK;
+                const double ms = time_ms(c->st, 5, [&] {
+                    if (st == PIMD_OK) st = enqueue_forces(c, c->st, c->buf.f, true, true);
+                });
+                if (st != PIMD_OK) return st;
+                if (ms < best) {
+                    best = ms;
+                    bestW = W;
+                    bestT = T;
+                }
+            }
+        c->cfg.exch_band = W0;
+        char vb[64];
+        snprintf(vb, sizeof vb, "W=%d;pair_t=%d", bestW, bestT);
+        cache_store(cache_path, key, vb);
+    }
+    if (bestW < 2 || bestW > XDF_MAXW || !pair_block_ok(bestT)) return fail(c, PIMD_EINVAL, "pimd_autotune: bad cache entry");
+    {
+        Layout L;
+        XLayout xl;
+        xdf_layout(L, xl, c->N, EX_STREAMS, bestW, c->cfg.table_mode == PIMD_TABLE_STORE);
+        if (c->use_df && L.total > c->L.total) bestW = cfg_band(c->cfg);  // cached choice does not fit this workspace
+    }
+    c->cfg.exch_band = bestW;
+    c->pair_t = bestT;
+    ctx_layout(c);
+    ctx_views(c);
+    drop_graph(c);
+    pimd_status s = enqueue_forces(c, c->st, c->buf.f, true, true);
+    if (s != PIMD_OK) return s;
+    return check_device_error(c);
+}
+
+extern "C" pimd_status pimd_tuning(pimd_t c, int* exch_band, int* pair_block)
+{
+    if (!c || !exch_band || !pair_block) return fail(c, PIMD_EINVAL, "pimd_tuning: NULL argument");
+    *exch_band = cfg_band(c->cfg);
+    *pair_block = c->pair_t;
+    return PIMD_OK;
 }
 
 extern "C" const char* pimd_profile_slot_name(pimd_t c, int slot)
@@ -1050,7 +1212,9 @@ static void batch_layout(pimd_batch* b, std::vector<XLayout>& xl, std::vector<si
     g.M = b->cfg.nhc_len;
     g.mixed = b->cfg.precision == PIMD_PREC_MIXED;
     g.gx_spr = springs_grid_x(nmax);
-    g.gx_pair = pair_grid_x(nmax);
+    if (!pair_block_ok(g.pair_t)) g.pair_t = 128;
+    g.gx_pair = pair_grid_x(nmax, g.pair_t);
+    g.gx_pair_max = pair_grid_x(nmax, PAIR_T_MIN);
     g.gx_md = batch_md_blocks((nmax + 31) / 32 * 32, b->P, b->d);
     g.gx_prep = xdf_prep_blocks(npmax);
     g.gx_fin = xdf_finalize_blocks(nmax);
@@ -1063,7 +1227,7 @@ static void batch_layout(pimd_batch* b, std::vector<XLayout>& xl, std::vector<si
         const int nb = (b->N[r] + 1 + 31) / 32;
         xdf_layout(b->L, xl[r], b->N[r], 1, nb, 1);
         offs[5 * r + 0] = b->L.add((size_t)g.gx_spr * b->P * sizeof(double));
-        offs[5 * r + 1] = b->L.add((size_t)g.gx_pair * b->P * 2 * sizeof(double));
+        offs[5 * r + 1] = b->L.add((size_t)g.gx_pair_max * b->P * 2 * sizeof(double));
         offs[5 * r + 2] = b->L.add((size_t)g.gx_fin * sizeof(double));
         offs[5 * r + 3] = b->L.add((size_t)g.gx_md * 2 * sizeof(double));
         offs[5 * r + 4] = b->L.add((size_t)g.gx_prep * 2 * sizeof(double));
@@ -1332,6 +1496,73 @@ extern "C" const char* pimd_batch_profile_slot_name(pimd_batch_t b, int slot)
 {
     if (!b || slot < 0 || slot >= 64 || !b->slot_names[slot]) return "";
     return b->slot_names[slot];
+}
+
+// Re-derives the grid-dependent fields of the replica arguments (after a
+// tuning change) and uploads them.
+static pimd_status batch_upload_args(pimd_batch* b)
+{
+    for (auto& a : b->args) a.ss.n_pair = b->grid.gx_pair * b->P;
+    cudaError_t e = cudaMemcpyAsync((char*)b->buf.work + b->off_args, b->args.data(), b->args.size() * sizeof(RepArgs),
+                                    cudaMemcpyHostToDevice, b->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+    return e == cudaSuccess ? PIMD_OK : bcuda(b, e, "batch argument upload");
+}
+
+static void batch_set_pair_t(pimd_batch* b, int T)
+{
+    int nmax = 0;
+    for (int n : b->N) nmax = std::max(nmax, n);
+    b->grid.pair_t = T;
+    b->grid.gx_pair = pair_grid_x(nmax, T);
+}
+
+extern "C" pimd_status pimd_batch_autotune(pimd_batch_t b, const char* cache_path)
+{
+    if (!b) return bfail(b, PIMD_EINVAL, "pimd_batch_autotune: NULL handle");
+    if (!b->bound) return bfail(b, PIMD_ESTATE, "pimd_batch_autotune: not bound");
+    long long sumN = 0, sumN2 = 0;
+    for (int n : b->N) {
+        sumN += n;
+        sumN2 += (long long)n * n;
+    }
+    char kb[256];
+    snprintf(kb, sizeof kb, "batch R=%d sumN=%lld sumN2=%lld P=%d d=%d prec=%d g0=%d", b->R, sumN, sumN2, b->P, b->d,
+             b->cfg.precision, b->A == 0.0);
+    const std::string key = device_key() + " " + kb;
+    std::string val;
+    int bestT = b->grid.pair_t;
+    if (cache_lookup(cache_path, key, val)) {
+        bestT = cache_field(val, "pair_t", bestT);
+    } else if (b->A != 0.0) {
+        double best = 1e30;
+        for (int T : {64, 128, 256}) {
+            batch_set_pair_t(b, T);
+            pimd_status st = batch_upload_args(b);
+            if (st != PIMD_OK) return st;
+            const double ms = time_ms(b->st, 3, [&] {
+                if (st == PIMD_OK) st = batch_enqueue_forces(b, b->st);
+            });
+            if (st != PIMD_OK) return st;
+            if (ms < best) {
+                best = ms;
+                bestT = T;
+            }
+        }
+        char vb[64];
+        snprintf(vb, sizeof vb, "pair_t=%d", bestT);
+        cache_store(cache_path, key, vb);
+    }
+    if (!pair_block_ok(bestT)) return bfail(b, PIMD_EINVAL, "pimd_batch_autotune: bad cache entry");
+    batch_set_pair_t(b, bestT);
+    pimd_status s = batch_upload_args(b);
+    if (s != PIMD_OK) return s;
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->graph_failed = false;
+    s = batch_enqueue_forces(b, b->st);
+    if (s != PIMD_OK) return s;
+    return batch_check_device(b);
 }
 
 extern "C" pimd_status pimd_batch_estimators(pimd_batch_t b, pimd_estimates* out)

@@ -22,6 +22,8 @@ struct BatchGrid {
     int R, P, d, M;
     int mixed;
     int gx_spr, gx_pair, gx_md, gx_prep, gx_fin, gx_table, nb_max;
+    int pair_t;       // pair-kernel block size (particles per block), 64/128/256
+    int gx_pair_max;  // pair partial-sum blocks per slice allocated (for the smallest block)
 };
 
 int batch_md_blocks(int nmax, int P, int d);

@@ -76,19 +76,19 @@ __global__ void __launch_bounds__(SPR_T) springs_kernel(BeadView b, ForceParams 
 // F += -grad(V_slice)/P.  One thread per particle, the partner slice staged in
 // shared memory 128 particles at a time.  Writes per-block (energy, virial).
 
-template <int D>
+template <int D, int PT>
 __device__ __forceinline__ void pair_body_f64(const BeadView& b, const ForceParams& fp, double* f, double* part)
 {
-    __shared__ double sx[D][PAIR_T];
+    __shared__ double sx[D][PT];
     __shared__ double red[64];
-    if (blockIdx.x * PAIR_T >= b.N) {  // a block past this replica's particles
+    if (blockIdx.x * PT >= b.N) {  // a block past this replica's particles
         if (threadIdx.x == 0) {
             part[2 * (blockIdx.y * gridDim.x + blockIdx.x) + 0] = 0.0;
             part[2 * (blockIdx.y * gridDim.x + blockIdx.x) + 1] = 0.0;
         }
         return;
     }
-    const int i = blockIdx.x * PAIR_T + threadIdx.x, j = blockIdx.y;
+    const int i = blockIdx.x * PT + threadIdx.x, j = blockIdx.y;
     const double* rs = b.r + (size_t)j * D * b.ld;
     double xi[D], g[D];
 #pragma unroll
@@ -98,12 +98,12 @@ __device__ __forceinline__ void pair_body_f64(const BeadView& b, const ForcePara
     }
     double esum = 0.0;
     if (fp.A != 0.0) {
-        for (int k0 = 0; k0 < b.N; k0 += PAIR_T) {
+        for (int k0 = 0; k0 < b.N; k0 += PT) {
             const int k = k0 + threadIdx.x;
 #pragma unroll
             for (int c = 0; c < D; ++c) sx[c][threadIdx.x] = (k < b.N) ? rs[(size_t)c * b.ld + k] : 0.0;
             __syncthreads();
-            const int kn = min(PAIR_T, b.N - k0);
+            const int kn = min(PT, b.N - k0);
             for (int kk = 0; kk < kn; ++kk) {
                 double q2 = 0.0, dx[D];
 #pragma unroll
@@ -147,19 +147,19 @@ __device__ __forceinline__ void pair_body_f64(const BeadView& b, const ForcePara
 // One thread per particle; partners are taken two at a time on the packed
 // FP32x2 pipe, the partner tile sitting in shared memory as negated
 // coordinate pairs {x_k, x_k+1} per component.
-template <int D>
+template <int D, int PT>
 __device__ __forceinline__ void pair_body_f32(const BeadView& b, const ForceParams& fp, double* f, double* part)
 {
-    __shared__ float2 sx[D][PAIR_T / 2];
+    __shared__ float2 sx[D][PT / 2];
     __shared__ double red[64];
-    if (blockIdx.x * PAIR_T >= b.N) {  // a block past this replica's particles
+    if (blockIdx.x * PT >= b.N) {  // a block past this replica's particles
         if (threadIdx.x == 0) {
             part[2 * (blockIdx.y * gridDim.x + blockIdx.x) + 0] = 0.0;
             part[2 * (blockIdx.y * gridDim.x + blockIdx.x) + 1] = 0.0;
         }
         return;
     }
-    const int i = blockIdx.x * PAIR_T + threadIdx.x, j = blockIdx.y;
+    const int i = blockIdx.x * PT + threadIdx.x, j = blockIdx.y;
     const double* rs = b.r + (size_t)j * D * b.ld;
     const float sc = (float)sqrt(fp.inv_s2 * 1.4426950408889634);
     double xd[D];
@@ -173,15 +173,15 @@ __device__ __forceinline__ void pair_body_f32(const BeadView& b, const ForcePara
     }
     float2 esum = make_float2(0.f, 0.f);
     if (fp.A != 0.0) {
-        for (int k0 = 0; k0 < b.N; k0 += PAIR_T) {
+        for (int k0 = 0; k0 < b.N; k0 += PT) {
             const int k = k0 + threadIdx.x;
             float* sxf = reinterpret_cast<float*>(&sx[0][0]);
 #pragma unroll
             for (int c = 0; c < D; ++c)
-                sxf[c * PAIR_T + threadIdx.x] = (k < b.N) ? -d2f_trunc(rs[(size_t)c * b.ld + k]) * sc : -1.0e18f;
+                sxf[c * PT + threadIdx.x] = (k < b.N) ? -d2f_trunc(rs[(size_t)c * b.ld + k]) * sc : -1.0e18f;
             __syncthreads();
 #pragma unroll 4
-            for (int kk = 0; kk < PAIR_T / 2; ++kk) {
+            for (int kk = 0; kk < PT / 2; ++kk) {
                 float2 dx[D];
 #pragma unroll
                 for (int c = 0; c < D; ++c) dx[c] = __fadd2_rn(xi[c], sx[c][kk]);
@@ -221,16 +221,16 @@ __device__ __forceinline__ void pair_body_f32(const BeadView& b, const ForcePara
     }
 }
 
-template <int D>
-__global__ void __launch_bounds__(PAIR_T) pair_kernel_f64(BeadView b, ForceParams fp, double* f, double* part)
+template <int D, int PT>
+__global__ void __launch_bounds__(PT) pair_kernel_f64(BeadView b, ForceParams fp, double* f, double* part)
 {
-    pair_body_f64<D>(b, fp, f, part);
+    pair_body_f64<D, PT>(b, fp, f, part);
 }
 
-template <int D>
-__global__ void __launch_bounds__(PAIR_T) pair_kernel_f32(BeadView b, ForceParams fp, double* f, double* part)
+template <int D, int PT>
+__global__ void __launch_bounds__(PT) pair_kernel_f32(BeadView b, ForceParams fp, double* f, double* part)
 {
-    pair_body_f32<D>(b, fp, f, part);
+    pair_body_f32<D, PT>(b, fp, f, part);
 }
 
 // ---------------------------------------------------------------------------
@@ -457,14 +457,14 @@ __global__ void __launch_bounds__(SPR_T) springs_batch(const RepArgs* ra)
     springs_body(a.bv, fp, a.bv.f, a.part_spr);
 }
 
-template <int D, bool MIXED>
-__global__ void __launch_bounds__(PAIR_T) pair_batch(const RepArgs* ra)
+template <int D, bool MIXED, int PT>
+__global__ void __launch_bounds__(PT) pair_batch(const RepArgs* ra)
 {
     const RepArgs& a = ra[blockIdx.z];
     ForceParams fp = a.fp;
     fp.accumulate = 1;
-    if (MIXED) pair_body_f32<D>(a.bv, fp, a.bv.f, a.part_pair);
-    else pair_body_f64<D>(a.bv, fp, a.bv.f, a.part_pair);
+    if (MIXED) pair_body_f32<D, PT>(a.bv, fp, a.bv.f, a.part_pair);
+    else pair_body_f64<D, PT>(a.bv, fp, a.bv.f, a.part_pair);
 }
 
 template <bool PRE, int M>
@@ -501,7 +501,8 @@ __global__ void nonfinite_kernel(const double* x, int N, int P, int d, int ld, i
 }  // namespace
 
 int springs_grid_x(int N) { return (N + SPR_T - 1) / SPR_T; }
-int pair_grid_x(int N) { return (N + PAIR_T - 1) / PAIR_T; }
+int pair_grid_x(int N, int pt) { return (N + pt - 1) / pt; }
+bool pair_block_ok(int pt) { return pt == 64 || pt == 128 || pt == 256; }
 int md_blocks(int N, int P, int d)
 {
     long long n = (long long)N * P * d;
@@ -515,18 +516,26 @@ cudaError_t launch_springs(const BeadView& b, const ForceParams& fp, double* f_o
     return cudaGetLastError();
 }
 
-cudaError_t launch_pair(const BeadView& b, const ForceParams& fp, double* f_out, double* part, cudaStream_t st)
+template <int PT>
+static void launch_pair_pt(const BeadView& b, const ForceParams& fp, double* f_out, double* part, cudaStream_t st)
 {
-    dim3 grid(pair_grid_x(b.N), b.P);
+    dim3 grid(pair_grid_x(b.N, PT), b.P);
     if (fp.mixed) {
-        if (b.d == 1) pair_kernel_f32<1><<<grid, PAIR_T, 0, st>>>(b, fp, f_out, part);
-        else if (b.d == 2) pair_kernel_f32<2><<<grid, PAIR_T, 0, st>>>(b, fp, f_out, part);
-        else pair_kernel_f32<3><<<grid, PAIR_T, 0, st>>>(b, fp, f_out, part);
+        if (b.d == 1) pair_kernel_f32<1, PT><<<grid, PT, 0, st>>>(b, fp, f_out, part);
+        else if (b.d == 2) pair_kernel_f32<2, PT><<<grid, PT, 0, st>>>(b, fp, f_out, part);
+        else pair_kernel_f32<3, PT><<<grid, PT, 0, st>>>(b, fp, f_out, part);
     } else {
-        if (b.d == 1) pair_kernel_f64<1><<<grid, PAIR_T, 0, st>>>(b, fp, f_out, part);
-        else if (b.d == 2) pair_kernel_f64<2><<<grid, PAIR_T, 0, st>>>(b, fp, f_out, part);
-        else pair_kernel_f64<3><<<grid, PAIR_T, 0, st>>>(b, fp, f_out, part);
+        if (b.d == 1) pair_kernel_f64<1, PT><<<grid, PT, 0, st>>>(b, fp, f_out, part);
+        else if (b.d == 2) pair_kernel_f64<2, PT><<<grid, PT, 0, st>>>(b, fp, f_out, part);
+        else pair_kernel_f64<3, PT><<<grid, PT, 0, st>>>(b, fp, f_out, part);
     }
+}
+
+cudaError_t launch_pair(const BeadView& b, const ForceParams& fp, double* f_out, double* part, cudaStream_t st, int pt)
+{
+    if (pt == 64) launch_pair_pt<64>(b, fp, f_out, part, st);
+    else if (pt == 256) launch_pair_pt<256>(b, fp, f_out, part, st);
+    else launch_pair_pt<128>(b, fp, f_out, part, st);
     return cudaGetLastError();
 }
 
@@ -605,15 +614,24 @@ cudaError_t batch_launch_forces(const RepArgs* ra, const BatchGrid& g, cudaStrea
     springs_batch<<<dim3(g.gx_spr, P, g.R), SPR_T, 0, st>>>(ra);
     prof_mark(pm, "batch_springs", st);
     const dim3 grid(g.gx_pair, P, g.R);
-    if (mixed) {
-        if (d == 1) pair_batch<1, true><<<grid, PAIR_T, 0, st>>>(ra);
-        else if (d == 2) pair_batch<2, true><<<grid, PAIR_T, 0, st>>>(ra);
-        else pair_batch<3, true><<<grid, PAIR_T, 0, st>>>(ra);
-    } else {
-        if (d == 1) pair_batch<1, false><<<grid, PAIR_T, 0, st>>>(ra);
-        else if (d == 2) pair_batch<2, false><<<grid, PAIR_T, 0, st>>>(ra);
-        else pair_batch<3, false><<<grid, PAIR_T, 0, st>>>(ra);
+#define PIMD_PB(PT)                                                                 \
+    if (mixed) {                                                                    \
+        if (d == 1) pair_batch<1, true, PT><<<grid, PT, 0, st>>>(ra);               \
+        else if (d == 2) pair_batch<2, true, PT><<<grid, PT, 0, st>>>(ra);          \
+        else pair_batch<3, true, PT><<<grid, PT, 0, st>>>(ra);                      \
+    } else {                                                                        \
+        if (d == 1) pair_batch<1, false, PT><<<grid, PT, 0, st>>>(ra);              \
+        else if (d == 2) pair_batch<2, false, PT><<<grid, PT, 0, st>>>(ra);         \
+        else pair_batch<3, false, PT><<<grid, PT, 0, st>>>(ra);                     \
     }
+    if (g.pair_t == 64) {
+        PIMD_PB(64)
+    } else if (g.pair_t == 256) {
+        PIMD_PB(256)
+    } else {
+        PIMD_PB(128)
+    }
+#undef PIMD_PB
     prof_mark(pm, "batch_pair", st);
     return cudaGetLastError();
 }

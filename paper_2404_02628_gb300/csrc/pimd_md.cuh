@@ -60,11 +60,13 @@ struct ScalarSources {
 };
 
 int springs_grid_x(int N);
-int pair_grid_x(int N);
+int pair_grid_x(int N, int pt);   // blocks per slice for pt particles per block
+bool pair_block_ok(int pt);       // pt in {64, 128, 256}
+constexpr int PAIR_T_MIN = 64;
 int md_blocks(int N, int P, int d);
 
 cudaError_t launch_springs(const BeadView& b, const ForceParams& fp, double* f_out, double* part, cudaStream_t st);
-cudaError_t launch_pair(const BeadView& b, const ForceParams& fp, double* f_out, double* part, cudaStream_t st);
+cudaError_t launch_pair(const BeadView& b, const ForceParams& fp, double* f_out, double* part, cudaStream_t st, int pt);
 cudaError_t launch_md_pre(const BeadView& b, const MDParams& mp, cudaStream_t st);
 cudaError_t launch_md_post(const BeadView& b, const MDParams& mp, cudaStream_t st);
 cudaError_t launch_md_energy(const BeadView& b, const MDParams& mp, double* part, cudaStream_t st);

@@ -152,3 +152,20 @@ def test_vb_table_mode_and_workspace(pkg):
     assert sizes[16384] < sizes[16383] / 20                 # recomputed
     assert sizes[40000] < 12 * 40000 * 40001 // 2 // 50     # O(N): 127 MB against the 9.6 GB table
     assert sizes[20000] < sizes[30000] < sizes[40000]
+
+
+def test_autotune_requires_bound_handle(pkg):
+    h = pkg.pimd_create(100, 4, 2, 1.0, 1.0, 0.0, 0.5, 1.0)
+    try:
+        with pytest.raises(pkg.PimdError) as ei:
+            pkg.pimd_autotune(h, None)
+        assert ei.value.status == pkg.PIMD_ESTATE
+    finally:
+        pkg.pimd_destroy(h)
+    b = pkg.pimd_batch_create([10, 20], 4, 2, [1.0, 1.0], [1.0, 1.0], 1.0, 0.0, 0.5)
+    try:
+        with pytest.raises(pkg.PimdError) as ei:
+            pkg.pimd_batch_autotune(b, None)
+        assert ei.value.status == pkg.PIMD_ESTATE
+    finally:
+        pkg.pimd_batch_destroy(b)
