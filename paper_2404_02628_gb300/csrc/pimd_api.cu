@@ -526,10 +526,7 @@ extern "C" pimd_status pimd_bind(pimd_t c, const pimd_buffers* b, void* stream)
     c->mp.inv_Q = 1.0 / c->mp.Q;
     c->mp.thermostat = c->cfg.thermostat;
     c->mp.nhc_fp32 = c->cfg.nhc_fp32 != 0;
-    c->mp.f_inv_mass = (float)c->mp.inv_mass;
-    c->mp.f_inv_Q = (float)c->mp.inv_Q;
-    c->mp.f_kT = (float)c->mp.kT;
-    c->mp.f_half_dt = (float)(0.5 * c->mp.dt);
+    nhc_constants(c->mp);
     cudaError_t e;
     if (c->cfg.thermostat) {
         const size_t n = (size_t)c->cfg.nhc_len * c->P * c->d * np;
@@ -1340,10 +1337,7 @@ extern "C" pimd_status pimd_batch_bind(pimd_batch_t b, const pimd_batch_buffers*
         a.mp.inv_Q = 1.0 / a.mp.Q;
         a.mp.thermostat = b->cfg.thermostat;
         a.mp.nhc_fp32 = b->cfg.nhc_fp32 != 0;
-        a.mp.f_inv_mass = (float)a.mp.inv_mass;
-        a.mp.f_inv_Q = (float)a.mp.inv_Q;
-        a.mp.f_kT = (float)a.mp.kT;
-        a.mp.f_half_dt = (float)(0.5 * a.mp.dt);
+        nhc_constants(a.mp);
         a.xv = xdf_view(base, xl[r], N, P, d, beta, b->xi[r], 1, nb, 1, rr + (size_t)(P - 1) * d * np, rr, np, np,
                         b->cfg.spin_limit, 0);
         a.xv.err = (int*)(base + b->off_err);

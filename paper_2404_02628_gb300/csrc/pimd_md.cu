@@ -240,50 +240,78 @@ __global__ void __launch_bounds__(PT) pair_kernel_f32(BeadView b, ForceParams fp
 // momentum scaled by exp(-tau p_1/Q), positions eta += tau p_eta/Q, then the
 // links again in the opposite order.
 
-// e^x in FP64.  The thermostat scalings have |x| of order 1e-3, where the
-// Taylor polynomial of degree 8 (Horner form) truncates below (1/32)^9/9! <
-// 1e-19 relative; larger |x| use the library exp.
-__device__ __forceinline__ double exp_small(double x)
+// FP64 <-> double-float without the FP64->FP32 hardware conversion: the high
+// part is x with its significand truncated to 24 bits (integer pipe), the
+// low part the FP64-exact remainder, truncated the same way (about 2^-47
+// relative overall).
+__device__ __forceinline__ df d2df(double x)
 {
-    if (!(fabs(x) <= 0.03125)) return exp(x);
-    double s = 1.0 / 40320.0;
-    s = fma(s, x, 1.0 / 5040.0);
-    s = fma(s, x, 1.0 / 720.0);
-    s = fma(s, x, 1.0 / 120.0);
-    s = fma(s, x, 1.0 / 24.0);
-    s = fma(s, x, 1.0 / 6.0);
-    s = fma(s, x, 0.5);
-    s = fma(s, x, 1.0);
-    return fma(s, x, 1.0);
+    const float h = d2f_trunc(x);
+    return df{h, d2f_trunc(x - (double)h)};
+}
+__device__ __forceinline__ double df2d(df a) { return (double)a.h + (double)a.l; }
+__device__ __forceinline__ df dfc(const float (&c)[2]) { return df{c[0], c[1]}; }
+
+// e^x for a double-float x: the Taylor polynomial of degree 8 (Horner form)
+// for |x| <= 1/32, where it truncates below (1/32)^9/9! < 1e-19 relative;
+// the thermostat's arguments are of order 1e-3.  Larger |x| through the FP64
+// library exp.
+__device__ __forceinline__ df df_exp_small(df x)
+{
+    if (!(fabsf(x.h) <= 0.03125f)) return d2df(exp(df2d(x)));
+#define PIMD_DFC(v) df{(float)(v), (float)((v) - (double)(float)(v))}
+    df s = PIMD_DFC(1.0 / 40320.0);
+    s = df_add(df_mul(s, x), PIMD_DFC(1.0 / 5040.0));
+    s = df_add(df_mul(s, x), PIMD_DFC(1.0 / 720.0));
+    s = df_add(df_mul(s, x), PIMD_DFC(1.0 / 120.0));
+    s = df_add(df_mul(s, x), PIMD_DFC(1.0 / 24.0));
+    s = df_add(df_mul(s, x), PIMD_DFC(1.0 / 6.0));
+    s = df_add(df_mul(s, x), df{0.5f, 0.f});
+    s = df_add(df_mul(s, x), df{1.f, 0.f});
+    return df_add(df_mul(s, x), df{1.f, 0.f});
+#undef PIMD_DFC
 }
 
-// One Trotter half step of length tau for the massive chains of one degree of
-// freedom; 1/m and 1/Q come precomputed.  M is a template argument so that
-// the chain stays in registers.
+// One Trotter half step of length tau = dt/2 for the massive chains of one
+// degree of freedom (Sec. IV A; MTK order): last link, links M-1..1 scaled by
+// exp(-tau p_{k+1}/(4Q)), the momentum scaled by exp(-tau p_1/Q), eta drift,
+// then the links again in reverse order.  Arithmetic in double-float on the
+// FP32 pipe (FP64-accurate to about 1e-14); state read and written in FP64.
 template <int M>
-__device__ __forceinline__ void nhc_half_step(double& p, double (&eta)[M], double (&pe)[M], double inv_m, double inv_Q,
-                                              double kT, double tau)
+__device__ __forceinline__ void nhc_half_step(double& p64, double (&eta64)[M], double (&pe64)[M], const NhcConst& c)
 {
-    const double ca = -0.25 * tau * inv_Q, cg = 0.5 * tau, ce = tau * inv_Q;
-    double G = ((M >= 2) ? pe[M - 2] * pe[M - 2] * inv_Q : p * p * inv_m) - kT;
-    pe[M - 1] = fma(cg, G, pe[M - 1]);
+    const df inv_m = dfc(c.inv_m), inv_Q = dfc(c.inv_Q), kT = df_neg(dfc(c.kT));
+    const df ca = dfc(c.ca), cg = dfc(c.cg), ce = dfc(c.ce), cp = dfc(c.cp);
+    df p = d2df(p64), q[M], e[M];
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        q[k] = d2df(pe64[k]);
+        e[k] = d2df(eta64[k]);
+    }
+    auto force = [&](int k) {  // G_k: kinetic energy of the link below, times 2, minus kT
+        return df_add(k == 0 ? df_mul(df_mul(p, p), inv_m) : df_mul(df_mul(q[k - 1], q[k - 1]), inv_Q), kT);
+    };
+    q[M - 1] = df_add(q[M - 1], df_mul(cg, force(M - 1)));
 #pragma unroll
     for (int k = M - 2; k >= 0; --k) {
-        const double a = exp_small(ca * pe[k + 1]);
-        G = ((k == 0) ? p * p * inv_m : pe[k - 1] * pe[k - 1] * inv_Q) - kT;
-        pe[k] = fma(pe[k], a * a, cg * G * a);
+        const df a = df_exp_small(df_mul(ca, q[k + 1]));
+        q[k] = df_add(df_mul(q[k], df_mul(a, a)), df_mul(df_mul(cg, force(k)), a));
     }
-    p *= exp_small(-tau * inv_Q * pe[0]);
+    p = df_mul(p, df_exp_small(df_mul(cp, q[0])));
 #pragma unroll
-    for (int k = 0; k < M; ++k) eta[k] = fma(ce, pe[k], eta[k]);
+    for (int k = 0; k < M; ++k) e[k] = df_add(e[k], df_mul(ce, q[k]));
 #pragma unroll
     for (int k = 0; k <= M - 2; ++k) {
-        const double a = exp_small(ca * pe[k + 1]);
-        G = ((k == 0) ? p * p * inv_m : pe[k - 1] * pe[k - 1] * inv_Q) - kT;
-        pe[k] = fma(pe[k], a * a, cg * G * a);
+        const df a = df_exp_small(df_mul(ca, q[k + 1]));
+        q[k] = df_add(df_mul(q[k], df_mul(a, a)), df_mul(df_mul(cg, force(k)), a));
     }
-    G = ((M >= 2) ? pe[M - 2] * pe[M - 2] * inv_Q : p * p * inv_m) - kT;
-    pe[M - 1] = fma(cg, G, pe[M - 1]);
+    q[M - 1] = df_add(q[M - 1], df_mul(cg, force(M - 1)));
+    p64 = df2d(p);
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        pe64[k] = df2d(q[k]);
+        eta64[k] = df2d(e[k]);
+    }
 }
 
 // The same half step with the chain arithmetic in FP32 (mixed precision): the
@@ -351,7 +379,7 @@ __device__ __forceinline__ void md_body(const BeadView& b, const MDParams& mp)
                 if (mp.nhc_fp32)
                     nhc_half_step_f32<M>(p, eta, pe, mp.f_inv_mass, mp.f_inv_Q, mp.f_kT, mp.f_half_dt);
                 else
-                    nhc_half_step<M>(p, eta, pe, mp.inv_mass, mp.inv_Q, mp.kT, 0.5 * mp.dt);
+                    nhc_half_step<M>(p, eta, pe, mp.nc);
             }
             p += 0.5 * mp.dt * b.f[o];
             b.r[o] = fma(mp.dt * mp.inv_mass, p, b.r[o]);
@@ -361,7 +389,7 @@ __device__ __forceinline__ void md_body(const BeadView& b, const MDParams& mp)
                 if (mp.nhc_fp32)
                     nhc_half_step_f32<M>(p, eta, pe, mp.f_inv_mass, mp.f_inv_Q, mp.f_kT, mp.f_half_dt);
                 else
-                    nhc_half_step<M>(p, eta, pe, mp.inv_mass, mp.inv_Q, mp.kT, 0.5 * mp.dt);
+                    nhc_half_step<M>(p, eta, pe, mp.nc);
             }
         }
         b.p[o] = p;
@@ -641,4 +669,28 @@ cudaError_t batch_launch_scalars(const RepArgs* ra, const BatchGrid& g, cudaStre
     md_energy_batch<<<dim3(g.gx_md, 1, g.R), MD_T, 0, st>>>(ra);
     scalars_batch<<<g.R, 32, 0, st>>>(ra);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+
+static void split_df(double x, float (&out)[2])
+{
+    out[0] = (float)x;
+    out[1] = (float)(x - (double)out[0]);
+}
+
+void nhc_constants(MDParams& mp)
+{
+    const double tau = 0.5 * mp.dt;
+    split_df(mp.inv_mass, mp.nc.inv_m);
+    split_df(mp.inv_Q, mp.nc.inv_Q);
+    split_df(mp.kT, mp.nc.kT);
+    split_df(-0.25 * tau * mp.inv_Q, mp.nc.ca);
+    split_df(0.5 * tau, mp.nc.cg);
+    split_df(tau * mp.inv_Q, mp.nc.ce);
+    split_df(-tau * mp.inv_Q, mp.nc.cp);
+    mp.f_inv_mass = (float)mp.inv_mass;
+    mp.f_inv_Q = (float)mp.inv_Q;
+    mp.f_kT = (float)mp.kT;
+    mp.f_half_dt = (float)tau;
 }

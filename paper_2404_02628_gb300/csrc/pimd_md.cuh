@@ -22,13 +22,27 @@ struct ForceParams {
     int accumulate; // 0: overwrite f, 1: add into f
 };
 
+// Double-float constants of the thermostat half step of length tau = dt/2
+// ({high, low} floats, formed on the host by nhc_constants).
+struct NhcConst {
+    float inv_m[2], inv_Q[2], kT[2];
+    float ca[2];  // -tau/(4Q): exponent of the chain-link scalings
+    float cg[2];  // tau/2: force-update factor
+    float ce[2];  // tau/Q: eta drift
+    float cp[2];  // -tau/Q: exponent of the momentum scaling
+};
+
 struct MDParams {
     double dt, mass, Q, kT;
     double inv_mass, inv_Q;   // 1/mass and 1/Q, formed on the host
     int thermostat;
     int nhc_fp32;             // thermostat chain arithmetic in FP32
     float f_inv_mass, f_inv_Q, f_kT, f_half_dt;  // FP32 copies for that mode
+    NhcConst nc;                                  // double-float constants (FP64-accurate mode)
 };
+
+// Fills mp.nc (and the FP32 copies) from dt, inv_mass, inv_Q, kT.  Host only.
+void nhc_constants(MDParams& mp);
 
 // Scalar slots of the per-step reduction (device array of doubles).
 enum {

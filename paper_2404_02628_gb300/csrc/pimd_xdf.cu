@@ -1465,8 +1465,10 @@ __global__ void xdf_vb_value_kernel(XView v, int nprep, double* V_out)
 
 }  // namespace
 
-int xdf_prep_blocks(int npad) { return min(152, (npad + 255) / 256); }
-int xdf_finalize_blocks(int N) { return (N + 255) / 256; }
+// prep and finalize do FP64 work per particle: 64-thread blocks spread it over more SMs
+constexpr int XDF_SMALL_T = 64;
+int xdf_prep_blocks(int npad) { return min(152 * 4, (npad + XDF_SMALL_T - 1) / XDF_SMALL_T); }
+int xdf_finalize_blocks(int N) { return (N + XDF_SMALL_T - 1) / XDF_SMALL_T; }
 
 size_t xdf_recursion_smem(int W)
 {
@@ -1480,7 +1482,7 @@ static size_t blockops_smem() { return 4 * sizeof(DfwTile); }
 
 cudaError_t xdf_launch_forward(const XView& v, cudaStream_t st, ProfMarks* pm)
 {
-    xdf_prep_kernel<<<xdf_prep_blocks(v.npad), 256, 0, st>>>(v);
+    xdf_prep_kernel<<<xdf_prep_blocks(v.npad), XDF_SMALL_T, 0, st>>>(v);
     prof_mark(pm, "exch_prep", st);
     if (v.xi_zero) return cudaGetLastError();
     const long long nt = xdf_ntiles(v.nb, v.W, v.store);
@@ -1524,7 +1526,7 @@ cudaError_t xdf_launch_adjoint(const XView& v, const FinalizeOut& o, cudaStream_
         xdf_band_kernel<<<dim3(v.nb, 2), 32 * v.W, band_smem(v.W), st>>>(v);
         prof_mark(pm, "exch_band", st);
     }
-    xdf_finalize_kernel<<<xdf_finalize_blocks(v.N), 256, 0, st>>>(v, o);
+    xdf_finalize_kernel<<<xdf_finalize_blocks(v.N), XDF_SMALL_T, 0, st>>>(v, o);
     prof_mark(pm, "exch_finalize", st);
     return cudaGetLastError();
 }
@@ -1562,7 +1564,7 @@ cudaError_t batch_launch_exchange(const RepArgs* ra, const BatchGrid& g, cudaStr
         if (e != cudaSuccess) return e;
         attrs = true;
     }
-    prep_batch<<<dim3(g.gx_prep, 1, g.R), 256, 0, st>>>(ra);
+    prep_batch<<<dim3(g.gx_prep, 1, g.R), XDF_SMALL_T, 0, st>>>(ra);
     prof_mark(pm, "batch_exch_prep", st);
     table_batch<<<dim3(g.gx_table, 1, g.R), 256, 0, st>>>(ra);
     prof_mark(pm, "batch_exch_table", st);
@@ -1572,7 +1574,7 @@ cudaError_t batch_launch_exchange(const RepArgs* ra, const BatchGrid& g, cudaStr
     prof_mark(pm, "batch_exch_recursion", st);
     band_batch<<<dim3(g.nb_max, 2, g.R), 256, band_smem(8), st>>>(ra);
     prof_mark(pm, "batch_exch_band", st);
-    finalize_batch<<<dim3(g.gx_fin, 1, g.R), 256, 0, st>>>(ra);
+    finalize_batch<<<dim3(g.gx_fin, 1, g.R), XDF_SMALL_T, 0, st>>>(ra);
     prof_mark(pm, "batch_exch_finalize", st);
     return cudaGetLastError();
 }
