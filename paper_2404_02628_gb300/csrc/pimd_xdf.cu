@@ -10,7 +10,8 @@ namespace {
 
 // Element (r, c) of an XTile (see pimd_xdf.cuh).
 #define RIDX(r, c) (((r) << 5) + (((c) + (r)) & 31))
-#define XDF_TILES 16  // tile slots per recursion block: 2 per helper, a ring of 16 / W sets of W for a chain block
+#define XDF_TILES 16  // tile slots per recursion block: two per helper warp, a ring of 16 / W sets of W for a chain block
+#define XDF_WSLOTS 16 // weight slots per recursion block: two per helper warp
 typedef XTile DfwTile;
 
 __device__ __forceinline__ void cp16(void* dst, const void* src)
@@ -487,10 +488,10 @@ __device__ __forceinline__ void blockops_body(const XView& v)
         cp_wait<0>();
     }
     block_sync();
-    // G = (I - L)^{-1} by forward substitution, one column per warp pass
-    // (lane = row): after step t, lane t holds its final G[t][c], which is
-    // broadcast and applied to the rows below.
-    for (int c = w; c < 32; c += XDF_WARPS) {
+    // G = (I - L)^{-1} by forward substitution, one column per warp (lane =
+    // row; 32 warps, all columns at once): after step t, lane t holds its
+    // final G[t][c], which is broadcast and applied to the rows below.
+    for (int c = w; c < 32; c += blockDim.x >> 5) {
         dfw acc = (lane == c) ? dfw{1.f, 0.f, 0} : dfw_zero();
         for (int t = c; t < 31; ++t) {
             dfw gt;
@@ -519,7 +520,8 @@ __device__ __forceinline__ void blockops_body(const XView& v)
     }
 }
 
-__global__ void __launch_bounds__(256) xdf_blockops_kernel(XView v) { blockops_body(v); }
+constexpr int XDF_BLOCKOPS_T = 1024;  // one warp per column of G
+__global__ void __launch_bounds__(XDF_BLOCKOPS_T) xdf_blockops_kernel(XView v) { blockops_body(v); }
 
 // ------------------------------------------------------------------------
 // recursion: chain blocks and helpers
@@ -729,12 +731,12 @@ __device__ __forceinline__ void compute_sync()
 //   2: warp 0 sums the partials of Q_J y_{J-1} (P_J^T c_{J+1}) and G_J s_J into
 //      the solution block; warp 1 forms s of the next block from its band
 //      sum, the new band partials and the helper partials; warps 2-3 add band
-//      partials into the other band accumulators; warp 5 issues the bulk copy
-//      of a later tile set into the slot just consumed.
+//      partials into the other band accumulators.
 // Only phase 2 of warp 0 and phase 1 of the Q (P) segments lie on the
 // dependent chain; the G s and band products for later blocks ride along.
 // Warp 6 fetches helper partials ahead of need; warp 7 publishes each
-// solution block (values, weight products, release flag).
+// solution block (values, weight products, release flag) and then issues the
+// bulk copy of a later tile set into the slot the block's phase 1 consumed.
 template <int DIR>
 __device__ void xchain(const XView& v, DfwTile* Tall, ChainS* cs)
 {
@@ -786,6 +788,11 @@ __device__ void xchain(const XView& v, DfwTile* Tall, ChainS* cs)
             }
         };
         load_e(0);
+        int issued = -1;  // lane 0: last tile set issued
+        if (lane == 0) {
+            for (int i = 0; i < min(NS, nb); ++i) chain_issue_set<DIR>(v, Tall, cs, i, NS);
+            issued = min(NS, nb) - 1;
+        }
         for (int it = 0; it < nb; ++it) {
             if (!smem_wait_ge(&cs->y_ready, it, cs, lim, v.err, 0x560000 + it)) break;
             const int J = chain_block<DIR>(v, it), xs = it % XDF_XR, n = 32 * J + lane;
@@ -799,15 +806,27 @@ __device__ void xchain(const XView& v, DfwTile* Tall, ChainS* cs)
                 (DIR == 0 ? v.uh : v.wh)[(size_t)c * v.npad + n] = u.h;
                 (DIR == 0 ? v.ul : v.wl)[(size_t)c * v.npad + n] = u.l;
             }
-            asm volatile("fence.acq_rel.gpu;" ::: "memory");
+            // the warp barrier orders every lane's stores before lane 0's
+            // release (cumulative), so one release publishes the block
             __syncwarp();
             if (lane == 0) {
                 st_release(&flag_chain[J], 1);
                 vstore(&cs->published, it);
+                // slot it % NS was consumed in phase 1 of this iteration
+                if (it + NS < nb && !vload(&cs->abort)) {
+                    chain_issue_set<DIR>(v, Tall, cs, it + NS, NS);
+                    issued = it + NS;
+                }
             }
             __syncwarp();
             if (it + 1 < nb) load_e(it + 1);
         }
+        // every issued bulk copy lands before the block's shared memory is released
+        if (lane == 0)
+            for (int s = 0; s < NS && s <= issued; ++s) {
+                const int last = s + ((issued - s) / NS) * NS;
+                mbar_wait(&cs->mb_set[s], (unsigned)(last / NS), lim, v.err, &cs->abort, 0x5f8000 + s, true);
+            }
         return;
     }
     if (w == XDF_WARPS - 2) {
@@ -846,11 +865,6 @@ __device__ void xchain(const XView& v, DfwTile* Tall, ChainS* cs)
     // ---- compute warps 0-5.  They never leave the loop early: after a
     // failed wait (error recorded, abort raised) they run to the end with
     // every further wait cut short, so the block always finishes.
-    int issued = -1;  // warp 5, lane 0: last tile set issued
-    if (w == 5 && lane == 0) {
-        for (int i = 0; i < min(NS, nb); ++i) chain_issue_set<DIR>(v, Tall, cs, i, NS);
-        issued = min(NS, nb) - 1;
-    }
     int sm[2], sc0[2], sc1[2];
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
@@ -870,8 +884,8 @@ __device__ void xchain(const XView& v, DfwTile* Tall, ChainS* cs)
         DfwTile* T = Tall + slot * W;
         const bool more = it + 1 < nb;
         mbar_wait(&cs->mb_set[slot], (unsigned)(it / NS), lim, v.err, &cs->abort, 0x5f0000 + it, false);
-        // phase 1 (at it = 0 only warp 0 reads its block from G, before warp 5
-        // may overwrite the slot in phase 2)
+        // phase 1 (at it = 0 only warp 0 reads its block from G, before the
+        // publisher may refill the slot once this iteration's y is ready)
         dfw x0 = dfw_zero();
         if (it == 0 && w == 0) x0 = DIR == 0 ? tile_get(&T[1], lane, 0) : tile_get(&T[1], v.N - 32 * J, lane);
         if (it >= 1) {
@@ -929,9 +943,6 @@ __device__ void xchain(const XView& v, DfwTile* Tall, ChainS* cs)
                 for (int i = 0; i < 7; ++i) t[1 + i] = i < rn ? dfw_unpack(C.r[ridx[i < 6 ? i : 0]][lane]) : dfw_zero();
                 cput(C.hh, C.hl, C.he, sl, lane, dfw_sum8(t, 1 + rn));
             }
-        } else if (w == 5 && lane == 0 && it + NS < nb && !vload(&cs->abort)) {
-            chain_issue_set<DIR>(v, Tall, cs, it + NS, NS);
-            issued = it + NS;
         }
         compute_sync();
         if (tid == 0) {
@@ -940,22 +951,94 @@ __device__ void xchain(const XView& v, DfwTile* Tall, ChainS* cs)
         }
         __syncwarp();
     }
-    // every issued bulk copy lands before the block's shared memory is released
-    if (w == 5 && lane == 0)
-        for (int s = 0; s < NS && s <= issued; ++s) {
-            const int last = s + ((issued - s) / NS) * NS;
-            mbar_wait(&cs->mb_set[s], (unsigned)(last / NS), lim, v.err, &cs->abort, 0x5f8000 + s, true);
+}
+
+// Running weighted sums of one lane over the tiles of a helper item:
+// s = sum_t A_t w_t and v_c = sum_t A_t u_{c,t}, where w_t is a published
+// solution entry and u_{c,t} its product with an endpoint coordinate (same
+// exponent as w_t).  Terms are scaled to the running largest exponent E;
+// each 4-term chunk rescales the sums when E grows (powers of two: exact, or
+// negligible when they underflow) and adds its terms with TwoSum /
+// TwoProduct compensation.
+struct RunAcc {
+    df s, v[3];
+    int E;
+};
+
+__device__ __forceinline__ void acc_prod(df& s, float ah, float al, float bh, float bl)
+{
+    const float p = __fmul_rn(ah, bh);
+    const float pe = __fmaf_rn(ah, bh, -p);
+    const float cross = __fmaf_rn(ah, bl, __fmul_rn(al, bh));
+    const df t = two_sum(s.h, p);
+    s.h = t.h;
+    s.l = __fadd_rn(s.l, __fadd_rn(t.l, __fadd_rn(pe, cross)));
+}
+
+// All 32 terms of one tile for lane `lane`: row walk (COL = false, lane = row)
+// or column walk (COL = true, lane = column).
+// Terms [ta, ta + 4 * n4) of one tile (n4 chunks of 4 terms).
+template <bool COL>
+__device__ __forceinline__ void run_tile(RunAcc& ra, const DfwTile* A, const WeightSmem* w, int lane, int d, int ta = 0,
+                                         int n4 = 8)
+{
+#pragma unroll 1
+    for (int t0 = ta; t0 < ta + 4 * n4; t0 += 4) {
+        float ah[4], al[4];
+        int k[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int t = t0 + u, q = COL ? RIDX(t, lane) : RIDX(lane, t);
+            ah[u] = A->h[q];
+            al[u] = A->l[q];
+            k[u] = A->e[q] + w->we[t];
         }
+        int Ec = k[0];
+#pragma unroll
+        for (int u = 1; u < 4; ++u) Ec = max(Ec, k[u]);
+        const int En = max(ra.E, Ec);
+        const float g = pow2f(ra.E - En);
+        ra.s = df_scale(ra.s, g);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) ra.v[c] = df_scale(ra.v[c], g);
+        ra.E = En;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int t = t0 + u;
+            const float f = pow2f(k[u] - En);
+            const float a_h = __fmul_rn(ah[u], f), a_l = __fmul_rn(al[u], f);
+            acc_prod(ra.s, a_h, a_l, w->wh[t], w->wl[t]);
+            for (int c = 0; c < d; ++c) acc_prod(ra.v[c], a_h, a_l, w->uh[c][t], w->ul[c][t]);
+        }
+    }
+}
+
+__device__ __forceinline__ DVAcc run_to_dv(const RunAcc& ra)
+{
+    if (!(ra.s.h > 0.f) || ra.E <= WEF_ZERO_E / 2) {
+        DVAcc z = dv_zero();
+        if (ra.s.h != ra.s.h) z.s = ra.s;  // NaN propagates
+        return z;
+    }
+    DVAcc out;
+    out.s = fast_two_sum(ra.s.h, ra.s.l);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) out.v[c] = fast_two_sum(ra.v[c].h, ra.v[c].l);
+    out.e = ra.E;
+    dv_renorm(out);
+    return out;
 }
 
 // Helper loop shared by both directions.  dir 0: items (B, s) = row block B,
 // column blocks I = s, s+S, ... <= B-W (row sums).  dir 1: items (B, s) =
 // column block B, row blocks J = B+W+s, B+W+s+S, ... < nb (column sums).
-// All 8 warps work on every tile of an item, warp w on its 4 columns
-// (forward) or rows (backward); tiles are visited from the first published
-// to the last, copied one ahead (cp.async), and when the newest tile's flag
-// is already set (checked once per item) no other flag is polled and the
-// published weights are prefetched with the tile.
+// Tiles already published when the item starts go warp-per-tile (warp w
+// takes tiles w, w+8, ..., all 32 terms per lane, one tile copied ahead with
+// its weights; warp-local waits); the tiles still to come go through the whole
+// block one by one as their flags are set (warp w on 4 columns / rows), which
+// keeps the latency from the last publication to the partial short.  Both
+// parts add into each warp's running sums; the eight warps' sums are merged
+// in warp order and published with one release.
 template <int DIR>
 __device__ void xhelper(const XView& v, DfwTile* T, WeightSmem* Ws, ChainS* cs, const float2* tab, int h)
 {
@@ -979,67 +1062,101 @@ __device__ void xhelper(const XView& v, DfwTile* T, WeightSmem* Ws, ChainS* cs, 
             };
             auto tJ = [&](int o) { return DIR == 0 ? B : o; };
             auto tI = [&](int o) { return DIR == 0 ? o : B; };
-            if (tid == 0) cs->ready = ld_acquire(&flag_chain[other(count - 1)]) >= 1;
-            {
-                const int o0 = other(0);
-                if (tile_stored(v, tJ(o0), tI(o0))) {
-                    const long long t = xdf_tile_index(v, tJ(o0), tI(o0));
-                    tile_copy(&T[0], v.M + t, tid, XDF_THREADS);
+            // tiles [0, kr) were published when the item starts: flags are set
+            // in publication order, so the published tiles form a prefix,
+            // found by bisection
+            if (tid == 0) {
+                int lo = 0, hi = count;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) / 2;
+                    if (ld_acquire(&flag_chain[other(mid - 1)]) >= 1) lo = mid;
+                    else hi = mid - 1;
                 }
+                cs->ready = lo;
             }
             block_sync();
-            const bool all_ready = cs->ready != 0;
-            if (all_ready && w == 0) fetch_weights_warp(v, &Ws[0], DIR, other(0), lane);
-            cp_commit();
-            DVAcc acc = dv_zero();
-            bool aborted = false;
-            for (int k = 0; k < count; ++k) {
-                const int cur = k & 1, o = other(k);
-                const int J = tJ(o), I = tI(o);
-                if (k + 1 < count) {
-                    const int on = other(k + 1);
-                    if (tile_stored(v, tJ(on), tI(on))) {
-                        const long long t = xdf_tile_index(v, tJ(on), tI(on));
-                        tile_copy(&T[cur ^ 1], v.M + t, tid, XDF_THREADS);
+            const int kr = cs->ready;
+            RunAcc ra;
+            ra.s = ra.v[0] = ra.v[1] = ra.v[2] = df{0.f, 0.f};
+            ra.E = WEF_ZERO_E;
+            bool ok = true;
+            // part 1, throughput: warp w takes published tiles w, w+8, ...,
+            // all 32 terms per lane, copied one tile ahead into its two slots
+            auto issue = [&](int j) {
+                const int k = w + XDF_WARPS * j;
+                if (k < kr) {
+                    const int o = other(k), sl = 2 * w + (j & 1);
+                    if (tile_stored(v, tJ(o), tI(o))) {
+                        const long long t = xdf_tile_index(v, tJ(o), tI(o));
+                        tile_copy(&T[sl], v.M + t, lane, 32);
                     }
-                    if (all_ready && w == 0) fetch_weights_warp(v, &Ws[cur ^ 1], DIR, on, lane);
+                    fetch_weights_warp(v, &Ws[sl], DIR, o, lane);
                 }
                 cp_commit();
-                if (!all_ready) {
+            };
+            issue(0);
+            for (int j = 0; w + XDF_WARPS * j < kr; ++j) {
+                const int k = w + XDF_WARPS * j, sl = 2 * w + (j & 1), o = other(k);
+                const int J = tJ(o), I = tI(o);
+                issue(j + 1);
+                cp_wait<1>();
+                __syncwarp();
+                if (!tile_stored(v, J, I)) {
+                    for (int c0 = 0; c0 < 32; c0 += 4) {
+                        if (DIR == 0) compute_cols_warp(v, &T[sl], J, I, c0, lane, tab);
+                        else compute_rows_warp(v, &T[sl], J, I, c0, lane, tab);
+                    }
+                    __syncwarp();
+                }
+                run_tile<DIR == 1>(ra, &T[sl], &Ws[sl], lane, v.d);
+                __syncwarp();  // the slot is refilled by issue(j + 2)
+            }
+            cp_wait<0>();
+            block_sync();
+            // part 2, latency: the tiles still to be published, each by the
+            // whole block (warp w on 4 of its columns / rows) as soon as its
+            // flag is set; all of them copied at once (at most 16 per round)
+            for (int k0 = kr; k0 < count; k0 += XDF_TILES) {
+                const int nk = min(XDF_TILES, count - k0);
+                for (int i = 0; i < nk; ++i) {
+                    const int o = other(k0 + i);
+                    if (tile_stored(v, tJ(o), tI(o))) {
+                        const long long t = xdf_tile_index(v, tJ(o), tI(o));
+                        tile_copy(&T[i], v.M + t, tid, XDF_THREADS);
+                    }
+                }
+                cp_commit();
+                for (int i = 0; i < nk && ok; ++i) {
+                    const int o = other(k0 + i), J = tJ(o), I = tI(o), sl = i % XDF_WSLOTS;
                     if (tid == 0) cs->ready = wait_flag(&flag_chain[o], 1, v.err, v.spin_limit, (DIR == 0 ? 0x530000 : 0x540000) + o);
                     block_sync();
                     if (!cs->ready) {
-                        aborted = true;
+                        ok = false;
                         break;
                     }
                     if (w == 0) {
-                        if (DIR == 0) load_wf(v, &Ws[cur], I, lane);
-                        else load_wb(v, &Ws[cur], J, lane);
+                        if (DIR == 0) load_wf(v, &Ws[sl], I, lane);
+                        else load_wb(v, &Ws[sl], J, lane);
                     }
+                    cp_wait<0>();
+                    if (!tile_stored(v, J, I)) {
+                        if (DIR == 0) compute_cols_warp(v, &T[i], J, I, 4 * w, lane, tab);
+                        else compute_rows_warp(v, &T[i], J, I, 4 * w, lane, tab);
+                    }
+                    block_sync();
+                    run_tile<DIR == 1>(ra, &T[i], &Ws[sl], lane, v.d, 4 * w, 1);
                 }
-                cp_wait<1>();
-                if (!tile_stored(v, J, I)) {
-                    if (DIR == 0) compute_cols_warp(v, &T[cur], J, I, 4 * w, lane, tab);
-                    else compute_rows_warp(v, &T[cur], J, I, 4 * w, lane, tab);
-                }
-                block_sync();
-                const DVAcc p = DIR == 0 ? weighted_rows(&T[cur], &Ws[cur], lane, v.d, 4 * w, 4 * w + 4)
-                                         : weighted_cols(&T[cur], &Ws[cur], lane, v.d, 4 * w, 4 * w + 4);
-                dv_add(acc, p);
+                cp_wait<0>();
                 block_sync();
             }
-            cp_wait<0>();
-            if (aborted) {
-                if (tid == 0) cs->abort = 1;
-                return;
-            }
-            cs->u.hm[w][lane] = acc;
+            if (!ok && tid == 0) cs->abort = 1;
+            cs->u.hm[w][lane] = run_to_dv(ra);
             block_sync();
+            if (cs->abort) return;  // every thread reads it after the barrier
             if (w == 0) {
                 DVAcc t = dv_zero();
                 for (int q2 = 0; q2 < XDF_WARPS; ++q2) dv_add(t, cs->u.hm[q2][lane]);
                 store_dv(v.parth, v.partl, v.parte, xpart_index(v, DIR, B, si, lane), t);
-                __threadfence();
                 __syncwarp();
                 if (lane == 0) st_release(&flag_part[B * v.S + si], 1);
             }
@@ -1053,9 +1170,9 @@ __global__ void __launch_bounds__(XDF_THREADS, 1) xdf_recursion_kernel(XView v)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     DfwTile* T = reinterpret_cast<DfwTile*>(smem_raw);
     WeightSmem* Ws = reinterpret_cast<WeightSmem*>(smem_raw + XDF_TILES * sizeof(DfwTile));
-    ChainS* cs = reinterpret_cast<ChainS*>(smem_raw + XDF_TILES * sizeof(DfwTile) + XDF_WARPS * sizeof(WeightSmem));
+    ChainS* cs = reinterpret_cast<ChainS*>(smem_raw + XDF_TILES * sizeof(DfwTile) + XDF_WSLOTS * sizeof(WeightSmem));
     // the float2 table needs 8-byte alignment: round its offset up to 16 bytes
-    const size_t tab_off = (XDF_TILES * sizeof(DfwTile) + XDF_WARPS * sizeof(WeightSmem) + sizeof(ChainS) + 15) & ~(size_t)15;
+    const size_t tab_off = (XDF_TILES * sizeof(DfwTile) + XDF_WSLOTS * sizeof(WeightSmem) + sizeof(ChainS) + 15) & ~(size_t)15;
     float2* tab = reinterpret_cast<float2*>(smem_raw + tab_off);
     load_tab_smem(tab, v.tab);
     block_sync();
@@ -1428,7 +1545,7 @@ __global__ void __launch_bounds__(256) table_batch(const RepArgs* ra)
     table_body(v, xdf_ntiles(v.nb, v.W, v.store));
 }
 
-__global__ void __launch_bounds__(256) blockops_batch(const RepArgs* ra)
+__global__ void __launch_bounds__(XDF_BLOCKOPS_T) blockops_batch(const RepArgs* ra)
 {
     const XView& v = ra[blockIdx.z].xv;
     if (v.xi_zero) return;
@@ -1473,7 +1590,7 @@ int xdf_finalize_blocks(int N) { return (N + XDF_SMALL_T - 1) / XDF_SMALL_T; }
 size_t xdf_recursion_smem(int W)
 {
     (void)W;
-    const size_t tab_off = (XDF_TILES * sizeof(DfwTile) + XDF_WARPS * sizeof(WeightSmem) + sizeof(ChainS) + 15) & ~(size_t)15;
+    const size_t tab_off = (XDF_TILES * sizeof(DfwTile) + XDF_WSLOTS * sizeof(WeightSmem) + sizeof(ChainS) + 15) & ~(size_t)15;
     return tab_off + 256 * sizeof(float2);
 }
 
@@ -1501,7 +1618,7 @@ cudaError_t xdf_launch_forward(const XView& v, cudaStream_t st, ProfMarks* pm)
         if (e != cudaSuccess) return e;
         attrs = true;
     }
-    xdf_blockops_kernel<<<v.nb, 256, blockops_smem(), st>>>(v);
+    xdf_blockops_kernel<<<v.nb, XDF_BLOCKOPS_T, blockops_smem(), st>>>(v);
     prof_mark(pm, "exch_blockops", st);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -1568,7 +1685,7 @@ cudaError_t batch_launch_exchange(const RepArgs* ra, const BatchGrid& g, cudaStr
     prof_mark(pm, "batch_exch_prep", st);
     table_batch<<<dim3(g.gx_table, 1, g.R), 256, 0, st>>>(ra);
     prof_mark(pm, "batch_exch_table", st);
-    blockops_batch<<<dim3(g.nb_max, 1, g.R), 256, blockops_smem(), st>>>(ra);
+    blockops_batch<<<dim3(g.nb_max, 1, g.R), XDF_BLOCKOPS_T, blockops_smem(), st>>>(ra);
     prof_mark(pm, "batch_exch_blockops", st);
     xsolo_batch<<<dim3(2, g.R), XDF_THREADS, xsolo_smem(), st>>>(ra);
     prof_mark(pm, "batch_exch_recursion", st);
