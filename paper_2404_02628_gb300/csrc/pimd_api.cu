@@ -518,6 +518,7 @@ extern "C" pimd_status pimd_bind(pimd_t c, const pimd_buffers* b, void* stream)
     c->fp.inv_s2 = 1.0 / (c->s * c->s);
     c->fp.mixed = c->cfg.precision == PIMD_PREC_MIXED;
     c->fp.accumulate = 0;
+    force_constants(c->fp, c->P);
     c->mp.dt = c->cfg.dt;
     c->mp.mass = c->cfg.mass;
     c->mp.kT = 1.0 / c->beta;
@@ -1329,6 +1330,7 @@ extern "C" pimd_status pimd_batch_bind(pimd_batch_t b, const pimd_batch_buffers*
         a.fp.A = b->A;
         a.fp.inv_s2 = 1.0 / (b->s * b->s);
         a.fp.mixed = b->cfg.precision == PIMD_PREC_MIXED;
+        force_constants(a.fp, P);
         a.mp.dt = b->cfg.dt;
         a.mp.mass = b->cfg.mass;
         a.mp.kT = 1.0 / beta;

@@ -127,7 +127,7 @@ __device__ __forceinline__ void pair_body_f64(const BeadView& b, const ForcePara
         for (int c = 0; c < D; ++c) {
             const double grad = fp.omega2 * xi[c] + cpair * g[c];
             const size_t o = ((size_t)j * D + c) * b.ld + i;
-            const double fo = -grad / b.P;
+            const double fo = -grad * fp.inv_P;
             f[o] = fp.accumulate ? f[o] + fo : fo;
             t2 = fma(xi[c], xi[c], t2);
             vir = fma(xi[c], grad, vir);
@@ -161,7 +161,7 @@ __device__ __forceinline__ void pair_body_f32(const BeadView& b, const ForcePara
     }
     const int i = blockIdx.x * PT + threadIdx.x, j = blockIdx.y;
     const double* rs = b.r + (size_t)j * D * b.ld;
-    const float sc = (float)sqrt(fp.inv_s2 * 1.4426950408889634);
+    const float sc = fp.sc32;
     double xd[D];
     float2 xi[D], g[D];
 #pragma unroll
@@ -198,13 +198,13 @@ __device__ __forceinline__ void pair_body_f32(const BeadView& b, const ForcePara
     }
     double v[2] = {0.0, 0.0};
     if (i < b.N) {
-        const double cpair = -2.0 * fp.A * fp.inv_s2 / (double)sc;
+        const double cpair = fp.cpair32;
         double t2 = 0.0, vir = 0.0;
 #pragma unroll
         for (int c = 0; c < D; ++c) {
             const double grad = fp.omega2 * xd[c] + cpair * ((double)g[c].x + (double)g[c].y);
             const size_t o = ((size_t)j * D + c) * b.ld + i;
-            const double fo = -grad / b.P;
+            const double fo = -grad * fp.inv_P;
             f[o] = fp.accumulate ? f[o] + fo : fo;
             t2 = fma(xd[c], xd[c], t2);
             vir = fma(xd[c], grad, vir);
@@ -693,4 +693,11 @@ void nhc_constants(MDParams& mp)
     mp.f_inv_Q = (float)mp.inv_Q;
     mp.f_kT = (float)mp.kT;
     mp.f_half_dt = (float)tau;
+}
+
+void force_constants(ForceParams& fp, int P)
+{
+    fp.inv_P = 1.0 / P;
+    fp.sc32 = (float)sqrt(fp.inv_s2 * 1.4426950408889634);
+    fp.cpair32 = -2.0 * fp.A * fp.inv_s2 / (double)fp.sc32;
 }

@@ -20,7 +20,13 @@ struct ForceParams {
     double A, inv_s2;
     int mixed;      // FP32 springs and pairs
     int accumulate; // 0: overwrite f, 1: add into f
+    double inv_P;   // 1/P (the action weight of V(slice)), formed on the host
+    double cpair32; // -2 A / (s^2 sc) for the FP32 pair kernel's scaled coordinates
+    float sc32;     // sqrt(log2(e))/s: coordinate scale of the FP32 pair kernel
 };
+
+// Fills the derived fields of fp (inv_P, cpair32, sc32) for P beads.  Host only.
+void force_constants(ForceParams& fp, int P);
 
 // Double-float constants of the thermostat half step of length tau = dt/2
 // ({high, low} floats, formed on the host by nhc_constants).

@@ -430,11 +430,16 @@ __global__ void __launch_bounds__(256) xdf_prep_kernel(XView v) { prep_body(v); 
 // ------------------------------------------------------------------------
 // factor table: M tiles (all in store mode, band |J-I| < W otherwise)
 
+// One tile's factors M[n][k] = exp(c_n - kappa |a_{n-1} - b_k|^2): the 32 row
+// endpoints a_{n-1}, row constants c_n and 32 column endpoints b_k are staged
+// in shared memory once per tile; each element then needs only double-float
+// arithmetic (difference, TwoProduct square, sum, scale) and the exp.
 __device__ __forceinline__ void table_body(const XView& v, long long ntiles)
 {
     __shared__ float2 tab[256];
+    __shared__ float sa[3][2][32], sb[3][2][32], scr[2][32];
     load_tab_smem(tab, v.tab);
-    block_sync();
+    const df kap = df{v.kap_h, v.kap_l};
     for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
         int J, I;
         if (v.store) {  // t = J(J+1)/2 + I; float estimate then integer correction
@@ -446,10 +451,40 @@ __device__ __forceinline__ void table_body(const XView& v, long long ntiles)
             J = (int)(t / v.W);
             I = J - (int)(t % v.W);
         }
+        block_sync();  // the previous tile's staged values are no longer read
+        if (threadIdx.x < 32) {
+            const int r = threadIdx.x, n = 32 * J + r;
+            const bool on = n >= 1 && n <= v.N;
+            for (int c = 0; c < 3; ++c) {
+                const bool cc = on && c < v.d;
+                sa[c][0][r] = cc ? v.ah[(size_t)c * v.npad + n - 1] : 0.f;
+                sa[c][1][r] = cc ? v.al[(size_t)c * v.npad + n - 1] : 0.f;
+            }
+            scr[0][r] = on ? v.crh[n] : 0.f;
+            scr[1][r] = on ? v.crl[n] : 0.f;
+        } else if (threadIdx.x < 64 && I >= 0) {
+            const int cl = threadIdx.x - 32, k = 32 * I + cl;
+            for (int c = 0; c < 3; ++c) {
+                const bool cc = c < v.d;
+                sb[c][0][cl] = cc ? v.bh[(size_t)c * v.npad + k] : 0.f;
+                sb[c][1][cl] = cc ? v.bl[(size_t)c * v.npad + k] : 0.f;
+            }
+        }
+        block_sync();
         XTile* Mt = v.M + t;
         for (int q = threadIdx.x; q < 1024; q += blockDim.x) {
-            const int r = q >> 5, c = q & 31;
-            const dfw m = (I >= 0) ? xM(v, 32 * J + r, 32 * I + c, tab) : dfw_zero();
+            const int r = q >> 5, c = q & 31, n = 32 * J + r, k = 32 * I + c;
+            dfw m = dfw_zero();
+            if (I >= 0 && n >= 1 && n <= v.N && k < n) {
+                df g = df{0.f, 0.f};
+                for (int cc = 0; cc < v.d; ++cc) {
+                    const df x = df_sub(df{sa[cc][0][r], sa[cc][1][r]}, df{sb[cc][0][c], sb[cc][1][c]});
+                    df sq = two_prod(x.h, x.h);
+                    sq.l = __fmaf_rn(2.f * x.h, x.l, sq.l);
+                    g = df_add(g, sq);
+                }
+                m = dfw_exp(df_sub(df{scr[0][r], scr[1][r]}, df_mul(g, kap)), tab);
+            }
             const int o = RIDX(r, c);
             Mt->h[o] = m.h;
             Mt->l[o] = m.l;
