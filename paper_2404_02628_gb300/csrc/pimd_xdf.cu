@@ -762,11 +762,12 @@ __device__ __forceinline__ void compute_sync()
 // One chain block per direction.  Warps 0-5 compute in two phases per
 // iteration `it` (block J), separated by a barrier on those six warps:
 //   1: every tile of the iteration's set times its vector (the previous
-//      solution block, or s_J for G_J), split into segments (chain_segments);
+//      solution block, or s_J = h_J + p_J for G_J, which the G segments form
+//      on their own entries first: the helper partial p_J is needed only
+//      here), split into segments (chain_segments);
 //   2: warp 0 sums the partials of Q_J y_{J-1} (P_J^T c_{J+1}) and G_J s_J into
-//      the solution block; warp 1 forms s of the next block from its band
-//      sum, the new band partials and the helper partials; warps 2-3 add band
-//      partials into the other band accumulators.
+//      the solution block; warps 1-3 add the band partials into the band
+//      accumulators h of later blocks; warp 4 clears block J's h and p slots.
 // Only phase 2 of warp 0 and phase 1 of the Q (P) segments lie on the
 // dependent chain; the G s and band products for later blocks ride along.
 // Warp 6 fetches helper partials ahead of need; warp 7 publishes each
@@ -866,12 +867,12 @@ __device__ void xchain(const XView& v, DfwTile* Tall, ChainS* cs)
     }
     if (w == XDF_WARPS - 2) {
         // ---- helper-partial fetcher: the partials of the block of iteration
-        // it are consumed in phase 2 of iteration it-1; its ring slot is free
-        // once iteration it-W-1 has finished.
+        // it are consumed in phase 1 of iteration it; its ring slot is cleared
+        // in phase 2 of iteration it-W.
         for (int it = 1; it < nb; ++it) {
             const int B = chain_block<DIR>(v, it), ns = chain_nparts<DIR>(v, B);
             if (ns > 0) {
-                if (!smem_wait_ge(&cs->done, it - W - 1, cs, lim, v.err, 0x570000 + it)) break;
+                if (!smem_wait_ge(&cs->done, it - W, cs, lim, v.err, 0x570000 + it)) break;
                 int ok = 1;
                 if (lane < ns) ok = wait_flag(&flag_part[B * v.S + lane], 1, v.err, lim, 0x510000 + (DIR << 16) + B);
                 if (!__all_sync(0xffffffffu, ok)) {
@@ -931,6 +932,17 @@ __device__ void xchain(const XView& v, DfwTile* Tall, ChainS* cs)
                 if (m < 0) continue;
                 dfw p = dfw_zero();
                 if (chain_tile_on<DIR>(v, it, m)) {
+                    if (m == 1) {
+                        // s_J = h_J + p_J on this segment's entries (the helper
+                        // partial of block J is needed only now)
+                        smem_wait_ge(&cs->parts_ready, it, cs, lim, v.err, 0x580000 + it);
+                        if (lane >= sc0[j] && lane < sc1[j]) {
+                            const int sl = J % W;
+                            C.xv[XDF_XR][lane] =
+                                dfw_pack(dfw_add(cget(C.hh, C.hl, C.he, sl, lane), cget(C.ph, C.pl, C.pe, sl, lane)));
+                        }
+                        __syncwarp();
+                    }
                     const float4* xv = C.xv[m == 1 ? XDF_XR : xp];
                     p = DIR == 0 ? dot_seg<false>(&T[m], lane, xv, sc0[j], sc1[j])
                                  : dot_seg<true>(&T[m], lane, xv, sc0[j], sc1[j]);
@@ -955,19 +967,11 @@ __device__ void xchain(const XView& v, DfwTile* Tall, ChainS* cs)
             __syncwarp();
             if (lane == 0) vstore(&cs->y_ready, it);
             __syncwarp();
-        } else if (w == 1) {
-            if (more && smem_wait_ge(&cs->parts_ready, it + 1, cs, lim, v.err, 0x580000 + it)) {
-                const int sl = chain_block<DIR>(v, it + 1) % W;
-                const int np = it >= 1 ? rn : 0;
-                dfw t[8];
-                t[0] = cget(C.hh, C.hl, C.he, sl, lane);
-                t[1] = cget(C.ph, C.pl, C.pe, sl, lane);
-#pragma unroll
-                for (int i = 0; i < 6; ++i) t[2 + i] = i < np ? dfw_unpack(C.r[ridx[i]][lane]) : dfw_zero();
-                C.xv[XDF_XR][lane] = dfw_pack(dfw_sum8(t, 2 + np));
-                cput(C.hh, C.hl, C.he, sl, lane, dfw_zero());
-                cput(C.ph, C.pl, C.pe, sl, lane, dfw_zero());
-            }
+        } else if (w == 4) {
+            // h and p of this block were read in phase 1: clear the slot for block J + W
+            const int sl = J % W;
+            cput(C.hh, C.hl, C.he, sl, lane, dfw_zero());
+            cput(C.ph, C.pl, C.pe, sl, lane, dfw_zero());
         } else if (w <= 3) {
             const int m = w + 1;
             if (m < W && it >= 1 && chain_tile_on<DIR>(v, it, m)) {
