@@ -734,20 +734,21 @@ __device__ __forceinline__ const XTile* chain_tile_src(const XView& v, int it, i
     return v.M + (DIR == 0 ? xdf_tile_index(v, J - 1 + m, J - 1) : xdf_tile_index(v, J + 1, J + 1 - m));
 }
 
-// Issue the bulk copies of the tile set of iteration `it` into its ring slot
-// (one thread, one 12 KB copy per tile).
+// Bulk copy of tile m of the set of iteration `it` into its ring slot: the
+// set's mbarrier expects one arrival per tile slot (W), each with the bytes
+// of its copy (none for an absent tile), so the copies of a set can be
+// issued by different threads in any order.
 template <int DIR>
-__device__ void chain_issue_set(const XView& v, DfwTile* Tall, ChainS* cs, int it, int NS)
+__device__ __forceinline__ void chain_issue_tile(const XView& v, DfwTile* Tall, ChainS* cs, int it, int NS, int m)
 {
     const int slot = it % NS;
-    DfwTile* T = Tall + slot * v.W;
-    unsigned n = 0;
-    for (int m = 0; m < v.W; ++m) n += chain_tile_on<DIR>(v, it, m) ? 1u : 0u;
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mbar_expect_tx(&cs->mb_set[slot], n * (unsigned)sizeof(XTile));
-    for (int m = 0; m < v.W; ++m) {
-        const XTile* src = chain_tile_src<DIR>(v, it, m);
-        if (src) bulk_g2s(&T[m], src, (unsigned)sizeof(XTile), &cs->mb_set[slot]);
+    const XTile* src = chain_tile_src<DIR>(v, it, m);
+    if (src) {
+        mbar_expect_tx(&cs->mb_set[slot], (unsigned)sizeof(XTile));
+        bulk_g2s(&Tall[slot * v.W + m], src, (unsigned)sizeof(XTile), &cs->mb_set[slot]);
+    } else {
+        asm volatile("{ .reg .b64 st; mbarrier.arrive.shared::cta.b64 st, [%0]; }" ::"r"(smem_u32(&cs->mb_set[slot]))
+                     : "memory");
     }
 }
 
@@ -797,7 +798,7 @@ __device__ void xchain(const XView& v, DfwTile* Tall, ChainS* cs)
                 if (cs->seg_m[k] >= mlo && cs->seg_m[k] <= mhi && n < 6) cs->red_idx[r][n++] = k;
             cs->red_n[r] = n;
         }
-        for (int q = 0; q < NS; ++q) mbar_init(&cs->mb_set[q], 1);
+        for (int q = 0; q < NS; ++q) mbar_init(&cs->mb_set[q], W);  // one arrival per tile slot
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -824,11 +825,6 @@ __device__ void xchain(const XView& v, DfwTile* Tall, ChainS* cs)
             }
         };
         load_e(0);
-        int issued = -1;  // lane 0: last tile set issued
-        if (lane == 0) {
-            for (int i = 0; i < min(NS, nb); ++i) chain_issue_set<DIR>(v, Tall, cs, i, NS);
-            issued = min(NS, nb) - 1;
-        }
         for (int it = 0; it < nb; ++it) {
             if (!smem_wait_ge(&cs->y_ready, it, cs, lim, v.err, 0x560000 + it)) break;
             const int J = chain_block<DIR>(v, it), xs = it % XDF_XR, n = 32 * J + lane;
@@ -848,21 +844,10 @@ __device__ void xchain(const XView& v, DfwTile* Tall, ChainS* cs)
             if (lane == 0) {
                 st_release(&flag_chain[J], 1);
                 vstore(&cs->published, it);
-                // slot it % NS was consumed in phase 1 of this iteration
-                if (it + NS < nb && !vload(&cs->abort)) {
-                    chain_issue_set<DIR>(v, Tall, cs, it + NS, NS);
-                    issued = it + NS;
-                }
             }
             __syncwarp();
             if (it + 1 < nb) load_e(it + 1);
         }
-        // every issued bulk copy lands before the block's shared memory is released
-        if (lane == 0)
-            for (int s = 0; s < NS && s <= issued; ++s) {
-                const int last = s + ((issued - s) / NS) * NS;
-                mbar_wait(&cs->mb_set[s], (unsigned)(last / NS), lim, v.err, &cs->abort, 0x5f8000 + s, true);
-            }
         return;
     }
     if (w == XDF_WARPS - 2) {
@@ -915,10 +900,13 @@ __device__ void xchain(const XView& v, DfwTile* Tall, ChainS* cs)
         for (int i = 0; i < 6; ++i) ridx[i] = cs->red_idx[w][i];
         rn = cs->red_n[w];
     }
+    // warp 5 issues the tile copies, lane m for tile m, every set of the run
+    // (also after an abort, so that every set's phase completes)
+    if (w == 5 && lane < W)
+        for (int i = 0; i < min(NS, nb); ++i) chain_issue_tile<DIR>(v, Tall, cs, i, NS, lane);
     for (int it = 0; it < nb; ++it) {
         const int J = chain_block<DIR>(v, it), slot = it % NS;
         DfwTile* T = Tall + slot * W;
-        const bool more = it + 1 < nb;
         mbar_wait(&cs->mb_set[slot], (unsigned)(it / NS), lim, v.err, &cs->abort, 0x5f0000 + it, false);
         // phase 1 (at it = 0 only warp 0 reads its block from G, before the
         // publisher may refill the slot once this iteration's y is ready)
@@ -972,6 +960,16 @@ __device__ void xchain(const XView& v, DfwTile* Tall, ChainS* cs)
             const int sl = J % W;
             cput(C.hh, C.hl, C.he, sl, lane, dfw_zero());
             cput(C.ph, C.pl, C.pe, sl, lane, dfw_zero());
+        } else if (w == 5) {
+            // the slot this iteration's phase 1 consumed takes the set of it + NS;
+            // its previous copies have landed (waited for again in case the
+            // block aborted and phase 1 skipped the wait)
+            if (it + NS < nb) {
+                if (lane == 0)
+                    mbar_wait(&cs->mb_set[slot], (unsigned)(it / NS), lim, v.err, &cs->abort, 0x5f4000 + it, true);
+                __syncwarp();
+                if (lane < W) chain_issue_tile<DIR>(v, Tall, cs, it + NS, NS, lane);
+            }
         } else if (w <= 3) {
             const int m = w + 1;
             if (m < W && it >= 1 && chain_tile_on<DIR>(v, it, m)) {
@@ -990,6 +988,12 @@ __device__ void xchain(const XView& v, DfwTile* Tall, ChainS* cs)
         }
         __syncwarp();
     }
+    // every issued bulk copy lands before the block's shared memory is released
+    if (w == 5 && lane == 0)
+        for (int q = 0; q < NS && q < nb; ++q) {
+            const int last = q + ((nb - 1 - q) / NS) * NS;
+            mbar_wait(&cs->mb_set[q], (unsigned)(last / NS), lim, v.err, &cs->abort, 0x5f8000 + q, true);
+        }
 }
 
 // Running weighted sums of one lane over the tiles of a helper item:
