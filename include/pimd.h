@@ -184,14 +184,19 @@ const char* pimd_profile_slot_name(pimd_t ctx, int slot);
 
 /* Autotuner: times the force evaluation (r and p are not advanced) for every
  * candidate launch shape -- the look-ahead band width W of the double-float
- * recursion (those whose workspace fits the bound one) and the pair-kernel
- * block of 64, 128 or 256 particles -- and keeps the fastest.  cache_path
+ * recursion (those whose workspace fits the bound one), the pair-kernel
+ * block of 64, 128 or 256 particles, and (double-float recursion with
+ * g != 0) the split of the SMs between recursion helper blocks and force
+ * workers that compute springs and trap + pair forces inside the recursion
+ * launch -- and keeps the fastest.  cache_path
  * (nullable): a text file of "device problem|choice" lines; a hit skips the
  * timing, a miss appends the new choice.  The step graph is re-captured on
  * the next pimd_step.  Synchronises. */
 pimd_status pimd_autotune(pimd_t ctx, const char* cache_path);
-/* The current tuned values (host only). */
-pimd_status pimd_tuning(pimd_t ctx, int* exch_band, int* pair_block);
+/* The current tuned values (host only).  helpers: recursion helper blocks;
+ * force_blocks: force-worker blocks in the recursion launch (0: springs and
+ * pairs run as kernels of their own).  helpers and force_blocks may be NULL. */
+pimd_status pimd_tuning(pimd_t ctx, int* exch_band, int* pair_block, int* helpers, int* force_blocks);
 
 /* Synchronises the bound stream and reports device-side errors. */
 pimd_status pimd_sync(pimd_t ctx);

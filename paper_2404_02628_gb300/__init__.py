@@ -125,7 +125,7 @@ _SIGS = {
     "pimd_batch_last_error": ([_vp], ctypes.c_char_p),
     "pimd_batch_destroy": ([_vp], None),
     "pimd_autotune": ([_vp, ctypes.c_char_p], ctypes.c_int),
-    "pimd_tuning": ([_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "pimd_tuning": ([_vp] + [ctypes.POINTER(ctypes.c_int)] * 4, ctypes.c_int),
     "pimd_batch_autotune": ([_vp, ctypes.c_char_p], ctypes.c_int),
 }
 
@@ -390,10 +390,9 @@ def pimd_autotune(h, cache_path=None):
 
 
 def pimd_tuning(h):
-    W = ctypes.c_int()
-    T = ctypes.c_int()
-    _check(lib().pimd_tuning(h, ctypes.byref(W), ctypes.byref(T)), h)
-    return {"exch_band": W.value, "pair_block": T.value}
+    W, T, H, F = (ctypes.c_int() for _ in range(4))
+    _check(lib().pimd_tuning(h, ctypes.byref(W), ctypes.byref(T), ctypes.byref(H), ctypes.byref(F)), h)
+    return {"exch_band": W.value, "pair_block": T.value, "helpers": H.value, "force_blocks": F.value}
 
 
 class Batch:

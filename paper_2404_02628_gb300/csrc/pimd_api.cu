@@ -12,6 +12,7 @@
 #include "pimd_exchange.cuh"
 #include "pimd_md.cuh"
 #include "pimd_batch.cuh"
+#include "pimd_forcework.cuh"
 
 namespace {
 
@@ -225,6 +226,8 @@ struct pimd_ctx {
     size_t off_spr, off_pair, off_fin, off_md, off_sc, off_flag;
     int n_help;
     int pair_t = 128;  // pair-kernel block size (pimd_autotune)
+    int n_force = 0;   // force-worker blocks folded into the recursion launch (0: separate kernels)
+    int fused_gx = 0;  // particle blocks per slice of the last folded force evaluation (0: not folded)
     ExchView xv;
     XView xd;
     BeadView bv;
@@ -380,6 +383,32 @@ static pimd_status enqueue_forces(pimd_ctx* c, cudaStream_t st, double* f, bool 
     ForceParams fp = c->fp;
     fp.accumulate = 0;
     char* base = (char*)c->buf.work;
+    c->fused_gx = 0;
+    if (exch && inter && c->use_df && c->xi != 0.0 && c->n_force > 0) {
+        // springs and trap + pairs run as force workers inside the recursion launch
+        ForceWork fw;
+        memset(&fw, 0, sizeof fw);
+        fw.b = c->bv;
+        fw.b.f = f;
+        fw.fp = c->fp;
+        fw.part_spr = (double*)(base + c->off_spr);
+        fw.part_pair = (double*)(base + c->off_pair);
+        fw.gx = (c->N + XDF_THREADS - 1) / XDF_THREADS;
+        fw.counter = (int*)(base + c->off_flag) + 1;
+        e = cudaMemsetAsync(fw.counter, 0, sizeof(int), st);
+        if (e == cudaSuccess) e = xdf_launch_forward(c->xd, st, pm, &fw, c->n_force);
+        if (e != cudaSuccess) return cuda_fail(c, e, "exchange recursion with force workers");
+        FinalizeOut o;
+        memset(&o, 0, sizeof(o));
+        o.f = f;
+        o.ldf = c->buf.n_pad;
+        o.P = c->P;
+        o.part = (double*)(base + c->off_fin);
+        e = xdf_launch_adjoint(c->xd, o, st, pm);
+        if (e != cudaSuccess) return cuda_fail(c, e, "exchange forces");
+        c->fused_gx = fw.gx;
+        return PIMD_OK;
+    }
     if (exch) {
         e = launch_springs(c->bv, fp, f, (double*)(base + c->off_spr), st);
         prof_mark(pm, "springs", st);
@@ -426,13 +455,13 @@ static pimd_status enqueue_scalars(pimd_ctx* c, cudaStream_t st)
     ScalarSources s;
     memset(&s, 0, sizeof(s));
     s.springs = (double*)(base + c->off_spr);
-    s.n_springs = springs_grid_x(c->N) * c->P;
+    s.n_springs = (c->fused_gx ? c->fused_gx : springs_grid_x(c->N)) * c->P;
     s.lsum = c->use_df ? c->xd.lsum : c->xv.lsum;
     s.n_lsum = c->use_df ? xdf_prep_blocks(c->xd.npad) : exch_prep_blocks(c->N);
     s.n_fin = c->use_df ? xdf_finalize_blocks(c->N) : exch_finalize_blocks(c->N);
     s.lam = c->use_df ? c->xd.lam : nullptr;
     s.pair = (double*)(base + c->off_pair);
-    s.n_pair = pair_grid_x(c->N, c->pair_t) * c->P;
+    s.n_pair = (c->fused_gx ? c->fused_gx : pair_grid_x(c->N, c->pair_t)) * c->P;
     s.fin = (double*)(base + c->off_fin);
     s.md = (double*)(base + c->off_md);
     s.n_md = md_blocks(c->N, c->P, c->d);
@@ -500,6 +529,13 @@ extern "C" pimd_status pimd_bind(pimd_t c, const pimd_buffers* b, void* stream)
     c->buf = *b;
     c->st = (cudaStream_t)stream;
     c->n_help = default_helpers(c->cfg);
+    c->n_force = 0;
+    if (c->use_df && c->A != 0.0 && c->xi != 0.0) {
+        // SMs the recursion's helpers do not need take the springs and pairs
+        const int sms = device_sms(), nb = (c->N + 1 + 31) / 32;
+        if (c->cfg.helper_ctas <= 0) c->n_help = std::max(4, std::min(sms - 2 - 8, nb));
+        c->n_force = std::max(0, sms - 2 - c->n_help);
+    }
     const int np = b->n_pad;
     ctx_views(c);
     c->bv.N = c->N;
@@ -796,10 +832,14 @@ extern "C" pimd_status pimd_autotune(pimd_t c, const char* cache_path)
              c->cfg.precision, c->cfg.exchange_arith, c->cfg.table_mode, c->xi == 0.0, c->A == 0.0);
     const std::string key = device_key() + " " + kb;
     std::string val;
-    int bestW = cfg_band(c->cfg), bestT = c->pair_t;
+    int bestW = cfg_band(c->cfg), bestT = c->pair_t, bestH = c->n_help, bestF = c->n_force;
+    const int sms = device_sms();
+    const bool can_fold = c->use_df && c->A != 0.0 && c->xi != 0.0;
     if (cache_lookup(cache_path, key, val)) {
         bestW = cache_field(val, "W", bestW);
         bestT = cache_field(val, "pair_t", bestT);
+        bestH = cache_field(val, "help", bestH);
+        bestF = cache_field(val, "fold", bestF);
     } else {
         std::vector<int> Ws, Ts;
         if (c->use_df && c->xi != 0.0) {
@@ -813,12 +853,29 @@ extern "C" pimd_status pimd_autotune(pimd_t c, const char* cache_path)
         if (Ws.empty()) Ws.push_back(bestW);
         if (c->A != 0.0) Ts = {64, 128, 256};
         else Ts = {c->pair_t};
+        // launch shapes: (pair block, helper blocks, force-worker blocks); the
+        // folded shapes hand the SMs the helpers leave to springs and pairs
+        struct Shape { int T, H, F; };
+        std::vector<Shape> shapes;
+        const int H_sep = default_helpers(c->cfg);
+        for (int T : Ts) shapes.push_back({T, H_sep, 0});
+        if (can_fold && sms > 16) {
+            const int nb = (c->N + 1 + 31) / 32;
+            std::vector<int> Hs;
+            for (int H : {nb / 2, nb, 2 * nb, 3 * nb}) {
+                H = std::max(4, std::min(sms - 2 - 8, H));
+                if (std::find(Hs.begin(), Hs.end(), H) == Hs.end()) Hs.push_back(H);
+            }
+            for (int H : Hs) shapes.push_back({c->pair_t, H, sms - 2 - H});
+        }
         double best = 1e30;
         const int W0 = c->cfg.exch_band;
         for (int W : Ws)
-            for (int T : Ts) {
+            for (const Shape& sh : shapes) {
                 c->cfg.exch_band = W;
-                c->pair_t = T;
+                c->pair_t = sh.T;
+                c->n_help = sh.H;
+                c->n_force = sh.F;
                 ctx_views(c);
                 pimd_status st = PIMD_OK;
                 const double ms = time_ms(c->st, 5, [&] {
@@ -828,15 +885,19 @@ extern "C" pimd_status pimd_autotune(pimd_t c, const char* cache_path)
                 if (ms < best) {
                     best = ms;
                     bestW = W;
-                    bestT = T;
+                    bestT = sh.T;
+                    bestH = sh.H;
+                    bestF = sh.F;
                 }
             }
         c->cfg.exch_band = W0;
-        char vb[64];
-        snprintf(vb, sizeof vb, "W=%d;pair_t=%d", bestW, bestT);
+        char vb[96];
+        snprintf(vb, sizeof vb, "W=%d;pair_t=%d;help=%d;fold=%d", bestW, bestT, bestH, bestF);
         cache_store(cache_path, key, vb);
     }
-    if (bestW < 2 || bestW > XDF_MAXW || !pair_block_ok(bestT)) return fail(c, PIMD_EINVAL, "pimd_autotune: bad cache entry");
+    if (bestW < 2 || bestW > XDF_MAXW || !pair_block_ok(bestT) || bestH < 2 || bestF < 0 ||
+        (bestF > 0 && (!can_fold || 2 + bestH + bestF > sms)))
+        return fail(c, PIMD_EINVAL, "pimd_autotune: bad cache entry");
     {
         Layout L;
         XLayout xl;
@@ -845,6 +906,8 @@ extern "C" pimd_status pimd_autotune(pimd_t c, const char* cache_path)
     }
     c->cfg.exch_band = bestW;
     c->pair_t = bestT;
+    c->n_help = bestH;
+    c->n_force = bestF;
     ctx_layout(c);
     ctx_views(c);
     drop_graph(c);
@@ -853,11 +916,13 @@ extern "C" pimd_status pimd_autotune(pimd_t c, const char* cache_path)
     return check_device_error(c);
 }
 
-extern "C" pimd_status pimd_tuning(pimd_t c, int* exch_band, int* pair_block)
+extern "C" pimd_status pimd_tuning(pimd_t c, int* exch_band, int* pair_block, int* helpers, int* force_blocks)
 {
     if (!c || !exch_band || !pair_block) return fail(c, PIMD_EINVAL, "pimd_tuning: NULL argument");
     *exch_band = cfg_band(c->cfg);
     *pair_block = c->pair_t;
+    if (helpers) *helpers = c->n_help;
+    if (force_blocks) *force_blocks = c->n_force;
     return PIMD_OK;
 }
 

@@ -1,0 +1,254 @@
+// Per-(slice, particle-block) units of the springs (a1) and the trap + pair
+// forces (a4), shared by their own kernels and by the force workers of the
+// persistent exchange launch.  Block coordinates and shared-memory scratch
+// come in as arguments; blockDim.x threads, one particle per thread.
+#pragma once
+#include "pimd_md.cuh"
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// double -> float by truncating the significand (round toward zero) with
+// integer operations: on GB300 the hardware F2F.F32.F64 conversion costs
+// about twice an FP64 FMA, the bit manipulation a few integer-pipe ops.
+// Relative error below 2^-23; values below the float normal range give a
+// signed zero and values above it (and NaN) an infinity of the same sign.
+__device__ __forceinline__ float d2f_trunc(double x)
+{
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const int e = (int)((hi >> 20) & 0x7FFu) - 1023 + 127;
+    const unsigned s = hi & 0x80000000u;
+    unsigned b = s | ((unsigned)e << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+    b = e <= 0 ? s : b;
+    b = e >= 255 ? (s | 0x7F800000u) : b;
+    return __uint_as_float(b);
+}
+
+// (a1) Internal ring-polymer springs (Sec. III interior-bead formula and the
+// within-particle half of the exterior-bead formulas): F_l^j = -k (2 r^j -
+// r^{j+1} - r^{j-1}), with the missing neighbour of beads 1 and P dropped.
+// Also the slice's part of sum_l E_int^(l) (always FP64) into part[j*gx + bx].
+__device__ __forceinline__ void springs_unit(const BeadView& b, const ForceParams& fp, double* f, double* part, int bx, int j,
+                                             int gx, double* red /* [32] */)
+{
+    const int l = bx * blockDim.x + threadIdx.x;
+    double e = 0.0;
+    if (l < b.N) {
+        for (int c = 0; c < b.d; ++c) {
+            const size_t o = ((size_t)j * b.d + c) * b.ld + l;
+            const double x = b.r[o];
+            const double xm = (j > 0) ? b.r[o - (size_t)b.d * b.ld] : x;
+            const double xp = (j < b.P - 1) ? b.r[o + (size_t)b.d * b.ld] : x;
+            double fo;
+            if (fp.mixed) {
+                const float xf = d2f_trunc(x);
+                fo = (double)(-(float)fp.ks * ((xf - d2f_trunc(xm)) + (xf - d2f_trunc(xp))));
+            } else {
+                fo = -fp.ks * ((x - xm) + (x - xp));
+            }
+            f[o] = fp.accumulate ? f[o] + fo : fo;
+            if (j < b.P - 1) e = fma(xp - x, xp - x, e);
+        }
+    }
+    double v[1] = {0.5 * fp.ks * e};
+    block_reduce<1>(v, red);
+    if (threadIdx.x == 0) part[j * gx + bx] = v[0];
+}
+
+// (a4) Trap + Gaussian pairs in slice `by` for particles [bx*PT, bx*PT + PT)
+// (Sec. II U, Sec. IV B): F += -grad(V_slice)/P; (energy, virial) partials
+// into part[2*(by*gx + bx)].  FP64 arithmetic.
+template <int D, int PT>
+__device__ __forceinline__ void pair_unit_f64(const BeadView& b, const ForceParams& fp, double* f, double* part, int bx,
+                                              int by, int gx, double* sx /* [D * PT] */, double* red /* [64] */)
+{
+    if (bx * PT >= b.N) {  // a block past this replica's particles
+        if (threadIdx.x == 0) {
+            part[2 * (by * gx + bx) + 0] = 0.0;
+            part[2 * (by * gx + bx) + 1] = 0.0;
+        }
+        return;
+    }
+    const int i = bx * PT + threadIdx.x, j = by;
+    const double* rs = b.r + (size_t)j * D * b.ld;
+    double xi[D], g[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        xi[c] = (i < b.N) ? rs[(size_t)c * b.ld + i] : 0.0;
+        g[c] = 0.0;
+    }
+    double esum = 0.0;
+    if (fp.A != 0.0) {
+        for (int k0 = 0; k0 < b.N; k0 += PT) {
+            const int k = k0 + threadIdx.x;
+#pragma unroll
+            for (int c = 0; c < D; ++c) sx[c * PT + threadIdx.x] = (k < b.N) ? rs[(size_t)c * b.ld + k] : 0.0;
+            __syncthreads();
+            const int kn = min(PT, b.N - k0);
+            for (int kk = 0; kk < kn; ++kk) {
+                double q2 = 0.0, dx[D];
+#pragma unroll
+                for (int c = 0; c < D; ++c) {
+                    dx[c] = xi[c] - sx[c * PT + kk];
+                    q2 = fma(dx[c], dx[c], q2);
+                }
+                double ee = (k0 + kk == i) ? 0.0 : exp(-q2 * fp.inv_s2);
+                esum += ee;
+#pragma unroll
+                for (int c = 0; c < D; ++c) g[c] = fma(ee, dx[c], g[c]);
+            }
+            __syncthreads();
+        }
+    }
+    double v[2] = {0.0, 0.0};
+    if (i < b.N) {
+        const double cpair = -2.0 * fp.A * fp.inv_s2;  // grad_i of A e^{-q2/s2} = cpair * e * dx
+        double t2 = 0.0, vir = 0.0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            const double grad = fp.omega2 * xi[c] + cpair * g[c];
+            const size_t o = ((size_t)j * D + c) * b.ld + i;
+            const double fo = -grad * fp.inv_P;
+            f[o] = fp.accumulate ? f[o] + fo : fo;
+            t2 = fma(xi[c], xi[c], t2);
+            vir = fma(xi[c], grad, vir);
+        }
+        v[0] = 0.5 * fp.omega2 * t2 + 0.5 * fp.A * esum;
+        v[1] = vir;
+    }
+    block_reduce<2>(v, red);
+    if (threadIdx.x == 0) {
+        part[2 * (by * gx + bx) + 0] = v[0];
+        part[2 * (by * gx + bx) + 1] = v[1];
+    }
+}
+
+// FP32 pair arithmetic with exp2 on the MUFU unit; coordinates pre-scaled by
+// sqrt(log2(e))/s so that each pair costs one ex2 and no extra multiply; one
+// particle per thread, partners two at a time on the packed FP32x2 pipe.
+template <int D, int PT>
+__device__ __forceinline__ void pair_unit_f32(const BeadView& b, const ForceParams& fp, double* f, double* part, int bx,
+                                              int by, int gx, float2* sx /* [D * PT / 2] */, double* red /* [64] */)
+{
+    if (bx * PT >= b.N) {  // a block past this replica's particles
+        if (threadIdx.x == 0) {
+            part[2 * (by * gx + bx) + 0] = 0.0;
+            part[2 * (by * gx + bx) + 1] = 0.0;
+        }
+        return;
+    }
+    const int i = bx * PT + threadIdx.x, j = by;
+    const double* rs = b.r + (size_t)j * D * b.ld;
+    const float sc = fp.sc32;
+    double xd[D];
+    float2 xi[D], g[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        xd[c] = (i < b.N) ? rs[(size_t)c * b.ld + i] : 0.0;
+        const float xs = (float)xd[c] * sc;
+        xi[c] = make_float2(xs, xs);
+        g[c] = make_float2(0.f, 0.f);
+    }
+    float2 esum = make_float2(0.f, 0.f);
+    if (fp.A != 0.0) {
+        for (int k0 = 0; k0 < b.N; k0 += PT) {
+            const int k = k0 + threadIdx.x;
+            float* sxf = reinterpret_cast<float*>(sx);
+#pragma unroll
+            for (int c = 0; c < D; ++c)
+                sxf[c * PT + threadIdx.x] = (k < b.N) ? -d2f_trunc(rs[(size_t)c * b.ld + k]) * sc : -1.0e18f;
+            __syncthreads();
+#pragma unroll 4
+            for (int kk = 0; kk < PT / 2; ++kk) {
+                float2 dx[D];
+#pragma unroll
+                for (int c = 0; c < D; ++c) dx[c] = __fadd2_rn(xi[c], sx[c * (PT / 2) + kk]);
+                float2 q2 = __fmul2_rn(dx[0], dx[0]);
+#pragma unroll
+                for (int c = 1; c < D; ++c) q2 = __ffma2_rn(dx[c], dx[c], q2);
+                const float2 ee = make_float2(ex2_approx(-q2.x), ex2_approx(-q2.y));
+                esum = __fadd2_rn(esum, ee);
+#pragma unroll
+                for (int c = 0; c < D; ++c) g[c] = __ffma2_rn(ee, dx[c], g[c]);
+            }
+            __syncthreads();
+        }
+    }
+    double v[2] = {0.0, 0.0};
+    if (i < b.N) {
+        const double cpair = fp.cpair32;
+        double t2 = 0.0, vir = 0.0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            const double grad = fp.omega2 * xd[c] + cpair * ((double)g[c].x + (double)g[c].y);
+            const size_t o = ((size_t)j * D + c) * b.ld + i;
+            const double fo = -grad * fp.inv_P;
+            f[o] = fp.accumulate ? f[o] + fo : fo;
+            t2 = fma(xd[c], xd[c], t2);
+            vir = fma(xd[c], grad, vir);
+        }
+        // the k == i term contributed exp(0) = 1 and no force
+        const double es = fp.A != 0.0 ? (double)esum.x + (double)esum.y - 1.0 : 0.0;
+        v[0] = 0.5 * fp.omega2 * t2 + 0.5 * fp.A * es;
+        v[1] = vir;
+    }
+    block_reduce<2>(v, red);
+    if (threadIdx.x == 0) {
+        part[2 * (by * gx + bx) + 0] = v[0];
+        part[2 * (by * gx + bx) + 1] = v[1];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Force work folded into the persistent exchange launch: the blocks after the
+// chain and helper blocks take (slice, particle-block) units from a counter
+// and compute the springs (overwriting F) and the trap + pairs (adding into
+// F) of each unit.  They wait on nothing, so they only fill SMs the exchange
+// recursion leaves idle.
+struct ForceWork {
+    BeadView b;
+    ForceParams fp;      // accumulate is set per part
+    double* part_spr;    // springs partials [gx * P]
+    double* part_pair;   // pair partials [gx * P][2]
+    int gx;              // particle blocks of blockDim.x per slice
+    int* counter;        // next unit; zeroed before the launch
+};
+
+// Shared-memory bytes a force worker needs (blockDim.x = 256 particles).
+constexpr int FW_SMEM = 16 + 96 * 8 + 3 * 256 * 8;
+
+template <int D, bool MIXED>
+__device__ void force_worker_t(const ForceWork& w, unsigned char* smem)
+{
+    constexpr int PT = 256;
+    int* su = reinterpret_cast<int*>(smem);
+    double* red = reinterpret_cast<double*>(smem + 16);  // [64] pairs, then [32] springs
+    unsigned char* sx = smem + 16 + 96 * 8;
+    const int nu = w.gx * w.b.P;
+    ForceParams fs = w.fp, fq = w.fp;
+    fs.accumulate = 0;
+    fq.accumulate = 1;
+    for (;;) {
+        if (threadIdx.x == 0) *su = atomicAdd(w.counter, 1);
+        block_sync();
+        const int u = *su;
+        block_sync();  // every thread has the unit before thread 0 takes the next
+        if (u >= nu) break;
+        const int j = u / w.gx, bx = u % w.gx;
+        springs_unit(w.b, fs, w.b.f, w.part_spr, bx, j, w.gx, red + 64);
+        if (MIXED) pair_unit_f32<D, PT>(w.b, fq, w.b.f, w.part_pair, bx, j, w.gx, reinterpret_cast<float2*>(sx), red);
+        else pair_unit_f64<D, PT>(w.b, fq, w.b.f, w.part_pair, bx, j, w.gx, reinterpret_cast<double*>(sx), red);
+    }
+}
+
+__device__ __forceinline__ void force_worker(const ForceWork& w, unsigned char* smem)
+{
+    const bool mixed = w.fp.mixed != 0;
+    if (w.b.d == 1) mixed ? force_worker_t<1, true>(w, smem) : force_worker_t<1, false>(w, smem);
+    else if (w.b.d == 2) mixed ? force_worker_t<2, true>(w, smem) : force_worker_t<2, false>(w, smem);
+    else mixed ? force_worker_t<3, true>(w, smem) : force_worker_t<3, false>(w, smem);
+}

@@ -3,35 +3,14 @@
 #include <math.h>
 
 #include "pimd_batch.cuh"
+#include "pimd_forcework.cuh"
 
 namespace {
 
 constexpr int SPR_T = 128;
-constexpr int PAIR_T = 128;
 constexpr int MD_T = 256;
 
-__device__ __forceinline__ float ex2_approx(float x)
-{
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
 
-// double -> float by truncating the significand (round toward zero) with
-// integer operations: on GB300 the hardware F2F.F32.F64 conversion costs
-// about twice an FP64 FMA, the bit manipulation a few integer-pipe ops.
-// Relative error below 2^-23; values below the float normal range give a
-// signed zero and values above it (and NaN) an infinity of the same sign.
-__device__ __forceinline__ float d2f_trunc(double x)
-{
-    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
-    const int e = (int)((hi >> 20) & 0x7FFu) - 1023 + 127;
-    const unsigned s = hi & 0x80000000u;
-    unsigned b = s | ((unsigned)e << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
-    b = e <= 0 ? s : b;
-    b = e >= 255 ? (s | 0x7F800000u) : b;
-    return __uint_as_float(b);
-}
 
 // ---------------------------------------------------------------------------
 // (a1) Internal ring-polymer springs (Sec. III interior-bead formula and the
@@ -41,28 +20,7 @@ __device__ __forceinline__ float d2f_trunc(double x)
 __device__ __forceinline__ void springs_body(const BeadView& b, const ForceParams& fp, double* f, double* part)
 {
     __shared__ double red[32];
-    const int l = blockIdx.x * SPR_T + threadIdx.x, j = blockIdx.y;
-    double e = 0.0;
-    if (l < b.N) {
-        for (int c = 0; c < b.d; ++c) {
-            const size_t o = ((size_t)j * b.d + c) * b.ld + l;
-            const double x = b.r[o];
-            const double xm = (j > 0) ? b.r[o - (size_t)b.d * b.ld] : x;
-            const double xp = (j < b.P - 1) ? b.r[o + (size_t)b.d * b.ld] : x;
-            double fo;
-            if (fp.mixed) {
-                const float xf = d2f_trunc(x);
-                fo = (double)(-(float)fp.ks * ((xf - d2f_trunc(xm)) + (xf - d2f_trunc(xp))));
-            } else {
-                fo = -fp.ks * ((x - xm) + (x - xp));
-            }
-            f[o] = fp.accumulate ? f[o] + fo : fo;
-            if (j < b.P - 1) e = fma(xp - x, xp - x, e);
-        }
-    }
-    double v[1] = {0.5 * fp.ks * e};
-    block_reduce<1>(v, red);
-    if (threadIdx.x == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = v[0];
+    springs_unit(b, fp, f, part, blockIdx.x, blockIdx.y, gridDim.x, red);
 }
 
 __global__ void __launch_bounds__(SPR_T) springs_kernel(BeadView b, ForceParams fp, double* f, double* part)
@@ -79,67 +37,9 @@ __global__ void __launch_bounds__(SPR_T) springs_kernel(BeadView b, ForceParams 
 template <int D, int PT>
 __device__ __forceinline__ void pair_body_f64(const BeadView& b, const ForceParams& fp, double* f, double* part)
 {
-    __shared__ double sx[D][PT];
+    __shared__ double sx[D * PT];
     __shared__ double red[64];
-    if (blockIdx.x * PT >= b.N) {  // a block past this replica's particles
-        if (threadIdx.x == 0) {
-            part[2 * (blockIdx.y * gridDim.x + blockIdx.x) + 0] = 0.0;
-            part[2 * (blockIdx.y * gridDim.x + blockIdx.x) + 1] = 0.0;
-        }
-        return;
-    }
-    const int i = blockIdx.x * PT + threadIdx.x, j = blockIdx.y;
-    const double* rs = b.r + (size_t)j * D * b.ld;
-    double xi[D], g[D];
-#pragma unroll
-    for (int c = 0; c < D; ++c) {
-        xi[c] = (i < b.N) ? rs[(size_t)c * b.ld + i] : 0.0;
-        g[c] = 0.0;
-    }
-    double esum = 0.0;
-    if (fp.A != 0.0) {
-        for (int k0 = 0; k0 < b.N; k0 += PT) {
-            const int k = k0 + threadIdx.x;
-#pragma unroll
-            for (int c = 0; c < D; ++c) sx[c][threadIdx.x] = (k < b.N) ? rs[(size_t)c * b.ld + k] : 0.0;
-            __syncthreads();
-            const int kn = min(PT, b.N - k0);
-            for (int kk = 0; kk < kn; ++kk) {
-                double q2 = 0.0, dx[D];
-#pragma unroll
-                for (int c = 0; c < D; ++c) {
-                    dx[c] = xi[c] - sx[c][kk];
-                    q2 = fma(dx[c], dx[c], q2);
-                }
-                double ee = (k0 + kk == i) ? 0.0 : exp(-q2 * fp.inv_s2);
-                esum += ee;
-#pragma unroll
-                for (int c = 0; c < D; ++c) g[c] = fma(ee, dx[c], g[c]);
-            }
-            __syncthreads();
-        }
-    }
-    double v[2] = {0.0, 0.0};
-    if (i < b.N) {
-        const double cpair = -2.0 * fp.A * fp.inv_s2;  // grad_i of A e^{-q2/s2} = cpair * e * dx
-        double t2 = 0.0, vir = 0.0;
-#pragma unroll
-        for (int c = 0; c < D; ++c) {
-            const double grad = fp.omega2 * xi[c] + cpair * g[c];
-            const size_t o = ((size_t)j * D + c) * b.ld + i;
-            const double fo = -grad * fp.inv_P;
-            f[o] = fp.accumulate ? f[o] + fo : fo;
-            t2 = fma(xi[c], xi[c], t2);
-            vir = fma(xi[c], grad, vir);
-        }
-        v[0] = 0.5 * fp.omega2 * t2 + 0.5 * fp.A * esum;
-        v[1] = vir;
-    }
-    block_reduce<2>(v, red);
-    if (threadIdx.x == 0) {
-        part[2 * (blockIdx.y * gridDim.x + blockIdx.x) + 0] = v[0];
-        part[2 * (blockIdx.y * gridDim.x + blockIdx.x) + 1] = v[1];
-    }
+    pair_unit_f64<D, PT>(b, fp, f, part, blockIdx.x, blockIdx.y, gridDim.x, sx, red);
 }
 
 // FP32 pair arithmetic with exp2 on the MUFU unit; coordinates pre-scaled by
@@ -150,75 +50,9 @@ __device__ __forceinline__ void pair_body_f64(const BeadView& b, const ForcePara
 template <int D, int PT>
 __device__ __forceinline__ void pair_body_f32(const BeadView& b, const ForceParams& fp, double* f, double* part)
 {
-    __shared__ float2 sx[D][PT / 2];
+    __shared__ float2 sx[D * PT / 2];
     __shared__ double red[64];
-    if (blockIdx.x * PT >= b.N) {  // a block past this replica's particles
-        if (threadIdx.x == 0) {
-            part[2 * (blockIdx.y * gridDim.x + blockIdx.x) + 0] = 0.0;
-            part[2 * (blockIdx.y * gridDim.x + blockIdx.x) + 1] = 0.0;
-        }
-        return;
-    }
-    const int i = blockIdx.x * PT + threadIdx.x, j = blockIdx.y;
-    const double* rs = b.r + (size_t)j * D * b.ld;
-    const float sc = fp.sc32;
-    double xd[D];
-    float2 xi[D], g[D];
-#pragma unroll
-    for (int c = 0; c < D; ++c) {
-        xd[c] = (i < b.N) ? rs[(size_t)c * b.ld + i] : 0.0;
-        const float xs = (float)xd[c] * sc;
-        xi[c] = make_float2(xs, xs);
-        g[c] = make_float2(0.f, 0.f);
-    }
-    float2 esum = make_float2(0.f, 0.f);
-    if (fp.A != 0.0) {
-        for (int k0 = 0; k0 < b.N; k0 += PT) {
-            const int k = k0 + threadIdx.x;
-            float* sxf = reinterpret_cast<float*>(&sx[0][0]);
-#pragma unroll
-            for (int c = 0; c < D; ++c)
-                sxf[c * PT + threadIdx.x] = (k < b.N) ? -d2f_trunc(rs[(size_t)c * b.ld + k]) * sc : -1.0e18f;
-            __syncthreads();
-#pragma unroll 4
-            for (int kk = 0; kk < PT / 2; ++kk) {
-                float2 dx[D];
-#pragma unroll
-                for (int c = 0; c < D; ++c) dx[c] = __fadd2_rn(xi[c], sx[c][kk]);
-                float2 q2 = __fmul2_rn(dx[0], dx[0]);
-#pragma unroll
-                for (int c = 1; c < D; ++c) q2 = __ffma2_rn(dx[c], dx[c], q2);
-                const float2 ee = make_float2(ex2_approx(-q2.x), ex2_approx(-q2.y));
-                esum = __fadd2_rn(esum, ee);
-#pragma unroll
-                for (int c = 0; c < D; ++c) g[c] = __ffma2_rn(ee, dx[c], g[c]);
-            }
-            __syncthreads();
-        }
-    }
-    double v[2] = {0.0, 0.0};
-    if (i < b.N) {
-        const double cpair = fp.cpair32;
-        double t2 = 0.0, vir = 0.0;
-#pragma unroll
-        for (int c = 0; c < D; ++c) {
-            const double grad = fp.omega2 * xd[c] + cpair * ((double)g[c].x + (double)g[c].y);
-            const size_t o = ((size_t)j * D + c) * b.ld + i;
-            const double fo = -grad * fp.inv_P;
-            f[o] = fp.accumulate ? f[o] + fo : fo;
-            t2 = fma(xd[c], xd[c], t2);
-            vir = fma(xd[c], grad, vir);
-        }
-        // the k == i term contributed exp(0) = 1 and no force
-        const double es = fp.A != 0.0 ? (double)esum.x + (double)esum.y - 1.0 : 0.0;
-        v[0] = 0.5 * fp.omega2 * t2 + 0.5 * fp.A * es;
-        v[1] = vir;
-    }
-    block_reduce<2>(v, red);
-    if (threadIdx.x == 0) {
-        part[2 * (blockIdx.y * gridDim.x + blockIdx.x) + 0] = v[0];
-        part[2 * (blockIdx.y * gridDim.x + blockIdx.x) + 1] = v[1];
-    }
+    pair_unit_f32<D, PT>(b, fp, f, part, blockIdx.x, blockIdx.y, gridDim.x, sx, red);
 }
 
 template <int D, int PT>

@@ -3,8 +3,10 @@
 // The equations are stated in pimd_xdf.cuh.
 #include <math.h>
 #include <stdio.h>
+#include <string.h>
 
 #include "pimd_batch.cuh"
+#include "pimd_forcework.cuh"
 
 namespace {
 
@@ -1208,7 +1210,7 @@ __device__ void xhelper(const XView& v, DfwTile* T, WeightSmem* Ws, ChainS* cs, 
     }
 }
 
-__global__ void __launch_bounds__(XDF_THREADS, 1) xdf_recursion_kernel(XView v)
+__global__ void __launch_bounds__(XDF_THREADS, 1) xdf_recursion_kernel(XView v, ForceWork fw)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     DfwTile* T = reinterpret_cast<DfwTile*>(smem_raw);
@@ -1223,7 +1225,8 @@ __global__ void __launch_bounds__(XDF_THREADS, 1) xdf_recursion_kernel(XView v)
     if (bid == 0) xchain<0>(v, T, cs);
     else if (bid == 1) xchain<1>(v, T, cs);
     else if (bid - 2 < v.n_help_f) xhelper<0>(v, T, Ws, cs, tab, bid - 2);
-    else xhelper<1>(v, T, Ws, cs, tab, bid - 2 - v.n_help_f);
+    else if (bid - 2 - v.n_help_f < v.n_help_b) xhelper<1>(v, T, Ws, cs, tab, bid - 2 - v.n_help_f);
+    else force_worker(fw, smem_raw);
 }
 
 // Band sums: forward row block J over tiles I in [J-W+1, J]; backward column
@@ -1640,7 +1643,7 @@ size_t xdf_recursion_smem(int W)
 static size_t band_smem(int nw) { return nw * (sizeof(DfwTile) + sizeof(WeightSmem) + 32 * sizeof(DVAcc)); }
 static size_t blockops_smem() { return 4 * sizeof(DfwTile); }
 
-cudaError_t xdf_launch_forward(const XView& v, cudaStream_t st, ProfMarks* pm)
+cudaError_t xdf_launch_forward(const XView& v, cudaStream_t st, ProfMarks* pm, const ForceWork* fw, int n_force)
 {
     xdf_prep_kernel<<<xdf_prep_blocks(v.npad), XDF_SMALL_T, 0, st>>>(v);
     prof_mark(pm, "exch_prep", st);
@@ -1666,7 +1669,10 @@ cudaError_t xdf_launch_forward(const XView& v, cudaStream_t st, ProfMarks* pm)
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(2 + v.n_help_f + v.n_help_b);
+    ForceWork none;
+    memset(&none, 0, sizeof none);
+    if (!fw || n_force < 0) n_force = 0;
+    cfg.gridDim = dim3(2 + v.n_help_f + v.n_help_b + n_force);
     cfg.blockDim = dim3(XDF_THREADS);
     cfg.dynamicSmemBytes = xdf_recursion_smem(v.W);
     cfg.stream = st;
@@ -1675,7 +1681,7 @@ cudaError_t xdf_launch_forward(const XView& v, cudaStream_t st, ProfMarks* pm)
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, xdf_recursion_kernel, v);
+    e = cudaLaunchKernelEx(&cfg, xdf_recursion_kernel, v, n_force > 0 ? *fw : none);
     prof_mark(pm, "exch_recursion", st);
     return e;
 }

@@ -89,6 +89,10 @@ int xdf_prep_blocks(int npad);
 int xdf_finalize_blocks(int N);
 size_t xdf_recursion_smem(int W);
 cudaError_t xdf_upload_table(float2* dev_table, cudaStream_t st);
-cudaError_t xdf_launch_forward(const XView& v, cudaStream_t st, ProfMarks* pm);
+struct ForceWork;
+// fw (nullable) with n_force > 0 folds the springs and trap + pair forces into
+// the recursion launch as n_force extra blocks.
+cudaError_t xdf_launch_forward(const XView& v, cudaStream_t st, ProfMarks* pm, const ForceWork* fw = nullptr,
+                               int n_force = 0);
 cudaError_t xdf_launch_adjoint(const XView& v, const FinalizeOut& o, cudaStream_t st, ProfMarks* pm);
 cudaError_t xdf_launch_vb_value(const XView& v, double* V_out, cudaStream_t st);

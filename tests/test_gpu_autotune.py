@@ -44,13 +44,57 @@ def test_every_candidate_gives_the_same_forces(tmp_path, prec, tol):
             key = open(key_probe).read().split("|")[0]
             forced = str(tmp_path / ("forced_%d_%d.txt" % (W, T)))
             open(forced, "w").write("%s|W=%d;pair_t=%d\n" % (key, W, T))
-            assert S.autotune(forced) == {"exch_band": W, "pair_block": T}
+            t = S.autotune(forced)
+            assert (t["exch_band"], t["pair_block"]) == (W, T)
             F = S.forces_array()
             S.close()
             if ref is None:
                 ref = F
             else:
                 assert rel_inf(F, ref) < tol, (W, T)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("N,P,d", [(1600, 32, 2), (257, 6, 3), (1000, 4, 1)])
+def test_folded_force_workers_match_oracle(tmp_path, prec, N, P, d):
+    """Springs and trap + pairs computed by force workers inside the recursion
+    launch, for several helper / worker splits and the separate-kernel shape:
+    each matches the oracle, and the shapes agree with one another.
+
+    FP64 tolerance: the endpoint forces are ratios of Boltzmann weights whose
+    exponents reach beta*|V_xi| (about 1.6e6 for N = 1600, P = 32 with beads
+    drawn independently), so any FP64 evaluation of them -- the oracle's too --
+    carries relative rounding of order eps*beta*|V_xi|; the bound is
+    max(1e-10, 16 eps beta |V_xi|).  Mixed precision: 1e-5."""
+    import torch
+
+    import paper_2404_02628_gb300 as pkg
+    beta, xi, g, s = 2.0, 1.0, 3.0, 0.5
+    r = beads(N, P, d, 1720 + N)
+    Fo, info = oracle.forces(r, beta, xi, 1.0, amplitude(g, s), s)
+    tol = max(1e-10, 16 * np.finfo(float).eps * beta * abs(info["V_xi"])) if prec == 0 else 1e-5
+    same = 1e-12 if prec == 0 else 1e-5
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    F0 = est0 = None
+    for H, Fb in ((sms - 2, 0), (8, sms - 10), (40, sms - 42), (sms - 12, 10)):
+        S = pkg.System(N, P, d, beta, 1.0, g, s, xi, r=r, precision=prec)
+        probe = str(tmp_path / ("probe_%d_%d_%d.txt" % (N, H, prec)))
+        t0 = S.autotune(probe)
+        key = open(probe).read().split("|")[0]
+        forced = str(tmp_path / ("forced_%d_%d_%d.txt" % (N, H, prec)))
+        open(forced, "w").write("%s|W=%d;pair_t=128;help=%d;fold=%d\n" % (key, t0["exch_band"], H, Fb))
+        t = S.autotune(forced)
+        assert (t["helpers"], t["force_blocks"]) == (H, Fb)
+        F = S.forces_array()
+        assert rel_inf(F, Fo) < tol, (H, Fb)
+        est = S.estimators()
+        if F0 is None:
+            F0, est0 = F, est
+        else:
+            assert rel_inf(F, F0) < same, (H, Fb)
+            for k in ("E_prim", "E_vir", "V_xi", "U_over_P", "spring", "virial"):
+                assert abs(est[k] - est0[k]) <= same * max(1.0, abs(est0[k])), (k, H, Fb)
+        S.close()
 
 
 def test_batch_autotune_keeps_oracle_parity(tmp_path):
