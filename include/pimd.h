@@ -175,6 +175,18 @@ pimd_status pimd_state_bytes(pimd_t ctx, size_t* bytes);
 pimd_status pimd_get_state(pimd_t ctx, void* host_blob, size_t bytes);
 pimd_status pimd_set_state(pimd_t ctx, const void* host_blob, size_t bytes);
 
+/* Seeded initial state on the device (Sec. IV: beads drawn from N(0, 1) per
+ * coordinate; momenta Maxwell-Boltzmann at kT = 1/beta, i.e. N(0, m/beta)).
+ * Generator: splitmix64 (Steele, Lea & Flood, OOPSLA 2014) used counter-wise,
+ * output i of stream `seed` = mix(seed + (i + 1) * 0x9E3779B97F4A7C15).
+ * Coordinate (q, j, c, l) -- q = 0 beads, 1 momenta; bead j < P, component
+ * c < d, particle l < N -- has counter k = ((q P + j) d + c) N + l and uses
+ * outputs 2k and 2k + 1 as uniforms u = ((x >> 11) + 1) 2^-53 in (0, 1]:
+ * z = sqrt(-2 ln u1) cos(2 pi u2).  Writes r and p of the bound buffers
+ * (padding columns zero), zeroes the thermostats and the step counter, and
+ * computes the forces of the new r.  Stream-ordered, asynchronous. */
+pimd_status pimd_init_state(pimd_t ctx, unsigned long long seed);
+
 /* Runs nsteps MD steps without the graph, with CUDA events between kernels
  * on the bound stream; ms_out[slot] accumulates each kernel's time (slot
  * names from pimd_profile_slot_name).  *n_slots receives the kernel count of
@@ -243,6 +255,9 @@ pimd_status pimd_batch_workspace_bytes(pimd_batch_t b, size_t* bytes);
  * forces of r; r and p must hold the initial state. */
 pimd_status pimd_batch_bind(pimd_batch_t b, const pimd_batch_buffers* bufs, void* stream);
 pimd_status pimd_batch_forces(pimd_batch_t b);
+/* As pimd_init_state for every replica; replica r uses the stream whose seed
+ * is output r of the splitmix64 stream `seed`. */
+pimd_status pimd_batch_init_state(pimd_batch_t b, unsigned long long seed);
 /* Captures one batched step as a CUDA graph on a private stream (done by the
  * first pimd_batch_step otherwise). */
 pimd_status pimd_batch_capture_graph(pimd_batch_t b);

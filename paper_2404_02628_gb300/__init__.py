@@ -25,7 +25,7 @@ __all__ = [
     "pimd_batch_bind", "pimd_batch_forces", "pimd_batch_capture_graph", "pimd_batch_step",
     "pimd_batch_step_eager", "pimd_batch_step_profiled", "pimd_batch_profile_slot_name",
     "pimd_batch_estimators", "pimd_batch_sync", "pimd_batch_last_error", "pimd_batch_destroy",
-    "pimd_batch_autotune", "pimd_autotune", "pimd_tuning",
+    "pimd_batch_autotune", "pimd_autotune", "pimd_tuning", "pimd_init_state", "pimd_batch_init_state",
 ]
 
 PIMD_OK, PIMD_EINVAL, PIMD_ENOMEM, PIMD_ECUDA, PIMD_ETIMEOUT, PIMD_ENONFINITE, PIMD_ESTATE = range(7)
@@ -125,6 +125,8 @@ _SIGS = {
     "pimd_batch_last_error": ([_vp], ctypes.c_char_p),
     "pimd_batch_destroy": ([_vp], None),
     "pimd_autotune": ([_vp, ctypes.c_char_p], ctypes.c_int),
+    "pimd_init_state": ([_vp, ctypes.c_ulonglong], ctypes.c_int),
+    "pimd_batch_init_state": ([_vp, ctypes.c_ulonglong], ctypes.c_int),
     "pimd_tuning": ([_vp] + [ctypes.POINTER(ctypes.c_int)] * 4, ctypes.c_int),
     "pimd_batch_autotune": ([_vp, ctypes.c_char_p], ctypes.c_int),
 }
@@ -385,6 +387,14 @@ def pimd_batch_autotune(h, cache_path=None):
     return _bcheck(lib().pimd_batch_autotune(h, cache_path.encode() if cache_path else None), h)
 
 
+def pimd_init_state(h, seed):
+    return _check(lib().pimd_init_state(h, int(seed) & 0xFFFFFFFFFFFFFFFF), h)
+
+
+def pimd_batch_init_state(h, seed):
+    return _bcheck(lib().pimd_batch_init_state(h, int(seed) & 0xFFFFFFFFFFFFFFFF), h)
+
+
 def pimd_autotune(h, cache_path=None):
     return _check(lib().pimd_autotune(h, cache_path.encode() if cache_path else None), h)
 
@@ -458,6 +468,10 @@ class Batch:
 
     def step(self, n=1, graph=True):
         (pimd_batch_step if graph else pimd_batch_step_eager)(self.h, n)
+
+    def init_state(self, seed):
+        """Seeded beads and momenta on the device for every replica (pimd_batch_init_state)."""
+        pimd_batch_init_state(self.h, seed)
 
     def autotune(self, cache_path=None):
         pimd_batch_autotune(self.h, cache_path)
@@ -551,6 +565,10 @@ class System:
 
     def step(self, n=1, graph=True):
         (pimd_step if graph else pimd_step_eager)(self.h, n)
+
+    def init_state(self, seed):
+        """Seeded beads and momenta on the device (pimd_init_state)."""
+        pimd_init_state(self.h, seed)
 
     def autotune(self, cache_path=None):
         pimd_autotune(self.h, cache_path)

@@ -346,7 +346,7 @@ static void ctx_layout(pimd_ctx* c)
     else exch_layout(c->L, c->ex, c->N, EX_STREAMS, c->cfg.table_mode == PIMD_TABLE_STORE);
     c->off_spr = c->L.add((size_t)springs_grid_x(c->N) * c->P * sizeof(double));
     c->off_pair = c->L.add((size_t)pair_grid_x(c->N, PAIR_T_MIN) * c->P * 2 * sizeof(double));
-    c->off_fin = c->L.add((size_t)exch_finalize_blocks(c->N) * sizeof(double));
+    c->off_fin = c->L.add((size_t)std::max(exch_finalize_blocks(c->N), xdf_finalize_blocks(c->N)) * sizeof(double));
     c->off_md = c->L.add((size_t)md_blocks(c->N, c->P, c->d) * 2 * sizeof(double));
     c->off_sc = c->L.add(SC_COUNT * sizeof(double));
     c->off_flag = c->L.add(4 * sizeof(int));
@@ -1048,6 +1048,21 @@ extern "C" pimd_status pimd_set_state(pimd_t c, const void* host, size_t bytes)
     return PIMD_OK;
 }
 
+extern "C" pimd_status pimd_init_state(pimd_t c, unsigned long long seed)
+{
+    if (!c) return fail(c, PIMD_EINVAL, "pimd_init_state: NULL handle");
+    if (!c->bound) return fail(c, PIMD_ESTATE, "pimd_init_state: not bound");
+    cudaError_t e = launch_init_state(c->bv, sqrt(c->mp.mass * c->mp.kT), seed, c->st);
+    if (e == cudaSuccess && c->cfg.thermostat) {
+        const size_t n = (size_t)c->cfg.nhc_len * c->P * c->d * c->buf.n_pad;
+        e = cudaMemsetAsync(c->buf.eta, 0, n * sizeof(double), c->st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->buf.peta, 0, n * sizeof(double), c->st);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "pimd_init_state");
+    c->steps = 0;
+    return enqueue_forces(c, c->st, c->buf.f, true, true);
+}
+
 extern "C" pimd_status pimd_sync(pimd_t c)
 {
     if (!c) return fail(c, PIMD_EINVAL, "pimd_sync: NULL handle");
@@ -1452,6 +1467,24 @@ extern "C" pimd_status pimd_batch_bind(pimd_batch_t b, const pimd_batch_buffers*
         return s;
     }
     return PIMD_OK;
+}
+
+extern "C" pimd_status pimd_batch_init_state(pimd_batch_t b, unsigned long long seed)
+{
+    if (!b) return bfail(b, PIMD_EINVAL, "pimd_batch_init_state: NULL handle");
+    if (!b->bound) return bfail(b, PIMD_ESTATE, "pimd_batch_init_state: not bound");
+    cudaError_t e = cudaSuccess;
+    for (int r = 0; r < b->R && e == cudaSuccess; ++r)
+        e = launch_init_state(b->args[r].bv, sqrt(b->args[r].mp.mass * b->args[r].mp.kT),
+                              splitmix64_at(seed, (unsigned long long)r), b->st);
+    if (e == cudaSuccess && b->cfg.thermostat) {
+        const size_t n = (size_t)b->cfg.nhc_len * b->off[b->R];
+        e = cudaMemsetAsync(b->buf.eta, 0, n * sizeof(double), b->st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->buf.peta, 0, n * sizeof(double), b->st);
+    }
+    if (e != cudaSuccess) return bcuda(b, e, "pimd_batch_init_state");
+    b->steps = 0;
+    return batch_enqueue_forces(b, b->st);
 }
 
 extern "C" pimd_status pimd_batch_forces(pimd_batch_t b)

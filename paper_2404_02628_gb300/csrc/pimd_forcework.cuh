@@ -28,6 +28,18 @@ __device__ __forceinline__ float d2f_trunc(double x)
     return __uint_as_float(b);
 }
 
+// float -> double on the integer pipe (exact): exponent rebiased, significand
+// shifted into place.  Zero, subnormal, infinite and NaN inputs take the
+// hardware conversion.
+__device__ __forceinline__ double f2d_exact(float x)
+{
+    const unsigned b = __float_as_uint(x);
+    const unsigned e = (b >> 23) & 0xFFu;
+    if (e == 0u || e == 0xFFu) return (double)x;
+    const unsigned hi = (b & 0x80000000u) | ((e - 127u + 1023u) << 20) | ((b & 0x7FFFFFu) >> 3);
+    return __hiloint2double((int)hi, (int)(b << 29));
+}
+
 // (a1) Internal ring-polymer springs (Sec. III interior-bead formula and the
 // within-particle half of the exterior-bead formulas): F_l^j = -k (2 r^j -
 // r^{j+1} - r^{j-1}), with the missing neighbour of beads 1 and P dropped.

@@ -1,5 +1,6 @@
 // Springs (a1), trap + pairs (a4), NHC velocity Verlet (a5) and scalar
 // reductions for sm_103a.
+#include <algorithm>
 #include <math.h>
 
 #include "pimd_batch.cuh"
@@ -74,31 +75,82 @@ __global__ void __launch_bounds__(PT) pair_kernel_f32(BeadView b, ForceParams fp
 // momentum scaled by exp(-tau p_1/Q), positions eta += tau p_eta/Q, then the
 // links again in the opposite order.
 
-// FP64 <-> double-float without the FP64->FP32 hardware conversion: the high
-// part is x with its significand truncated to 24 bits (integer pipe), the
-// low part the FP64-exact remainder, truncated the same way (about 2^-47
-// relative overall).
+// FP64 <-> double-float on the integer pipe: the FP64 conversions and adds
+// run on the FP64 pipe, which on this part is the bottleneck of the
+// thermostat kernels, so both directions take the bit fields apart instead.
+// FP64 -> df: the high part is x with its significand truncated to 24 bits,
+// the low part the remaining 29 significand bits as a float (rounded to 24
+// bits: about 2^-47 relative overall).  Exponents outside [-70, 100] (and
+// zero, infinities, NaN) take the FP64 route.
 __device__ __forceinline__ df d2df(double x)
 {
-    const float h = d2f_trunc(x);
-    return df{h, d2f_trunc(x - (double)h)};
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const int E = (int)((hi >> 20) & 0x7FFu) - 1023;
+    if (E < -70 || E > 100) {
+        const float h = d2f_trunc(x);
+        return df{h, d2f_trunc(x - (double)h)};
+    }
+    const unsigned sgn = hi & 0x80000000u;
+    const float h = __uint_as_float(sgn | ((unsigned)(E + 127) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
+    const float scale = __uint_as_float((unsigned)(E - 52 + 127) << 23);  // 2^(E-52), a normal float
+    const float l = __uint_as_float(__float_as_uint(__uint2float_rn(lo & 0x1FFFFFFFu) * scale) | sgn);
+    return df{h, l};
 }
-__device__ __forceinline__ double df2d(df a) { return (double)a.h + (double)a.l; }
+
+// df -> FP64: the 24-bit significand of h widened to 53 bits, the low part's
+// significand added (or subtracted) at its offset, one renormalising shift.
+// Bits of l below the FP64 unit are truncated (at most 2 ulp).  Parts outside
+// the normal range, or an l too large for a normalised pair, take the FP64
+// route.
+__device__ __forceinline__ double df2d(df a)
+{
+    const unsigned hb = __float_as_uint(a.h), lb = __float_as_uint(a.l);
+    const int Eh = (int)((hb >> 23) & 0xFFu) - 127;
+    const int El = (int)((lb >> 23) & 0xFFu) - 127;
+    const int sh = El - Eh + 29;  // offset of l's significand in units of 2^(Eh-52)
+    const bool l_zero = (lb & 0x7FFFFFFFu) == 0u;
+    if (Eh < -100 || Eh > 100 || (!l_zero && (El == -127 || sh > 6))) return (double)a.h + (double)a.l;
+    unsigned long long M = (unsigned long long)((hb & 0x7FFFFFu) | 0x800000u) << 29;
+    int E = Eh;
+    if (!l_zero && sh > -25) {
+        const unsigned long long ml = (lb & 0x7FFFFFu) | 0x800000u;
+        const unsigned long long L = sh >= 0 ? ml << sh : ml >> (-sh);
+        if ((hb ^ lb) & 0x80000000u) {
+            M -= L;
+            if (M < (1ull << 52)) {
+                M <<= 1;
+                E -= 1;
+            }
+        } else {
+            M += L;
+            if (M >= (1ull << 53)) {
+                M >>= 1;
+                E += 1;
+            }
+        }
+    }
+    const unsigned long long bits = ((unsigned long long)(hb & 0x80000000u) << 32) |
+                                    ((unsigned long long)(E + 1023) << 52) | (M & ((1ull << 52) - 1));
+    return __longlong_as_double((long long)bits);
+}
 __device__ __forceinline__ df dfc(const float (&c)[2]) { return df{c[0], c[1]}; }
 
-// e^x for a double-float x: the Taylor polynomial of degree 8 (Horner form)
-// for |x| <= 1/32, where it truncates below (1/32)^9/9! < 1e-19 relative;
-// the thermostat's arguments are of order 1e-3.  Larger |x| through the FP64
-// library exp.
+// e^x for a double-float x, |x| <= 1/32: the Taylor series to x^4 in
+// double-float (Horner form), the rest, x^5/120 (1 + x/6 + x^2/42 + x^3/336),
+// in FP32 from the high part -- it is below 2.5e-10, so its FP32 rounding
+// stays under 1e-16 -- and the truncation after x^8 below (1/32)^9/9! < 1e-19.
+// The thermostat's arguments are of order 1e-3; larger |x| go through the
+// FP64 library exp.
 __device__ __forceinline__ df df_exp_small(df x)
 {
     if (!(fabsf(x.h) <= 0.03125f)) return d2df(exp(df2d(x)));
 #define PIMD_DFC(v) df{(float)(v), (float)((v) - (double)(float)(v))}
-    df s = PIMD_DFC(1.0 / 40320.0);
-    s = df_add(df_mul(s, x), PIMD_DFC(1.0 / 5040.0));
-    s = df_add(df_mul(s, x), PIMD_DFC(1.0 / 720.0));
-    s = df_add(df_mul(s, x), PIMD_DFC(1.0 / 120.0));
-    s = df_add(df_mul(s, x), PIMD_DFC(1.0 / 24.0));
+    const float xh = x.h;
+    float t = fmaf(xh, 1.0f / 336.0f, 1.0f / 42.0f);
+    t = fmaf(xh, t, 1.0f / 6.0f);
+    t = fmaf(xh, t, 1.0f);
+    t = xh * t * (1.0f / 120.0f);
+    df s = df_add(PIMD_DFC(1.0 / 24.0), df{t, 0.f});
     s = df_add(df_mul(s, x), PIMD_DFC(1.0 / 6.0));
     s = df_add(df_mul(s, x), df{0.5f, 0.f});
     s = df_add(df_mul(s, x), df{1.f, 0.f});
@@ -173,7 +225,7 @@ __device__ __forceinline__ void nhc_half_step_f32(double& p, double (&eta)[M], d
         q[k] = fmaf(q[k], a * a, cg * G * a);
     }
     const float sp = ex2_approx(-tau * inv_Q * L2E * q[0]);
-    p *= (double)sp;
+    p *= f2d_exact(sp);
     pf = d2f_trunc(p);
 #pragma unroll
     for (int k = 0; k < M; ++k) e[k] = fmaf(ce, q[k], e[k]);
@@ -187,8 +239,8 @@ __device__ __forceinline__ void nhc_half_step_f32(double& p, double (&eta)[M], d
     q[M - 1] = fmaf(cg, G, q[M - 1]);
 #pragma unroll
     for (int k = 0; k < M; ++k) {
-        pe[k] = (double)q[k];
-        eta[k] = (double)e[k];
+        pe[k] = f2d_exact(q[k]);
+        eta[k] = f2d_exact(e[k]);
     }
 }
 
@@ -196,8 +248,9 @@ template <bool PRE, int M>
 __device__ __forceinline__ void md_body(const BeadView& b, const MDParams& mp)
 {
     const size_t stride = (size_t)b.P * b.d * b.ld;
+    const bool narrow = (stride >> 32) == 0;  // 32-bit remainder suffices
     for (size_t o = (size_t)blockIdx.x * MD_T + threadIdx.x; o < stride; o += (size_t)gridDim.x * MD_T) {
-        const int l = (int)(o % b.ld);
+        const int l = narrow ? (int)((unsigned)o % (unsigned)b.ld) : (int)(o % b.ld);
         if (l >= b.N) continue;
         double p = b.p[o];
         double eta[M], pe[M];
@@ -432,6 +485,60 @@ cudaError_t launch_md_energy(const BeadView& b, const MDParams& mp, double* part
 cudaError_t launch_scalars(const ScalarSources& s, cudaStream_t st)
 {
     scalars_kernel<<<1, 32, 0, st>>>(s);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Seeded initial state (Sec. IV: beads drawn from a standard normal per
+// coordinate, momenta from the Maxwell-Boltzmann distribution at kT = 1/beta).
+// splitmix64 (Steele, Lea & Flood, OOPSLA 2014) as a counter-based generator:
+// output i of stream s mixes s + (i + 1) * 0x9E3779B97F4A7C15.  Coordinate
+// (q, j, c, l) of quantity q (0: beads, 1: momenta) has counter
+// k = ((q P + j) d + c) N + l and takes uniforms 2k and 2k + 1 in (0, 1]
+// (top 53 bits, plus one unit); z = sqrt(-2 ln u1) cos(2 pi u2).
+
+__host__ __device__ __forceinline__ unsigned long long sm64_mix(unsigned long long z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+unsigned long long splitmix64_at(unsigned long long seed, unsigned long long i)
+{
+    return sm64_mix(seed + (i + 1) * 0x9E3779B97F4A7C15ull);
+}
+
+__device__ __forceinline__ double sm64_uniform(unsigned long long seed, unsigned long long i)
+{
+    const unsigned long long x = sm64_mix(seed + (i + 1) * 0x9E3779B97F4A7C15ull);
+    return (double)((x >> 11) + 1ull) * 0x1.0p-53;
+}
+
+__global__ void __launch_bounds__(256) init_state_kernel(BeadView b, double p_scale, unsigned long long seed)
+{
+    const size_t n = (size_t)b.P * b.d * b.ld;
+    for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < 2 * n; o += (size_t)gridDim.x * blockDim.x) {
+        const int q = o >= n ? 1 : 0;
+        const size_t oq = o - q * n;
+        const size_t row = oq / b.ld;  // j d + c
+        const int l = (int)(oq - row * b.ld);
+        double z = 0.0;
+        if (l < b.N) {
+            const unsigned long long k = ((unsigned long long)q * b.P * b.d + row) * b.N + l;
+            const double u1 = sm64_uniform(seed, 2 * k), u2 = sm64_uniform(seed, 2 * k + 1);
+            z = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+        }
+        if (q == 0) b.r[oq] = z;
+        else b.p[oq] = p_scale * z;
+    }
+}
+
+cudaError_t launch_init_state(const BeadView& b, double p_scale, unsigned long long seed, cudaStream_t st)
+{
+    const size_t n = 2 * (size_t)b.P * b.d * b.ld;
+    const int grid = (int)std::min<size_t>((n + 255) / 256, 152 * 8);
+    init_state_kernel<<<grid, 256, 0, st>>>(b, p_scale, seed);
     return cudaGetLastError();
 }
 

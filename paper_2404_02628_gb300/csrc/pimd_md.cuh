@@ -92,4 +92,10 @@ cudaError_t launch_md_post(const BeadView& b, const MDParams& mp, cudaStream_t s
 cudaError_t launch_md_energy(const BeadView& b, const MDParams& mp, double* part, cudaStream_t st);
 cudaError_t launch_scalars(const ScalarSources& s, cudaStream_t st);
 cudaError_t launch_zero(double* x, size_t n, cudaStream_t st);
+// Seeded initial state: beads ~ N(0, 1) per coordinate, momenta ~ N(0, p_scale^2)
+// (p_scale = sqrt(m kT)), padding columns zero.  Counter-based splitmix64
+// stream `seed`, two uniforms per coordinate, Box-Muller (cosine branch).
+cudaError_t launch_init_state(const BeadView& b, double p_scale, unsigned long long seed, cudaStream_t st);
+// Output i of the splitmix64 stream `seed` (host copy, for per-replica seeds).
+unsigned long long splitmix64_at(unsigned long long seed, unsigned long long i);
 cudaError_t launch_nonfinite_scan(const double* x, int N, int P, int d, int ld, int* flag, cudaStream_t st);

@@ -500,7 +500,8 @@ __global__ void __launch_bounds__(256) xdf_table_kernel(XView v, long long ntile
 // ------------------------------------------------------------------------
 // block operators: G_J = (I - M_JJ)^{-1}, Q_J = G_J M_{J,J-1}, P_J = M_{J+1,J} G_J
 
-__device__ __forceinline__ void blockops_body(const XView& v)
+// part 0: G_J and Q_J; part 1: P_J (G_J recomputed); part -1: all three.
+__device__ __forceinline__ void blockops_body(const XView& v, int part)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     DfwTile* L = reinterpret_cast<DfwTile*>(smem_raw);
@@ -513,11 +514,11 @@ __device__ __forceinline__ void blockops_body(const XView& v)
     {
         const long long t = xdf_tile_index(v, J, J);
         tile_copy(L, v.M + t, threadIdx.x, blockDim.x);
-        if (J >= 1) {
+        if (J >= 1 && part != 1) {
             const long long ts = xdf_tile_index(v, J, J - 1);
             tile_copy(Ms, v.M + ts, threadIdx.x, blockDim.x);
         }
-        if (J + 1 < v.nb) {
+        if (J + 1 < v.nb && part != 0) {
             const long long tp = xdf_tile_index(v, J + 1, J);
             tile_copy(Mp, v.M + tp, threadIdx.x, blockDim.x);
         }
@@ -542,23 +543,34 @@ __device__ __forceinline__ void blockops_body(const XView& v)
     block_sync();
     for (int q = threadIdx.x; q < 1024; q += blockDim.x) {
         const int r = q >> 5, c = q & 31, o = RIDX(r, c);
-        v.G[J].h[o] = G->h[o];
-        v.G[J].l[o] = G->l[o];
-        v.G[J].e[o] = G->e[o];
-        dfw Q = dfw_zero(), Pm = dfw_zero();
-        if (J >= 1) Q = dot_mat(G, Ms, r, c, 0, r + 1);
-        if (J + 1 < v.nb) Pm = dot_mat(Mp, G, r, c, c, 32);
-        v.Q[J].h[o] = Q.h;
-        v.Q[J].l[o] = Q.l;
-        v.Q[J].e[o] = Q.e;
-        v.P[J].h[o] = Pm.h;
-        v.P[J].l[o] = Pm.l;
-        v.P[J].e[o] = Pm.e;
+        if (part != 1) {
+            v.G[J].h[o] = G->h[o];
+            v.G[J].l[o] = G->l[o];
+            v.G[J].e[o] = G->e[o];
+            dfw Q = dfw_zero();
+            if (J >= 1) Q = dot_mat(G, Ms, r, c, 0, r + 1);
+            v.Q[J].h[o] = Q.h;
+            v.Q[J].l[o] = Q.l;
+            v.Q[J].e[o] = Q.e;
+        }
+        if (part != 0) {
+            dfw Pm = dfw_zero();
+            if (J + 1 < v.nb) Pm = dot_mat(Mp, G, r, c, c, 32);
+            v.P[J].h[o] = Pm.h;
+            v.P[J].l[o] = Pm.l;
+            v.P[J].e[o] = Pm.e;
+        }
     }
 }
 
 constexpr int XDF_BLOCKOPS_T = 1024;  // one warp per column of G
-__global__ void __launch_bounds__(XDF_BLOCKOPS_T) xdf_blockops_kernel(XView v) { blockops_body(v); }
+// With gridDim.y = 2, two blocks per diagonal block J (blockIdx.y = part):
+// the G recurrence is short next to the two 32 x 32 products, so each block
+// redoes it.
+__global__ void __launch_bounds__(XDF_BLOCKOPS_T) xdf_blockops_kernel(XView v)
+{
+    blockops_body(v, gridDim.y == 2 ? (int)blockIdx.y : -1);
+}
 
 // ------------------------------------------------------------------------
 // recursion: chain blocks and helpers
@@ -1268,6 +1280,23 @@ __global__ void __launch_bounds__(256) xdf_band_kernel(XView v) { band_body(v); 
 
 __device__ __forceinline__ dfw xget(const float* h, const float* l, const int* e, int i) { return dfw{h[i], l[i], e[i]}; }
 
+// Sum of the ns helper partials and the band partial of row (dir 0) or
+// column (dir 1) `lane` of block `blk`: all loads issued first, then a tree
+// of additions.
+__device__ __forceinline__ DVAcc sum_partials(const XView& v, int dir, int blk, int lane, int ns)
+{
+    DVAcc q[XDF_MAXS + 1];
+#pragma unroll
+    for (int t = 0; t < XDF_MAXS; ++t)
+        q[t] = (t < ns) ? load_dv(v.parth, v.partl, v.parte, xpart_index(v, dir, blk, t, lane)) : dv_zero();
+    q[XDF_MAXS] = load_dv(v.bandh, v.bandl, v.bande, xband_index(v, dir, blk, lane));
+#pragma unroll
+    for (int h = 1; h <= XDF_MAXS; h <<= 1)
+#pragma unroll
+        for (int t = 0; t + h <= XDF_MAXS; t += 2 * h) dv_add(q[t], q[t + h]);
+    return q[0];
+}
+
 __device__ __forceinline__ double dv_comp(const DVAcc& a, int c, dfw scale)
 {
     // a.v[c] * 2^a.e * scale
@@ -1276,7 +1305,9 @@ __device__ __forceinline__ double dv_comp(const DVAcc& a, int c, dfw scale)
     return df_to_double(a.v[c]) * dfw_to_double(s);
 }
 
-// Endpoint forces (Sec. III exterior-bead formulas, factorised form).
+// Endpoint forces (Sec. III exterior-bead formulas, factorised form).  D is
+// the dimension (the coordinate loops unroll, nothing goes to local memory).
+template <int D>
 __device__ __forceinline__ void finalize_body(const XView& v, const FinalizeOut& o)
 {
     __shared__ double red[32];
@@ -1291,63 +1322,67 @@ __device__ __forceinline__ void finalize_body(const XView& v, const FinalizeOut&
         }
     }
     if (l < v.N) {
-        double a[3] = {0.0, 0.0, 0.0}, b[3] = {0.0, 0.0, 0.0};
-        for (int c = 0; c < v.d; ++c) {
-            a[c] = v.a[(size_t)c * v.lda + l];
-            b[c] = v.b[(size_t)c * v.ldb + l];
+        const int n = l + 1;  // row of bead P of particle l
+        const int Jn = n >> 5, rn = n & 31;
+        const int Jk = l >> 5, rk = l & 31;
+        DVAcc R = dv_zero(), C = dv_zero();
+        if (!v.xi_zero) {
+            // every partial of the row (then of the column) is loaded before
+            // any is added, so the loads overlap
+            R = sum_partials(v, 0, Jn, rn, min(v.S, Jn - v.W + 1));
+            C = sum_partials(v, 1, Jk, rk, min(v.S, v.nb - Jk - v.W));
         }
-        double rowtot, coltot, PB[3] = {0.0, 0.0, 0.0}, PA[3] = {0.0, 0.0, 0.0}, link, linkin;
-        if (v.xi_zero) {
-            rowtot = coltot = 1.0;
-            for (int c = 0; c < 3; ++c) {
-                PB[c] = b[c];
-                PA[c] = a[c];
+        {
+            double a[D], b[D];
+            for (int c = 0; c < D; ++c) {
+                a[c] = v.a[(size_t)c * v.lda + l];
+                b[c] = v.b[(size_t)c * v.ldb + l];
             }
-            link = linkin = 0.0;
-        } else {
-            const int n = l + 1;  // row of bead P of particle l
-            const int Jn = n >> 5, rn = n & 31;
-            const int Jk = l >> 5, rk = l & 31;
-            DVAcc R = dv_zero(), C = dv_zero();
-            for (int s = 0; s < min(v.S, Jn - v.W + 1); ++s) dv_add(R, load_dv(v.parth, v.partl, v.parte, xpart_index(v, 0, Jn, s, rn)));
-            dv_add(R, load_dv(v.bandh, v.bandl, v.bande, xband_index(v, 0, Jn, rn)));
-            for (int s = 0; s < min(v.S, v.nb - Jk - v.W); ++s) dv_add(C, load_dv(v.parth, v.partl, v.parte, xpart_index(v, 1, Jk, s, rk)));
-            dv_add(C, load_dv(v.bandh, v.bandl, v.bande, xband_index(v, 1, Jk, rk)));
-            const dfw Z = xget(v.yh, v.yl, v.ye, v.N);
-            const double zm = df_to_double(df{Z.h, Z.l});
-            const dfw iZ = dfw_norm(df_from_double(1.0 / zm), -Z.e);
-            const dfw yn = xget(v.yh, v.yl, v.ye, n), cn = xget(v.ch, v.cl, v.ce, n);
-            const dfw yl = xget(v.yh, v.yl, v.ye, l), cl = xget(v.ch, v.cl, v.ce, l);
-            rowtot = dfw_to_double(dfw_mul(dfw_mul(yn, cn), iZ));
-            coltot = dfw_to_double(dfw_mul(dfw_mul(yl, cl), iZ));
-            const dfw fr = dfw_mul(cn, iZ), fc = dfw_mul(yl, iZ);
-            for (int c = 0; c < v.d; ++c) {
-                PB[c] = dv_comp(R, c, fr);
-                PA[c] = dv_comp(C, c, fc);
+            double rowtot, coltot, PB[D], PA[D], link, linkin;
+            if (v.xi_zero) {
+                rowtot = coltot = 1.0;
+                for (int c = 0; c < D; ++c) {
+                    PB[c] = b[c];
+                    PA[c] = a[c];
+                }
+                link = linkin = 0.0;
+            } else {
+                const dfw Z = xget(v.yh, v.yl, v.ye, v.N);
+                const double zm = df_to_double(df{Z.h, Z.l});
+                const dfw iZ = dfw_norm(df_from_double(1.0 / zm), -Z.e);
+                const dfw yn = xget(v.yh, v.yl, v.ye, n), cn = xget(v.ch, v.cl, v.ce, n);
+                const dfw yl = xget(v.yh, v.yl, v.ye, l), cl = xget(v.ch, v.cl, v.ce, l);
+                rowtot = dfw_to_double(dfw_mul(dfw_mul(yn, cn), iZ));
+                coltot = dfw_to_double(dfw_mul(dfw_mul(yl, cl), iZ));
+                const dfw fr = dfw_mul(cn, iZ), fc = dfw_mul(yl, iZ);
+                for (int c = 0; c < D; ++c) {
+                    PB[c] = dv_comp(R, c, fr);
+                    PA[c] = dv_comp(C, c, fc);
+                }
+                link = (l < v.N - 1) ? 1.0 - rowtot : 0.0;
+                linkin = (l >= 1) ? 1.0 - coltot : 0.0;
             }
-            link = (l < v.N - 1) ? 1.0 - rowtot : 0.0;
-            linkin = (l >= 1) ? 1.0 - coltot : 0.0;
-        }
-        double FP[3], F1[3], e = 0.0;
-        for (int c = 0; c < v.d; ++c) {
-            const double bn = (l < v.N - 1) ? v.b[(size_t)c * v.ldb + l + 1] : 0.0;
-            const double ap = (l >= 1) ? v.a[(size_t)c * v.lda + l - 1] : 0.0;
-            FP[c] = -v.ks * (rowtot * a[c] - PB[c] + link * (a[c] - bn));
-            F1[c] = -v.ks * (coltot * b[c] - PA[c] + linkin * (b[c] - ap));
-            e += rowtot * a[c] * a[c] - 2.0 * a[c] * PB[c] + coltot * b[c] * b[c] + link * (a[c] - bn) * (a[c] - bn);
-        }
-        esum[0] = 0.5 * v.ks * e;
-        if (o.f) {
-            for (int c = 0; c < v.d; ++c) {
-                o.f[((size_t)(o.P - 1) * v.d + c) * o.ldf + l] += FP[c];
-                o.f[((size_t)c) * o.ldf + l] += F1[c];
+            double FP[D], F1[D], e = 0.0;
+            for (int c = 0; c < D; ++c) {
+                const double bn = (l < v.N - 1) ? v.b[(size_t)c * v.ldb + l + 1] : 0.0;
+                const double ap = (l >= 1) ? v.a[(size_t)c * v.lda + l - 1] : 0.0;
+                FP[c] = -v.ks * (rowtot * a[c] - PB[c] + link * (a[c] - bn));
+                F1[c] = -v.ks * (coltot * b[c] - PA[c] + linkin * (b[c] - ap));
+                e += rowtot * a[c] * a[c] - 2.0 * a[c] * PB[c] + coltot * b[c] * b[c] + link * (a[c] - bn) * (a[c] - bn);
             }
-        }
-        if (o.g1) {
-            const double gs = *o.gscale;
-            for (int c = 0; c < v.d; ++c) {
-                o.g1[(size_t)c * o.ldg + l] = -gs * F1[c];
-                o.gP[(size_t)c * o.ldg + l] = -gs * FP[c];
+            esum[0] = 0.5 * v.ks * e;
+            if (o.f) {
+                for (int c = 0; c < D; ++c) {
+                    o.f[((size_t)(o.P - 1) * v.d + c) * o.ldf + l] += FP[c];
+                    o.f[((size_t)c) * o.ldf + l] += F1[c];
+                }
+            }
+            if (o.g1) {
+                const double gs = *o.gscale;
+                for (int c = 0; c < D; ++c) {
+                    o.g1[(size_t)c * o.ldg + l] = -gs * F1[c];
+                    o.gP[(size_t)c * o.ldg + l] = -gs * FP[c];
+                }
             }
         }
     }
@@ -1355,7 +1390,8 @@ __device__ __forceinline__ void finalize_body(const XView& v, const FinalizeOut&
     if (threadIdx.x == 0 && o.part) o.part[blockIdx.x] = esum[0];
 }
 
-__global__ void __launch_bounds__(256) xdf_finalize_kernel(XView v, FinalizeOut o) { finalize_body(v, o); }
+template <int D>
+__global__ void __launch_bounds__(256) xdf_finalize_kernel(XView v, FinalizeOut o) { finalize_body<D>(v, o); }
 
 // ------------------------------------------------------------------------
 // Self-contained recursion for small systems (batched replicas): one block per
@@ -1595,7 +1631,7 @@ __global__ void __launch_bounds__(XDF_BLOCKOPS_T) blockops_batch(const RepArgs* 
 {
     const XView& v = ra[blockIdx.z].xv;
     if (v.xi_zero) return;
-    blockops_body(v);
+    blockops_body(v, -1);
 }
 
 __global__ void __launch_bounds__(256) band_batch(const RepArgs* ra)
@@ -1608,7 +1644,9 @@ __global__ void __launch_bounds__(256) band_batch(const RepArgs* ra)
 __global__ void __launch_bounds__(256) finalize_batch(const RepArgs* ra)
 {
     const RepArgs& a = ra[blockIdx.z];
-    finalize_body(a.xv, a.fo);
+    if (a.xv.d == 1) finalize_body<1>(a.xv, a.fo);
+    else if (a.xv.d == 2) finalize_body<2>(a.xv, a.fo);
+    else finalize_body<3>(a.xv, a.fo);
 }
 
 // V_ends = V_xi - sum E_int = (sum_l g(l, l+1) - ln W_N)/beta with
@@ -1631,7 +1669,8 @@ __global__ void xdf_vb_value_kernel(XView v, int nprep, double* V_out)
 // prep and finalize do FP64 work per particle: 64-thread blocks spread it over more SMs
 constexpr int XDF_SMALL_T = 64;
 int xdf_prep_blocks(int npad) { return min(152 * 4, (npad + XDF_SMALL_T - 1) / XDF_SMALL_T); }
-int xdf_finalize_blocks(int N) { return (N + XDF_SMALL_T - 1) / XDF_SMALL_T; }
+constexpr int XDF_FIN_T = 64;  // finalize: one thread per particle
+int xdf_finalize_blocks(int N) { return (N + XDF_FIN_T - 1) / XDF_FIN_T; }
 
 size_t xdf_recursion_smem(int W)
 {
@@ -1664,7 +1703,8 @@ cudaError_t xdf_launch_forward(const XView& v, cudaStream_t st, ProfMarks* pm, c
         if (e != cudaSuccess) return e;
         attrs = true;
     }
-    xdf_blockops_kernel<<<v.nb, XDF_BLOCKOPS_T, blockops_smem(), st>>>(v);
+    // two blocks per diagonal block while 2 nb blocks fit one wave (two 1024-thread blocks per SM)
+    xdf_blockops_kernel<<<dim3(v.nb, v.nb <= 152 ? 2 : 1), XDF_BLOCKOPS_T, blockops_smem(), st>>>(v);
     prof_mark(pm, "exch_blockops", st);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -1692,7 +1732,9 @@ cudaError_t xdf_launch_adjoint(const XView& v, const FinalizeOut& o, cudaStream_
         xdf_band_kernel<<<dim3(v.nb, 2), 32 * v.W, band_smem(v.W), st>>>(v);
         prof_mark(pm, "exch_band", st);
     }
-    xdf_finalize_kernel<<<xdf_finalize_blocks(v.N), XDF_SMALL_T, 0, st>>>(v, o);
+    if (v.d == 1) xdf_finalize_kernel<1><<<xdf_finalize_blocks(v.N), XDF_FIN_T, 0, st>>>(v, o);
+    else if (v.d == 2) xdf_finalize_kernel<2><<<xdf_finalize_blocks(v.N), XDF_FIN_T, 0, st>>>(v, o);
+    else xdf_finalize_kernel<3><<<xdf_finalize_blocks(v.N), XDF_FIN_T, 0, st>>>(v, o);
     prof_mark(pm, "exch_finalize", st);
     return cudaGetLastError();
 }
@@ -1740,7 +1782,7 @@ cudaError_t batch_launch_exchange(const RepArgs* ra, const BatchGrid& g, cudaStr
     prof_mark(pm, "batch_exch_recursion", st);
     band_batch<<<dim3(g.nb_max, 2, g.R), 256, band_smem(8), st>>>(ra);
     prof_mark(pm, "batch_exch_band", st);
-    finalize_batch<<<dim3(g.gx_fin, 1, g.R), XDF_SMALL_T, 0, st>>>(ra);
+    finalize_batch<<<dim3(g.gx_fin, 1, g.R), XDF_FIN_T, 0, st>>>(ra);
     prof_mark(pm, "batch_exch_finalize", st);
     return cudaGetLastError();
 }

@@ -393,3 +393,19 @@ def test_long_run_energy_matches_exact(xi):
         m, err = blocked_error(x)
         assert err < 0.01 * Eex
         assert abs(m - Eex) < 4.0 * err, (name, m, err, Eex)
+
+
+def test_ground_state_energy_printed_in_paper():
+    """Sec. IV A prints E = N for the ideal trapped gas at beta = 6 (ground
+    state) and simulated energies within about 0.3 % of it at P = 72; the
+    oracle's exact finite-P energy must lie inside that band."""
+    import os
+    vals = {}
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", "paper_ground_state.txt")):
+        line = line.split("#", 1)[0].strip()
+        if line:
+            k, v = line.split()
+            vals[k] = float(v)
+    for N in (100, 1600):
+        E = exact.energy(N, vals["beta"], P=int(vals["P"]))
+        assert abs(E / (N * vals["energy_per_particle"]) - 1.0) < vals["agreement_rel"], (N, E)
