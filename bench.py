@@ -203,6 +203,61 @@ def kernel_work(name, w):
     return "hbm", dof * 8 / 1e9, "GB/s", hbm, hbm_src
 
 
+def mixed_force_error(pkg, S, w, device, snapshots=10, stride=20):
+    """Mixed-precision forces (FP32 springs / pairs) against FP64 forces of the
+    same configuration, on `snapshots` configurations of the running trajectory
+    (every `stride` steps): max over snapshots of |F_mixed - F_fp64|_inf / |F_fp64|_inf."""
+    import torch
+
+    R = pkg.System(w["N"], w["P"], w["d"], w["beta"], w["omega"], w["g"], w["s"], w["xi"], device=device,
+                   precision=pkg.PREC_FP64, nhc_len=w["M"], dt=w["dt"])
+    errs = []
+    for _ in range(snapshots):
+        S.step(stride)
+        torch.cuda.synchronize()
+        R.r.copy_(S.r)
+        R.forces()
+        pkg.pimd_forces(S.h, False)
+        torch.cuda.synchronize()
+        N = w["N"]
+        d = (S.f[:, :, :N] - R.f[:, :, :N]).abs().max().item()
+        errs.append(d / R.f[:, :, :N].abs().max().item())
+    R.close()
+    return {"max_rel_inf": float("%.3e" % max(errs)), "mean_rel_inf": float("%.3e" % (sum(errs) / len(errs))),
+            "snapshots": snapshots, "stride_steps": stride,
+            "what": "|F_mixed - F_fp64|_inf / |F_fp64|_inf on snapshots of the timed trajectory"}
+
+
+def memory_sweep(pkg, device, Ns=(10000, 20000, 30000, 40000), K=3):
+    """Ideal trapped bosons (g = 0), P = 32, beta = 3, xi = 1, mixed precision:
+    steps/s and workspace bytes against N, factor table stored and recomputed."""
+    import torch
+
+    from workloads import beads, momenta
+
+    out = []
+    for N in Ns:
+        r = beads(N, 32, 2, 5)
+        p = momenta(N, 32, 2, 3.0, 5)
+        for mode, name in ((pkg.TABLE_STORE, "store"), (pkg.TABLE_RECOMPUTE, "recompute")):
+            S = pkg.System(N, 32, 2, 3.0, 1.0, 0.0, 0.5, 1.0, r=r, p=p, device=device, precision=pkg.PREC_MIXED,
+                           nhc_len=4, dt=0.01, table_mode=mode)
+            S.step(2)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            S.step(K)
+            b.record()
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / K
+            out.append({"N": N, "table": name, "steps_per_s": round(1e3 / ms, 3), "ms_per_step": round(ms, 3),
+                        "workspace_GB": round(S.work_bytes / 1e9, 4)})
+            S.close()
+            del S
+            torch.cuda.empty_cache()
+    return out
+
+
 def run_batch(pkg, device, flush, stream, K, warmup):
     """Batched 64-replica workload (uneven N, beta, xi) against the plain FP64
     single-system form run replica by replica on the same GPU."""
@@ -359,6 +414,8 @@ def run_ours(args):
                                           "precision": "fp64 exchange + fp32 springs"}}
         S2.close()
         extra["batch64"] = run_batch(pkg, device, flush, stream, max(10, min(args.steps // 4, 50)), args.warmup)
+        extra["mixed_vs_fp64_forces"] = mixed_force_error(pkg, S, w, device)
+        extra["sweep_ideal_N"] = memory_sweep(pkg, device)
 
     cpu = None
     if not args.no_extra and rank == 0 and ws == 1:

@@ -175,6 +175,19 @@ pimd_status pimd_state_bytes(pimd_t ctx, size_t* bytes);
 pimd_status pimd_get_state(pimd_t ctx, void* host_blob, size_t bytes);
 pimd_status pimd_set_state(pimd_t ctx, const void* host_blob, size_t bytes);
 
+/* Radial bead density (Sec. IV B density profiles; per particle, so the
+ * ideal gas in its ground state gives exp(-r^2)/pi in d = 2).  For the
+ * current configuration, adds rho_b = n_b / (N P V_b) to hist[b] for
+ * b < nbins: n_b counts the beads (every particle, every slice) with
+ * floor(sqrt(r2) / dr) = b, where dr = r_max / nbins and r2 = x_0^2 + ... +
+ * x_{d-1}^2 rounded after every operation (so the bin of each bead is
+ * reproducible bit for bit); V_b is the volume of shell b in d dimensions
+ * (2 dr; pi (r_{b+1}^2 - r_b^2); 4/3 pi (r_{b+1}^3 - r_b^3)).  Beads at or
+ * beyond r_max are not counted.  hist: caller-owned device array of nbins
+ * doubles, zeroed by the caller; averaging over calls is the caller's.
+ * nbins in [1, 8192].  Stream-ordered, asynchronous. */
+pimd_status pimd_density_accumulate(pimd_t ctx, int nbins, double r_max, double* hist);
+
 /* Seeded initial state on the device (Sec. IV: beads drawn from N(0, 1) per
  * coordinate; momenta Maxwell-Boltzmann at kT = 1/beta, i.e. N(0, m/beta)).
  * Generator: splitmix64 (Steele, Lea & Flood, OOPSLA 2014) used counter-wise,

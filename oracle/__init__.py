@@ -241,3 +241,30 @@ def estimators(state, beta, xi, omega, A, s, Q, mass=1.0, thermostat=True):
     if rc:
         raise ValueError("oracle rejected the arguments")
     return {f: getattr(est, f) for f in ESTIMATE_FIELDS}
+
+
+def radial_density(r, nbins, r_max):
+    """Radial bead density of one configuration (Sec. IV B density profiles),
+    per particle: rho_b = n_b / (N P V_b), where n_b counts the beads with
+    floor(sqrt(r2) / dr) = b, dr = r_max / nbins, r2 = x_0^2 + ... summed in
+    component order with IEEE rounding after every operation, and V_b is the
+    d-dimensional volume of shell b.  Beads at or beyond r_max are dropped.
+    Returns (rho[nbins], counts[nbins])."""
+    r = np.asarray(r, dtype=np.float64)
+    N, P, d = r.shape
+    dr = r_max / nbins
+    r2 = np.zeros((N, P))
+    for c in range(d):
+        x = r[:, :, c]
+        r2 = r2 + x * x
+    t = np.floor(np.sqrt(r2) / dr)
+    t = t[t < nbins].astype(np.int64)
+    counts = np.bincount(t, minlength=nbins)[:nbins]
+    edges = np.arange(nbins + 1) * dr
+    if d == 1:
+        vol = 2.0 * (edges[1:] - edges[:-1])
+    elif d == 2:
+        vol = np.pi * (edges[1:] ** 2 - edges[:-1] ** 2)
+    else:
+        vol = 4.0 / 3.0 * np.pi * (edges[1:] ** 3 - edges[:-1] ** 3)
+    return counts / (N * P * vol), counts

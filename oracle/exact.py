@@ -91,3 +91,27 @@ def ring_partition(k, beta, P=None, d=2, omega=1.0):
     """z(k): partition function of one exchange ring of k particles."""
     th, _ = theta(beta, P, omega)
     return (2.0 * math.sinh(k * th)) ** (-d)
+
+
+def bead_variance(beta, P, omega=1.0, m=1.0):
+    """Variance of one Cartesian coordinate of any bead of a distinguishable
+    trapped ring polymer (xi = 0, Sec. III springs k_s = m P / beta^2, trap
+    weighted 1/P): the Gaussian weight exp(-beta x^T A x / 2) with
+    A = k_s L + (m omega^2 / P) I, L the ring Laplacian (eigenvalues
+    4 sin^2(pi k / P)), gives (1/P) sum_k 1 / (beta A_k)."""
+    ks = m * P / beta**2
+    return sum(1.0 / (beta * (ks * 4.0 * math.sin(math.pi * k / P) ** 2 + m * omega**2 / P))
+               for k in range(P)) / P
+
+
+def shell_probability(r1, r2, var, d):
+    """Probability that an isotropic Gaussian point (variance var per
+    coordinate) in d dimensions lies at radius in [r1, r2)."""
+    if d == 1:
+        return math.erf(r2 / math.sqrt(2 * var)) - math.erf(r1 / math.sqrt(2 * var))
+    if d == 2:
+        return math.exp(-r1 * r1 / (2 * var)) - math.exp(-r2 * r2 / (2 * var))
+    def cdf(x):  # chi distribution with 3 degrees of freedom
+        z = x / math.sqrt(2 * var)
+        return math.erf(z) - 2 * z * math.exp(-z * z) / math.sqrt(math.pi)
+    return cdf(r2) - cdf(r1)

@@ -26,6 +26,7 @@ __all__ = [
     "pimd_batch_step_eager", "pimd_batch_step_profiled", "pimd_batch_profile_slot_name",
     "pimd_batch_estimators", "pimd_batch_sync", "pimd_batch_last_error", "pimd_batch_destroy",
     "pimd_batch_autotune", "pimd_autotune", "pimd_tuning", "pimd_init_state", "pimd_batch_init_state",
+    "pimd_density_accumulate",
 ]
 
 PIMD_OK, PIMD_EINVAL, PIMD_ENOMEM, PIMD_ECUDA, PIMD_ETIMEOUT, PIMD_ENONFINITE, PIMD_ESTATE = range(7)
@@ -125,6 +126,7 @@ _SIGS = {
     "pimd_batch_last_error": ([_vp], ctypes.c_char_p),
     "pimd_batch_destroy": ([_vp], None),
     "pimd_autotune": ([_vp, ctypes.c_char_p], ctypes.c_int),
+    "pimd_density_accumulate": ([_vp, ctypes.c_int, ctypes.c_double, _vp], ctypes.c_int),
     "pimd_init_state": ([_vp, ctypes.c_ulonglong], ctypes.c_int),
     "pimd_batch_init_state": ([_vp, ctypes.c_ulonglong], ctypes.c_int),
     "pimd_tuning": ([_vp] + [ctypes.POINTER(ctypes.c_int)] * 4, ctypes.c_int),
@@ -387,6 +389,10 @@ def pimd_batch_autotune(h, cache_path=None):
     return _bcheck(lib().pimd_batch_autotune(h, cache_path.encode() if cache_path else None), h)
 
 
+def pimd_density_accumulate(h, nbins, r_max, hist_ptr):
+    return _check(lib().pimd_density_accumulate(h, int(nbins), float(r_max), hist_ptr), h)
+
+
 def pimd_init_state(h, seed):
     return _check(lib().pimd_init_state(h, int(seed) & 0xFFFFFFFFFFFFFFFF), h)
 
@@ -565,6 +571,15 @@ class System:
 
     def step(self, n=1, graph=True):
         (pimd_step if graph else pimd_step_eager)(self.h, n)
+
+    def density(self, nbins, r_max, hist=None):
+        """Adds the radial bead density of the current configuration into
+        ``hist`` (a float64 CUDA tensor of nbins, created zeroed if None) and
+        returns it (pimd_density_accumulate)."""
+        if hist is None:
+            hist = self.torch.zeros(nbins, dtype=self.torch.float64, device=self.r.device)
+        pimd_density_accumulate(self.h, nbins, r_max, hist.data_ptr())
+        return hist
 
     def init_state(self, seed):
         """Seeded beads and momenta on the device (pimd_init_state)."""

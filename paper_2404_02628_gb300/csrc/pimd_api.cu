@@ -1048,6 +1048,17 @@ extern "C" pimd_status pimd_set_state(pimd_t c, const void* host, size_t bytes)
     return PIMD_OK;
 }
 
+extern "C" pimd_status pimd_density_accumulate(pimd_t c, int nbins, double r_max, double* hist)
+{
+    if (!c || !hist) return fail(c, PIMD_EINVAL, "pimd_density_accumulate: NULL argument");
+    if (!c->bound) return fail(c, PIMD_ESTATE, "pimd_density_accumulate: not bound");
+    if (nbins < 1 || nbins > DENSITY_MAX_BINS || !(r_max > 0.0) || !std::isfinite(r_max))
+        return fail(c, PIMD_EINVAL, "pimd_density_accumulate: nbins in [1, 8192] and finite r_max > 0 required");
+    cudaError_t e = launch_density(c->bv, nbins, r_max / nbins, hist, c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pimd_density_accumulate");
+    return PIMD_OK;
+}
+
 extern "C" pimd_status pimd_init_state(pimd_t c, unsigned long long seed)
 {
     if (!c) return fail(c, PIMD_EINVAL, "pimd_init_state: NULL handle");

@@ -542,6 +542,58 @@ cudaError_t launch_init_state(const BeadView& b, double p_scale, unsigned long l
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Radial density of all beads (Sec. IV B density profiles, per particle):
+// rho_b = n_b / (N P V_b).  Counts per block in shared memory, then one
+// weighted atomic add per occupied bin.
+
+__device__ __forceinline__ double shell_volume(int d, double r1, double r2)
+{
+    const double PI = 3.141592653589793;
+    if (d == 1) return 2.0 * (r2 - r1);
+    if (d == 2) return PI * (r2 * r2 - r1 * r1);
+    return 4.0 / 3.0 * PI * (r2 * r2 * r2 - r1 * r1 * r1);
+}
+
+__global__ void __launch_bounds__(256) density_kernel(BeadView b, int nbins, double dr, double* hist)
+{
+    extern __shared__ unsigned int cnt[];
+    for (int k = threadIdx.x; k < nbins; k += blockDim.x) cnt[k] = 0u;
+    __syncthreads();
+    const long long n = (long long)b.P * b.N;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(q / b.N), l = (int)(q - (long long)j * b.N);
+        double r2 = 0.0;
+        for (int c = 0; c < b.d; ++c) {
+            const double x = b.r[((size_t)j * b.d + c) * b.ld + l];
+            r2 = __dadd_rn(r2, __dmul_rn(x, x));
+        }
+        const double t = floor(__ddiv_rn(__dsqrt_rn(r2), dr));
+        if (t < (double)nbins) atomicAdd(&cnt[(int)t], 1u);
+    }
+    __syncthreads();
+    const double inv = 1.0 / ((double)b.N * b.P);
+    for (int k = threadIdx.x; k < nbins; k += blockDim.x)
+        if (cnt[k]) atomicAdd(&hist[k], (double)cnt[k] * inv / shell_volume(b.d, k * dr, (k + 1) * dr));
+}
+
+cudaError_t launch_density(const BeadView& b, int nbins, double dr, double* hist, cudaStream_t st)
+{
+    if (nbins < 1 || nbins > DENSITY_MAX_BINS || !(dr > 0.0)) return cudaErrorInvalidValue;
+    const long long n = (long long)b.P * b.N;
+    const int grid = (int)std::min<long long>((n + 255) / 256, 152 * 4);
+    const size_t smem = (size_t)nbins * sizeof(unsigned int);
+    static bool attr = false;
+    if (!attr) {
+        const cudaError_t e = cudaFuncSetAttribute(density_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)(DENSITY_MAX_BINS * sizeof(unsigned int)));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    density_kernel<<<grid, 256, smem, st>>>(b, nbins, dr, hist);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_zero(double* x, size_t n, cudaStream_t st)
 {
     zero_kernel<<<152, 256, 0, st>>>(x, n);

@@ -96,6 +96,12 @@ cudaError_t launch_zero(double* x, size_t n, cudaStream_t st);
 // (p_scale = sqrt(m kT)), padding columns zero.  Counter-based splitmix64
 // stream `seed`, two uniforms per coordinate, Box-Muller (cosine branch).
 cudaError_t launch_init_state(const BeadView& b, double p_scale, unsigned long long seed, cudaStream_t st);
+// Radial bead density of the current configuration added into hist[nbins]:
+// bin b = floor(sqrt(r2) / dr) with r2 = x0*x0 + x1*x1 + x2*x2 rounded after
+// every operation (no contraction), weight 1 / (N P V_b), V_b the d-dimensional
+// shell volume.  nbins <= DENSITY_MAX_BINS.
+constexpr int DENSITY_MAX_BINS = 8192;
+cudaError_t launch_density(const BeadView& b, int nbins, double dr, double* hist, cudaStream_t st);
 // Output i of the splitmix64 stream `seed` (host copy, for per-replica seeds).
 unsigned long long splitmix64_at(unsigned long long seed, unsigned long long i);
 cudaError_t launch_nonfinite_scan(const double* x, int N, int P, int d, int ld, int* flag, cudaStream_t st);

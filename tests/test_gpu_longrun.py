@@ -9,6 +9,9 @@ xi = 0, so the two settings differ by 28 % and a wrong exchange weight, a wrong
 temperature or a broken thermostat shows far outside the error bars.  Averages
 use blocks of the sampled series; the check is |mean - exact| < 4 standard
 errors of the block means, with the standard error itself below 3 % of E (200k steps).
+For xi = 0 the radial bead density averaged over the run is also checked, bin
+by bin (5 standard errors), against the exact Gaussian density of a bead of a
+distinguishable trapped ring polymer.
 """
 import numpy as np
 import pytest
@@ -30,11 +33,28 @@ def test_long_run_energy_matches_exact(xi):
     n_samples, stride = 20000, 10
     Ep = np.empty(n_samples)
     Ev = np.empty(n_samples)
+    nbins, r_max, nblk = 24, 4.0, 20
+    hist = [S.torch.zeros(nbins, dtype=S.torch.float64, device="cuda") for _ in range(nblk)]
     for i in range(n_samples):
         S.step(stride)
+        S.density(nbins, r_max, hist[i * nblk // n_samples])
         est = S.estimators()
         Ep[i], Ev[i] = est["E_prim"], est["E_vir"]
     S.close()
+    if xi == 0.0:
+        # distinguishable particles: every bead is an isotropic Gaussian of
+        # variance exact.bead_variance per coordinate, so the averaged
+        # density must match the exact shell probabilities per volume
+        var = exact.bead_variance(beta, P)
+        rho = np.stack([h.cpu().numpy() for h in hist]) / (n_samples // nblk)
+        dr = r_max / nbins
+        for b in range(nbins):
+            V = np.pi * (((b + 1) * dr) ** 2 - (b * dr) ** 2)
+            ref = exact.shell_probability(b * dr, (b + 1) * dr, var, d) / V
+            if ref * V < 1e-3:
+                continue
+            mean, se = rho[:, b].mean(), rho[:, b].std(ddof=1) / np.sqrt(nblk)
+            assert abs(mean - ref) < 5 * se + 1e-3 * ref, (b, mean, ref, se)
     E_exact = exact.energy(N, beta, P=P, d=d, xi=xi)
     for series in (Ev, Ep):
         blocks = series.reshape(20, -1).mean(axis=1)

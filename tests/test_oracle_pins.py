@@ -409,3 +409,45 @@ def test_ground_state_energy_printed_in_paper():
     for N in (100, 1600):
         E = exact.energy(N, vals["beta"], P=int(vals["P"]))
         assert abs(E / (N * vals["energy_per_particle"]) - 1.0) < vals["agreement_rel"], (N, E)
+
+
+# --------------------------------------------------------------------------
+# radial density (Sec. IV B density profiles)
+
+def test_bead_variance_limits_and_matrix_inverse():
+    """Spectral sum of the distinguishable ring polymer against (i) the
+    inverse of its Gaussian weight matrix, (ii) the classical limit P = 1,
+    (iii) the quantum oscillator coth(beta omega / 2) / (2 m omega) as P grows,
+    and (iv) the ground state (variance 1/2: density exp(-r^2)/pi in d = 2)."""
+    beta, om, m, P = 1.7, 1.3, 0.8, 7
+    ks = m * P / beta**2
+    A = np.zeros((P, P))
+    for j in range(P):
+        A[j, j] += 2 * ks + m * om**2 / P
+        A[j, (j + 1) % P] -= ks
+        A[j, (j - 1) % P] -= ks
+    cov = np.linalg.inv(beta * A)
+    assert abs(exact.bead_variance(beta, P, om, m) - cov[3, 3]) < 1e-13 * cov[3, 3]
+    assert abs(exact.bead_variance(beta, 1, om, m) - 1.0 / (beta * m * om**2)) < 1e-14
+    q = 1.0 / (2 * m * om * math.tanh(beta * om / 2))
+    assert abs(exact.bead_variance(beta, 4000, om, m) - q) < 1e-6 * q
+    assert abs(exact.bead_variance(40.0, 4000) - 0.5) < 1e-3
+
+
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_radial_density_of_gaussian_samples(d):
+    """The oracle's binned density of isotropic Gaussian points matches the
+    exact shell probabilities within binomial error bars, and sums to the
+    fraction inside r_max."""
+    rng = np.random.default_rng(40 + d)
+    var, n, nbins, r_max = 0.7, 400000, 40, 4.0
+    r = rng.normal(0.0, math.sqrt(var), size=(n, 1, d))
+    rho, counts = oracle.radial_density(r, nbins, r_max)
+    dr = r_max / nbins
+    for b in range(nbins):
+        p = exact.shell_probability(b * dr, (b + 1) * dr, var, d)
+        se = math.sqrt(max(p * (1 - p), 1e-12) / n)
+        assert abs(counts[b] / n - p) < 5 * se + 1e-12, (b, counts[b] / n, p)
+    edges = np.arange(nbins + 1) * dr
+    vol = {1: 2 * np.diff(edges), 2: np.pi * np.diff(edges**2), 3: 4 / 3 * np.pi * np.diff(edges**3)}[d]
+    assert abs(float(np.sum(rho * vol)) - counts.sum() / n) < 1e-12
