@@ -156,12 +156,12 @@ __device__ __forceinline__ void pair_unit_f32(const BeadView& b, const ForcePara
     const int i = bx * PT + threadIdx.x, j = by;
     const double* rs = b.r + (size_t)j * D * b.ld;
     const float sc = fp.sc32;
-    double xd[D];
+    float xf[D];
     float2 xi[D], g[D];
 #pragma unroll
     for (int c = 0; c < D; ++c) {
-        xd[c] = (i < b.N) ? rs[(size_t)c * b.ld + i] : 0.0;
-        const float xs = (float)xd[c] * sc;
+        xf[c] = (i < b.N) ? d2f_trunc(rs[(size_t)c * b.ld + i]) : 0.f;
+        const float xs = xf[c] * sc;
         xi[c] = make_float2(xs, xs);
         g[c] = make_float2(0.f, 0.f);
     }
@@ -190,23 +190,26 @@ __device__ __forceinline__ void pair_unit_f32(const BeadView& b, const ForcePara
             __syncthreads();
         }
     }
+    // per-particle epilogue in FP32 (mixed precision: the pair and trap
+    // forces are FP32 quantities); the force is added to the FP64 array and
+    // the block's energy and virial are summed in FP64
     double v[2] = {0.0, 0.0};
     if (i < b.N) {
-        const double cpair = fp.cpair32;
-        double t2 = 0.0, vir = 0.0;
+        const float cpair = (float)fp.cpair32, om2 = (float)fp.omega2, mip = -(float)fp.inv_P;
+        float t2 = 0.f, vir = 0.f;
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-            const double grad = fp.omega2 * xd[c] + cpair * ((double)g[c].x + (double)g[c].y);
+            const float grad = fmaf(om2, xf[c], cpair * (g[c].x + g[c].y));
             const size_t o = ((size_t)j * D + c) * b.ld + i;
-            const double fo = -grad * fp.inv_P;
+            const double fo = f2d_exact(grad * mip);
             f[o] = fp.accumulate ? f[o] + fo : fo;
-            t2 = fma(xd[c], xd[c], t2);
-            vir = fma(xd[c], grad, vir);
+            t2 = fmaf(xf[c], xf[c], t2);
+            vir = fmaf(xf[c], grad, vir);
         }
         // the k == i term contributed exp(0) = 1 and no force
-        const double es = fp.A != 0.0 ? (double)esum.x + (double)esum.y - 1.0 : 0.0;
-        v[0] = 0.5 * fp.omega2 * t2 + 0.5 * fp.A * es;
-        v[1] = vir;
+        const float es = fp.A != 0.0 ? (esum.x - 1.0f) + esum.y : 0.f;
+        v[0] = f2d_exact(fmaf(0.5f * om2, t2, 0.5f * (float)fp.A * es));
+        v[1] = f2d_exact(vir);
     }
     block_reduce<2>(v, red);
     if (threadIdx.x == 0) {
