@@ -169,3 +169,26 @@ def test_autotune_requires_bound_handle(pkg):
         assert ei.value.status == pkg.PIMD_ESTATE
     finally:
         pkg.pimd_batch_destroy(b)
+
+
+def test_init_state_and_density_require_bound_handle(pkg):
+    """Host-side checks of the seeded initial state and the density estimator
+    (no device work: the handle is never bound)."""
+    h = pkg.pimd_create(100, 4, 2, 1.0, 1.0, 0.0, 0.5, 1.0)
+    try:
+        for call in (lambda: pkg.pimd_init_state(h, 1), lambda: pkg.pimd_density_accumulate(h, 16, 3.0, 1 << 20)):
+            with pytest.raises(pkg.PimdError) as ei:
+                call()
+            assert ei.value.status == pkg.PIMD_ESTATE
+        with pytest.raises(pkg.PimdError) as ei:
+            pkg.pimd_density_accumulate(h, 16, 3.0, 0)  # NULL histogram
+        assert ei.value.status == pkg.PIMD_EINVAL
+    finally:
+        pkg.pimd_destroy(h)
+    b = pkg.pimd_batch_create([10, 20], 4, 2, [1.0, 1.0], [1.0, 1.0], 1.0, 0.0, 0.5)
+    try:
+        with pytest.raises(pkg.PimdError) as ei:
+            pkg.pimd_batch_init_state(b, 7)
+        assert ei.value.status == pkg.PIMD_ESTATE
+    finally:
+        pkg.pimd_batch_destroy(b)
