@@ -395,7 +395,7 @@ def run_ours(args):
     nb = pkg.pimd_state_bytes(S.h)
     host = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
     pkg.pimd_get_state(S.h, host.data_ptr(), nb)
-    est_bytes = 80
+    est_bytes = 4 + 4 + 10 * 8  # pimd_estimators reads the error word, the non-finite flag and 10 FP64 scalar slots
     K2 = min(args.steps, 100)
     torch.cuda.synchronize()
     barrier(device)

@@ -138,7 +138,9 @@ pimd_status pimd_workspace_bytes(pimd_t ctx, int n_pad, size_t* bytes);
  * NULL for the legacy default stream).  Zeroes the thermostat arrays and the
  * step counter; r and p must already hold the initial state.  Computes the
  * forces of r (asynchronously).  Captures the per-step CUDA graph on first
- * pimd_step, so bind before any capture of the caller's own. */
+ * pimd_step, so bind before any capture of the caller's own.  The context
+ * allocates one small pinned host buffer here (the estimators' read-back),
+ * released by pimd_destroy; all device memory stays the caller's. */
 pimd_status pimd_bind(pimd_t ctx, const pimd_buffers* bufs, void* stream);
 
 /* Recomputes F = -grad(V_xi + U/P) for the bound r.  If V_total_out (host)

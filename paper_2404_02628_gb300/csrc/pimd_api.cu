@@ -227,6 +227,10 @@ struct pimd_ctx {
     int n_help;
     int pair_t = 128;  // pair-kernel block size (pimd_autotune)
     int n_force = 0;   // force-worker blocks folded into the recursion launch (0: separate kernels)
+    struct HostReport {  // pinned: device error word, non-finite flag and scalar slots, read in one round trip
+        int err, flag;
+        double sc[SC_COUNT];
+    }* host_rep = nullptr;
     int fused_gx = 0;  // particle blocks per slice of the last folded force evaluation (0: not folded)
     ExchView xv;
     XView xd;
@@ -528,6 +532,12 @@ extern "C" pimd_status pimd_bind(pimd_t c, const pimd_buffers* b, void* stream)
     }
     c->buf = *b;
     c->st = (cudaStream_t)stream;
+    if (!c->host_rep) {
+        void* hp = nullptr;
+        cudaError_t e2 = cudaMallocHost(&hp, sizeof(pimd_ctx::HostReport));
+        if (e2 != cudaSuccess) return cuda_fail(c, e2, "pimd_bind: pinned report buffer");
+        c->host_rep = (pimd_ctx::HostReport*)hp;
+    }
     c->n_help = default_helpers(c->cfg);
     c->n_force = 0;
     if (c->use_df && c->A != 0.0 && c->xi != 0.0) {
@@ -965,13 +975,25 @@ extern "C" pimd_status pimd_estimators(pimd_t c, pimd_estimates* out)
     if (e != cudaSuccess) return cuda_fail(c, e, "pimd_estimators: flag reset");
     e = launch_nonfinite_scan(c->buf.f, c->N, c->P, c->d, c->buf.n_pad, (int*)(base + c->off_flag), c->st);
     if (e != cudaSuccess) return cuda_fail(c, e, "pimd_estimators: scan");
-    s = check_device_error(c);
-    if (s != PIMD_OK) return s;
-    double t[SC_COUNT];
-    int flag = 0;
-    e = cudaMemcpy(t, base + c->off_sc, sizeof t, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemcpy(&flag, base + c->off_flag, sizeof(int), cudaMemcpyDeviceToHost);
+    // error word, flag and scalars in one round trip through the pinned buffer
+    pimd_ctx::HostReport* hr = c->host_rep;
+    int* errp = c->use_df ? c->xd.err : c->xv.err;
+    e = cudaMemcpyAsync(&hr->err, errp, sizeof(int), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hr->flag, base + c->off_flag, sizeof(int), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hr->sc, base + c->off_sc, sizeof hr->sc, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
     if (e != cudaSuccess) return cuda_fail(c, e, "pimd_estimators: read");
+    if (hr->err != 0) {
+        const int code = hr->err;
+        cudaMemsetAsync(errp, 0, sizeof(int), c->st);
+        cudaStreamSynchronize(c->st);
+        char msg[160];
+        snprintf(msg, sizeof msg, "device wait gave up (code 0x%08x); increase spin_limit or check co-residency", code);
+        return fail(c, PIMD_ETIMEOUT, msg);
+    }
+    double t[SC_COUNT];
+    memcpy(t, hr->sc, sizeof t);
+    const int flag = hr->flag;
     if (!fill_estimates(t, c->P, c->N, c->d, c->beta, c->cfg.thermostat, c->steps, out))
         return fail(c, PIMD_ENONFINITE, "pimd_estimators: non-finite estimate");
     if (flag) return fail(c, PIMD_ENONFINITE, "pimd_estimators: non-finite force");
@@ -1089,6 +1111,7 @@ extern "C" void pimd_destroy(pimd_t c)
     if (!c) return;
     if (c->graph) cudaGraphExecDestroy(c->graph);
     if (c->cap) cudaStreamDestroy(c->cap);
+    if (c->host_rep) cudaFreeHost(c->host_rep);
     delete c;
 }
 
