@@ -868,27 +868,51 @@ __device__ void xchain(const XView& v, DfwTile* Tall, ChainS* cs)
         // ---- helper-partial fetcher: the partials of the block of iteration
         // it are consumed in phase 1 of iteration it; its ring slot is cleared
         // in phase 2 of iteration it-W.
+        // One global round trip per block in steady state: the flags of the
+        // next block are polled (once, acquire) while this block's partials
+        // are in flight, so a set flag needs no second round trip.
+        int seen = 0;  // this lane's stream flag of the current block already observed set
         for (int it = 1; it < nb; ++it) {
             const int B = chain_block<DIR>(v, it), ns = chain_nparts<DIR>(v, B);
             if (ns > 0) {
-                if (!smem_wait_ge(&cs->done, it - W, cs, lim, v.err, 0x570000 + it)) break;
                 int ok = 1;
-                if (lane < ns) ok = wait_flag(&flag_part[B * v.S + lane], 1, v.err, lim, 0x510000 + (DIR << 16) + B);
+                if (lane < ns && !seen) ok = wait_flag(&flag_part[B * v.S + lane], 1, v.err, lim, 0x510000 + (DIR << 16) + B);
                 if (!__all_sync(0xffffffffu, ok)) {
                     if (lane == 0) vstore(&cs->abort, 1);
                     __syncwarp();
                     break;
                 }
-                dfw t[8];
+                __syncwarp();
+                float ph8[8], pl8[8];
+                int pe8[8];
 #pragma unroll
                 for (int s = 0; s < 8; ++s) {
-                    t[s] = dfw_zero();
+                    ph8[s] = pl8[s] = 0.f;
+                    pe8[s] = 0;
                     if (s < ns) {
                         const size_t idx = xpart_index(v, DIR, B, s, lane);
-                        t[s] = dfw_norm(df{__ldcg(&v.parth[idx * 4]), __ldcg(&v.partl[idx * 4])}, __ldcg(&v.parte[idx]));
+                        ph8[s] = __ldcg(&v.parth[idx * 4]);
+                        pl8[s] = __ldcg(&v.partl[idx * 4]);
+                        pe8[s] = __ldcg(&v.parte[idx]);
                     }
                 }
+                seen = 0;
+                if (it + 1 < nb) {
+                    const int B2 = chain_block<DIR>(v, it + 1), ns2 = chain_nparts<DIR>(v, B2);
+                    if (lane < ns2) seen = ld_acquire(&flag_part[B2 * v.S + lane]) >= 1;
+                }
+                // the ring slot of block B was last read W iterations ago
+                if (!smem_wait_ge(&cs->done, it - W, cs, lim, v.err, 0x570000 + it)) break;
+                dfw t[8];
+#pragma unroll
+                for (int s = 0; s < 8; ++s) t[s] = s < ns ? dfw_norm(df{ph8[s], pl8[s]}, pe8[s]) : dfw_zero();
                 cput(C.ph, C.pl, C.pe, B % W, lane, dfw_sum8(t, ns));
+            } else {
+                seen = 0;
+                if (it + 1 < nb) {
+                    const int B2 = chain_block<DIR>(v, it + 1), ns2 = chain_nparts<DIR>(v, B2);
+                    if (lane < ns2) seen = ld_acquire(&flag_part[B2 * v.S + lane]) >= 1;
+                }
             }
             __threadfence_block();
             __syncwarp();
