@@ -872,7 +872,7 @@ extern "C" pimd_status pimd_autotune(pimd_t c, const char* cache_path)
         if (can_fold && sms > 16) {
             const int nb = (c->N + 1 + 31) / 32;
             std::vector<int> Hs;
-            for (int H : {nb / 2, nb, (3 * nb) / 2, 2 * nb, (5 * nb) / 2, 3 * nb}) {
+            for (int H : {nb / 2, nb, (5 * nb) / 4, (3 * nb) / 2, (7 * nb) / 4, 2 * nb, (5 * nb) / 2, 3 * nb}) {
                 H = std::max(4, std::min(sms - 2 - 8, H));
                 if (std::find(Hs.begin(), Hs.end(), H) == Hs.end()) Hs.push_back(H);
             }

@@ -436,7 +436,8 @@ __global__ void __launch_bounds__(256) xdf_prep_kernel(XView v) { prep_body(v); 
 // endpoints a_{n-1}, row constants c_n and 32 column endpoints b_k are staged
 // in shared memory once per tile; each element then needs only double-float
 // arithmetic (difference, TwoProduct square, sum, scale) and the exp.
-__device__ __forceinline__ void table_body(const XView& v, long long ntiles)
+template <int D>
+__device__ __forceinline__ void table_body_t(const XView& v, long long ntiles)
 {
     __shared__ float2 tab[256];
     __shared__ float sa[3][2][32], sb[3][2][32], scr[2][32];
@@ -479,7 +480,8 @@ __device__ __forceinline__ void table_body(const XView& v, long long ntiles)
             dfw m = dfw_zero();
             if (I >= 0 && n >= 1 && n <= v.N && k < n) {
                 df g = df{0.f, 0.f};
-                for (int cc = 0; cc < v.d; ++cc) {
+#pragma unroll
+                for (int cc = 0; cc < D; ++cc) {
                     const df x = df_sub(df{sa[cc][0][r], sa[cc][1][r]}, df{sb[cc][0][c], sb[cc][1][c]});
                     df sq = two_prod(x.h, x.h);
                     sq.l = __fmaf_rn(2.f * x.h, x.l, sq.l);
@@ -493,6 +495,14 @@ __device__ __forceinline__ void table_body(const XView& v, long long ntiles)
             Mt->e[o] = m.e;
         }
     }
+}
+
+// the dimension as a template argument, so the per-element coordinate loop unrolls
+__device__ __forceinline__ void table_body(const XView& v, long long ntiles)
+{
+    if (v.d == 1) table_body_t<1>(v, ntiles);
+    else if (v.d == 2) table_body_t<2>(v, ntiles);
+    else table_body_t<3>(v, ntiles);
 }
 
 __global__ void __launch_bounds__(256) xdf_table_kernel(XView v, long long ntiles) { table_body(v, ntiles); }
