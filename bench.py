@@ -148,9 +148,9 @@ class ClockSampler:
 # SHA-256 of their concatenation at capture time); otherwise the roofline line
 # reports traffic null.
 NCU_TRAFFIC = {
-    "exch_recursion": {"bytes": 18.038272e6 + 0.0, "sources": ["paper_2404_02628_gb300/csrc/pimd_xdf.cu",
+    "exch_recursion": {"bytes": 18.034176e6 + 256.0, "sources": ["paper_2404_02628_gb300/csrc/pimd_xdf.cu",
                                                            "paper_2404_02628_gb300/csrc/pimd_forcework.cuh"],
-                       "sha256_16": "6f5bc5dcca0c2403"},
+                       "sha256_16": "8c88cdd86abc182c"},
 }
 
 
