@@ -438,11 +438,8 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 5),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 pairs/springs + f64-accurate exchange", "data": "synthetic",
-            "config": {"workload": "gauss1600: N=1600 trapped bosons, d=2, P=32, beta=3, xi=1, "
-                                   "Gaussian g=1 s=0.5, NHC M=4, dt=0.01, mixed precision",
-                       "N": w["N"], "P": w["P"], "d": w["d"], "beta": w["beta"], "xi": w["xi"],
-                       "g": w["g"], "s": w["s"], "amp": "g/(pi s^2)", "parallelism": "replicas x%d" % ws,
-                       "l2": "flushed between timed steps (512 MB write)", "autotuned": tuning},
+            "config": dict(workload_config(w, ws), l2="flushed between timed steps (512 MB write)",
+                           autotuned=tuning),
             "roofline": {"kernel": dom, "bound": bound, "achieved": round(achieved, 6), "peak": peak,
                          "unit": unit, "frac": round(achieved / peak, 6), "traffic": ncu_traffic(dom),
                          "traffic_unit": "bytes per launch (ncu capture, same workload)",
@@ -486,6 +483,14 @@ def cpu_baseline(w, budget_s=12.0):
                       "FP64 C oracle" % (n, w["N"])}
 
 
+def workload_config(w, ws):
+    """The workload keys both arms report (same metric, same configuration)."""
+    return {"workload": "gauss1600: N=1600 trapped bosons, d=2, P=32, beta=3, xi=1, "
+                        "Gaussian g=1 s=0.5, NHC M=4, dt=0.01, mixed precision",
+            "N": w["N"], "P": w["P"], "d": w["d"], "beta": w["beta"], "xi": w["xi"],
+            "g": w["g"], "s": w["s"], "amp": "g/(pi s^2)", "parallelism": "replicas x%d" % ws}
+
+
 def run_reference(args):
     from workloads import WORKLOADS
 
@@ -516,8 +521,7 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": round(v, 5), "unit": "steps/s", "n_gpus": ws,
            "steps": K, "warmup": args.warmup, "ms_per_step": round(1e3 * dt / K, 3), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "gauss1600: N=1600 trapped bosons, d=2, P=32, beta=3, xi=1, Gaussian g=1 "
-                                  "s=0.5, NHC M=4, dt=0.01", "N": w["N"], "P": w["P"]},
+           "config": workload_config(w, ws),
            "cpu_baseline": {"value": round(v, 5), "unit": "steps/s", "cores": 1, "kind": "oracle", "sample": sample},
            "e2e": {"value": round(v, 5), "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)

@@ -58,3 +58,24 @@ def test_kernel_work_table():
     for name in ("exch_recursion", "exch_table", "pair", "md_pre", "md_post", "springs", "other"):
         bound, work, unit, peak, src = bench.kernel_work(name, w)
         assert bound in ("alu", "hbm") and work > 0 and peak > 0
+
+
+def test_reference_arm_line(capsys):
+    """The reference arm (the oracle on the host cores) prints one JSON line
+    with the contract's keys and the same workload config as the CUDA arm."""
+    import json
+    import types
+
+    import bench
+    from workloads import WORKLOADS
+
+    args = types.SimpleNamespace(steps=1, warmup=1, workload="gauss1600")
+    bench.run_reference(args)
+    line = capsys.readouterr().out.strip().splitlines()[-1]
+    d = json.loads(line)
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["value"] > 0
+    assert d["config"] == bench.workload_config(dict(WORKLOADS["gauss1600"]), 1)
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
