@@ -451,3 +451,26 @@ def test_radial_density_of_gaussian_samples(d):
     edges = np.arange(nbins + 1) * dr
     vol = {1: 2 * np.diff(edges), 2: np.pi * np.diff(edges**2), 3: 4 / 3 * np.pi * np.diff(edges**3)}[d]
     assert abs(float(np.sum(rho * vol)) - counts.sum() / n) < 1e-12
+
+
+@pytest.mark.parametrize("d", [1, 3])
+def test_exact_energy_other_dimensions(d):
+    """The trapped ideal gas factorises over Cartesian directions: the d-dimensional
+    distinguishable energy is d times the one-dimensional one, the N = 1 energy
+    is d/2 coth(beta omega / 2) in the continuum, and the permutation sum of
+    the partition function matches the recursion in d dimensions as well."""
+    beta, P = 1.7, 9
+    th, dth = exact.theta(beta, P)
+    ref = 5 * d * dth / math.tanh(th)
+    assert abs(exact.energy(5, beta, P, d=d, xi=0.0) - ref) <= 1e-12 * ref
+    assert abs(exact.energy(5, beta, P, d=d, xi=0.0) - d * exact.energy(5, beta, P, d=1, xi=0.0)) <= 1e-12 * ref
+    e1 = exact.energy(1, beta, None, d=d)
+    assert abs(e1 - 0.5 * d / math.tanh(beta / 2)) <= 1e-12 * e1
+    N, xi = 4, 0.6
+    z = {k: exact.ring_partition(k, beta, P, d=d) for k in range(1, N + 1)}
+    tot = 0.0
+    for perm in itertools.permutations(range(N)):
+        cl = cycle_lengths(perm)
+        tot += xi_pow(xi, N - len(cl)) * math.prod(z[k] for k in cl)
+    _, Z = exact.energy_mp(N, beta, P, d=d, xi=xi)
+    assert abs(float(Z[N]) - tot / math.factorial(N)) <= 1e-13 * tot / math.factorial(N)
