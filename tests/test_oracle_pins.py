@@ -474,3 +474,23 @@ def test_exact_energy_other_dimensions(d):
         tot += xi_pow(xi, N - len(cl)) * math.prod(z[k] for k in cl)
     _, Z = exact.energy_mp(N, beta, P, d=d, xi=xi)
     assert abs(float(Z[N]) - tot / math.factorial(N)) <= 1e-13 * tot / math.factorial(N)
+
+
+@pytest.mark.parametrize("d", [1, 3])
+def test_forces_match_finite_differences_other_dimensions(d):
+    """Exchange + trap + Gaussian-pair forces against Richardson-extrapolated
+    central differences of V_xi + U/P in one and three dimensions."""
+    N, P, beta, xi, om, A, s = 3, 4, 1.2, 0.7, 1.1, 2.0, 0.6
+    r = beads(N, P, d, 41 + d)
+    F, _ = oracle.forces(r, beta, xi, om, A, s)
+    h = 1e-3
+    Ffd = np.zeros_like(r)
+    for idx in np.ndindex(r.shape):
+        def Vat(dx):
+            q = r.copy()
+            q[idx] += dx
+            return _total_V(q, beta, xi, om, A, s)
+        d1 = (Vat(h) - Vat(-h)) / (2 * h)
+        d2 = (Vat(h / 2) - Vat(-h / 2)) / h
+        Ffd[idx] = -(4 * d2 - d1) / 3
+    np.testing.assert_allclose(F, Ffd, rtol=0, atol=1e-7 * np.abs(F).max())
