@@ -1,0 +1,73 @@
+"""The factorised form of the exchange recursion that the CUDA path solves,
+checked on CPU against the oracle's literal recursions (no GPU, no CUDA code).
+
+Sec. III's forward recursion over cycle energies E^[u,v] becomes, with
+a_i = r_i^P, b_k = r_k^1, g(i,k) = kappa |a_i - b_k|^2 (kappa = P / (2 beta)),
+row constants c_n = g(n-1,n) - ln n - ln xi (c_N = -ln N - ln xi) and
+M[n][k] = exp(c_n - g(n-1,k)) for 0 <= k < n <= N, the unit lower-triangular
+system y = e_0 + M y, and the backward recursion its transpose
+c = e_N + M^T c; then W_N = xi^N y[N], y[N] = c[0], and
+
+    V_xi = sum_l E_int(l) + sum_{i<N-1} g(i,i+1)/beta - (N ln xi + ln y[N]) / beta,
+    Pr[G(l) = k]   = M[l+1][k] y[k] c[l+1] / y[N]     (k <= l),
+    Pr[G(l) = l+1] = 1 - y[l+1] c[l+1] / y[N].
+
+Here both sides are plain FP64 (substitution on one side, the oracle's
+log-sum-exp recursions on the other), so a wrong sign, index or constant in
+the factorisation fails at the 1e-12 level.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from workloads import beads
+
+
+def _factorised(r, beta, xi):
+    N, P, d = r.shape
+    kappa = P / (2.0 * beta)
+    a, b = r[:, P - 1, :], r[:, 0, :]
+
+    def g(i, k):
+        return kappa * float(np.sum((a[i] - b[k]) ** 2))
+
+    c = np.zeros(N + 1)
+    for n in range(1, N + 1):
+        c[n] = (g(n - 1, n) if n < N else 0.0) - math.log(n) - math.log(xi)
+    M = np.zeros((N + 1, N + 1))
+    for n in range(1, N + 1):
+        for k in range(n):
+            M[n, k] = math.exp(c[n] - g(n - 1, k))
+    # forward and back substitution (every term is non-negative, so nothing cancels)
+    y = np.zeros(N + 1)
+    y[0] = 1.0
+    for n in range(1, N + 1):
+        y[n] = math.fsum(M[n, k] * y[k] for k in range(n))
+    cb = np.zeros(N + 1)
+    cb[N] = 1.0
+    for k in range(N - 1, -1, -1):
+        cb[k] = math.fsum(M[n, k] * cb[n] for n in range(k + 1, N + 1))
+    return M, y, cb, g
+
+
+@pytest.mark.parametrize("N,P,d,beta,xi,seed", [(1, 4, 2, 1.0, 1.0, 3), (5, 6, 2, 1.3, 0.4, 4),
+                                                (17, 8, 3, 0.8, 1.0, 5), (40, 5, 1, 2.0, 0.7, 6)])
+def test_factorised_system_reproduces_the_recursions(N, P, d, beta, xi, seed):
+    r = beads(N, P, d, seed) * 0.6  # keeps the plain (unscaled) FP64 factors in range
+    M, y, cb, g = _factorised(r, beta, xi)
+    Z = y[N]
+    assert abs(Z - cb[0]) <= 1e-12 * Z                      # forward and backward agree
+    E_int = sum(0.5 * P / beta**2 * float(np.sum(np.diff(r[l], axis=0) ** 2)) for l in range(N))
+    link = sum(g(i, i + 1) for i in range(N - 1)) / beta
+    V = E_int + link - (N * math.log(xi) + math.log(Z)) / beta
+    F, info, Pr = oracle.forces(r, beta, xi, want_pr=True)
+    assert abs(V - info["V_xi"]) <= 1e-12 * max(1.0, abs(info["V_xi"]))
+    Pf = np.zeros((N, N + 1))
+    for l in range(N):
+        for k in range(l + 1):
+            Pf[l, k] = M[l + 1, k] * y[k] * cb[l + 1] / Z
+        if l + 1 < N:
+            Pf[l, l + 1] = 1.0 - y[l + 1] * cb[l + 1] / Z
+    np.testing.assert_allclose(Pf, Pr, rtol=0, atol=1e-12)
