@@ -71,3 +71,39 @@ def test_factorised_system_reproduces_the_recursions(N, P, d, beta, xi, seed):
         if l + 1 < N:
             Pf[l, l + 1] = 1.0 - y[l + 1] * cb[l + 1] / Z
     np.testing.assert_allclose(Pf, Pr, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("N,B", [(23, 4), (40, 8), (9, 32)])
+def test_blocked_look_ahead_solve(N, B):
+    """The blocked form of the solve: with G_J = (I - M_JJ)^{-1},
+    Q_J = G_J M_{J,J-1}, P_J = M_{J+1,J} G_J and the off-band sums
+    h_J = sum_{I<=J-2} M_JI y_I, hb_J = sum_{I>=J+2} M_IJ^T c_I,
+        y_J = G_J h_J + Q_J y_{J-1},   c_J = G_J^T hb_J + P_J^T c_{J+1},
+    block by block (blocks of B indices, the last one ragged), equals the
+    plain substitution."""
+    r = beads(N, 5, 2, 70 + N) * 0.6
+    M, y, cb, _ = _factorised(r, 1.1, 0.8)
+    n = N + 1
+    nb = (n + B - 1) // B
+    sl = [slice(J * B, min(n, J * B + B)) for J in range(nb)]
+    e0 = np.zeros(n)
+    e0[0] = 1.0
+    eN = np.zeros(n)
+    eN[N] = 1.0
+    la = pytest.importorskip("scipy.linalg")
+    # G_J by unit lower-triangular substitution (all terms non-negative: no cancellation)
+    G = [la.solve_triangular(np.eye(sl[J].stop - sl[J].start) - M[sl[J], sl[J]], np.eye(sl[J].stop - sl[J].start),
+                             lower=True, unit_diagonal=True) for J in range(nb)]
+    yb = np.zeros(n)
+    for J in range(nb):
+        h = e0[sl[J]] + sum((M[sl[J], sl[I]] @ yb[sl[I]] for I in range(J - 1)), np.zeros(sl[J].stop - sl[J].start))
+        q = G[J] @ M[sl[J], sl[J - 1]] @ yb[sl[J - 1]] if J >= 1 else 0.0
+        yb[sl[J]] = G[J] @ h + q
+    np.testing.assert_allclose(yb, y, rtol=1e-11, atol=0)
+    cbb = np.zeros(n)
+    for J in range(nb - 1, -1, -1):
+        hb = eN[sl[J]] + sum((M[sl[I], sl[J]].T @ cbb[sl[I]] for I in range(J + 2, nb)),
+                             np.zeros(sl[J].stop - sl[J].start))
+        p = (M[sl[J + 1], sl[J]] @ G[J]).T @ cbb[sl[J + 1]] if J + 1 < nb else 0.0
+        cbb[sl[J]] = G[J].T @ hb + p
+    np.testing.assert_allclose(cbb, cb, rtol=1e-11, atol=0)
