@@ -107,3 +107,35 @@ def test_blocked_look_ahead_solve(N, B):
         p = (M[sl[J + 1], sl[J]] @ G[J]).T @ cbb[sl[J + 1]] if J + 1 < nb else 0.0
         cbb[sl[J]] = G[J].T @ hb + p
     np.testing.assert_allclose(cbb, cb, rtol=1e-11, atol=0)
+
+
+@pytest.mark.parametrize("N,P,d,beta,xi", [(7, 5, 2, 1.2, 1.0), (30, 4, 3, 0.9, 0.6), (12, 6, 1, 2.0, 0.3)])
+def test_endpoint_forces_from_connection_probabilities(N, P, d, beta, xi):
+    """Exterior-bead forces (Sec. III) in the form the finalize step uses:
+    bead P of l is pulled towards bead 1 of every l' it may connect to,
+    bead 1 of l towards bead P of every l'' that may connect to it, each
+    weighted by Pr; plus the internal springs.  Against the oracle's forces."""
+    r = beads(N, P, d, 90 + N) * 0.6
+    M, y, cb, _ = _factorised(r, beta, xi)
+    Z = y[N]
+    Pf = np.zeros((N, N + 1))
+    for l in range(N):
+        for k in range(l + 1):
+            Pf[l, k] = M[l + 1, k] * y[k] * cb[l + 1] / Z
+        if l + 1 < N:
+            Pf[l, l + 1] = 1.0 - y[l + 1] * cb[l + 1] / Z
+    ks = P / beta**2
+    a, b = r[:, P - 1, :], r[:, 0, :]
+    F, _ = oracle.forces(r, beta, xi, omega=0.0, A=0.0)  # exchange and springs only
+    for l in range(N):
+        fp = -ks * (a[l] - r[l, P - 2])
+        fp -= ks * sum(Pf[l, k] * (a[l] - b[k]) for k in range(l + 1))
+        if l + 1 < N:
+            fp -= ks * Pf[l, l + 1] * (a[l] - b[l + 1])
+        f1 = -ks * (b[l] - r[l, 1])
+        f1 -= ks * sum(Pf[m, l] * (b[l] - a[m]) for m in range(l, N))
+        if l >= 1:
+            f1 -= ks * Pf[l - 1, l] * (b[l] - a[l - 1])
+        scale = np.abs(F).max()
+        assert np.abs(fp - F[l, P - 1]).max() <= 1e-11 * scale, l
+        assert np.abs(f1 - F[l, 0]).max() <= 1e-11 * scale, l
