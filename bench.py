@@ -236,6 +236,22 @@ def mixed_force_error(pkg, S, w, device, snapshots=10, stride=20):
             "what": "|F_mixed - F_fp64|_inf / |F_fp64|_inf on snapshots of the timed trajectory"}
 
 
+def small_workload(pkg, w, device, flush, stream, K):
+    """Steps/s of one of the small reference workloads (graph-replayed, L2
+    flushed between steps like the main line)."""
+    import torch
+
+    S = make_system(pkg, dict(w), device)
+    tuning = S.autotune(None)
+    S.step(5)
+    torch.cuda.synchronize()
+    ms = timed_steps(S, K, flush, stream)
+    S.close()
+    return {"value": round(K / (ms / 1e3), 3), "unit": "steps/s", "steps": K, "ms_per_step": round(ms / K, 4),
+            "config": {"N": w["N"], "P": w["P"], "d": w["d"], "beta": w["beta"], "xi": w["xi"], "g": w["g"],
+                       "s": w["s"], "precision": w["precision"], "autotuned": tuning}}
+
+
 def memory_sweep(pkg, device, Ns=(10000, 20000, 30000, 40000), K=3):
     """Ideal trapped bosons (g = 0), P = 32, beta = 3, xi = 1, mixed precision:
     steps/s and workspace bytes against N, factor table stored and recomputed."""
@@ -425,6 +441,8 @@ def run_ours(args):
         S2.close()
         extra["batch64"] = run_batch(pkg, device, flush, stream, max(10, min(args.steps // 4, 50)), args.warmup)
         extra["mixed_vs_fp64_forces"] = mixed_force_error(pkg, S, w, device)
+        for name in ("ideal16", "gauss100"):
+            extra[name] = small_workload(pkg, WORKLOADS[name], device, flush, stream, max(20, min(args.steps, 500)))
         extra["sweep_ideal_N"] = memory_sweep(pkg, device)
 
     cpu = None
