@@ -443,6 +443,9 @@ def run_ours(args):
         extra["mixed_vs_fp64_forces"] = mixed_force_error(pkg, S, w, device)
         for name in ("ideal16", "gauss100"):
             extra[name] = small_workload(pkg, WORKLOADS[name], device, flush, stream, max(20, min(args.steps, 500)))
+        # the paper's timing workloads; its RTX 4090 figures (about 2.6 and 0.24 steps/s) are context only
+        extra["paper1600"] = small_workload(pkg, WORKLOADS["paper1600"], device, flush, stream, max(20, min(args.steps, 200)))
+        extra["paper10000"] = small_workload(pkg, WORKLOADS["paper10000"], device, flush, stream, 10)
         extra["sweep_ideal_N"] = memory_sweep(pkg, device)
 
     cpu = None

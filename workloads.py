@@ -30,6 +30,11 @@ WORKLOADS = {
                       precision="mixed", M=4, dt=0.01, seed=3),
     "ideal10000": dict(N=10000, P=32, d=2, beta=3.0, xi=1.0, g=0.0, s=0.5, omega=1.0,
                        precision="mixed", M=4, dt=0.01, seed=5),
+    # the paper's own timing runs (Sec. IV A: ideal trapped bosons at beta = 6, P = 72)
+    "paper1600": dict(N=1600, P=72, d=2, beta=6.0, xi=1.0, g=0.0, s=0.5, omega=1.0,
+                      precision="mixed", M=4, dt=0.01, seed=6),
+    "paper10000": dict(N=10000, P=72, d=2, beta=6.0, xi=1.0, g=0.0, s=0.5, omega=1.0,
+                       precision="mixed", M=4, dt=0.01, seed=7),
 }
 
 BATCH64 = dict(R=64, N_lo=32, N_hi=512, P=32, d=2, betas=(1.0, 2.0, 3.0, 4.0),
