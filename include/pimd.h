@@ -285,6 +285,8 @@ pimd_status pimd_batch_estimators(pimd_batch_t b, pimd_estimates* out);
 /* Autotuner of the batched step (as pimd_autotune): the pair-kernel block of
  * 64, 128 or 256 particles, cached by device and (R, sum N, sum N^2, P, d). */
 pimd_status pimd_batch_autotune(pimd_batch_t b, const char* cache_path);
+/* The batch's current pair-kernel block (host only; any time after create). */
+pimd_status pimd_batch_tuning(pimd_batch_t b, int* pair_block);
 pimd_status pimd_batch_sync(pimd_batch_t b);
 const char* pimd_batch_last_error(pimd_batch_t b);
 void pimd_batch_destroy(pimd_batch_t b);

@@ -26,7 +26,7 @@ __all__ = [
     "pimd_batch_step_eager", "pimd_batch_step_profiled", "pimd_batch_profile_slot_name",
     "pimd_batch_estimators", "pimd_batch_sync", "pimd_batch_last_error", "pimd_batch_destroy",
     "pimd_batch_autotune", "pimd_autotune", "pimd_tuning", "pimd_init_state", "pimd_batch_init_state",
-    "pimd_density_accumulate",
+    "pimd_density_accumulate", "pimd_batch_tuning",
 ]
 
 PIMD_OK, PIMD_EINVAL, PIMD_ENOMEM, PIMD_ECUDA, PIMD_ETIMEOUT, PIMD_ENONFINITE, PIMD_ESTATE = range(7)
@@ -127,6 +127,7 @@ _SIGS = {
     "pimd_batch_destroy": ([_vp], None),
     "pimd_autotune": ([_vp, ctypes.c_char_p], ctypes.c_int),
     "pimd_density_accumulate": ([_vp, ctypes.c_int, ctypes.c_double, _vp], ctypes.c_int),
+    "pimd_batch_tuning": ([_vp, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "pimd_init_state": ([_vp, ctypes.c_ulonglong], ctypes.c_int),
     "pimd_batch_init_state": ([_vp, ctypes.c_ulonglong], ctypes.c_int),
     "pimd_tuning": ([_vp] + [ctypes.POINTER(ctypes.c_int)] * 4, ctypes.c_int),
@@ -393,6 +394,12 @@ def pimd_density_accumulate(h, nbins, r_max, hist_ptr):
     return _check(lib().pimd_density_accumulate(h, int(nbins), float(r_max), hist_ptr), h)
 
 
+def pimd_batch_tuning(h):
+    T = ctypes.c_int()
+    _bcheck(lib().pimd_batch_tuning(h, ctypes.byref(T)), h)
+    return {"pair_block": T.value}
+
+
 def pimd_init_state(h, seed):
     return _check(lib().pimd_init_state(h, int(seed) & 0xFFFFFFFFFFFFFFFF), h)
 
@@ -481,6 +488,7 @@ class Batch:
 
     def autotune(self, cache_path=None):
         pimd_batch_autotune(self.h, cache_path)
+        return pimd_batch_tuning(self.h)
 
     def estimators(self):
         return pimd_batch_estimators(self.h, self.R)

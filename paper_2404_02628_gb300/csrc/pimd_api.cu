@@ -1645,6 +1645,13 @@ static void batch_set_pair_t(pimd_batch* b, int T)
     b->grid.gx_pair = pair_grid_x(nmax, T);
 }
 
+extern "C" pimd_status pimd_batch_tuning(pimd_batch_t b, int* pair_block)
+{
+    if (!b || !pair_block) return bfail(b, PIMD_EINVAL, "pimd_batch_tuning: NULL argument");
+    *pair_block = pair_block_ok(b->grid.pair_t) ? b->grid.pair_t : 128;  // the layout's default before bind
+    return PIMD_OK;
+}
+
 extern "C" pimd_status pimd_batch_autotune(pimd_batch_t b, const char* cache_path)
 {
     if (!b) return bfail(b, PIMD_EINVAL, "pimd_batch_autotune: NULL handle");

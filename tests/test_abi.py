@@ -192,3 +192,12 @@ def test_init_state_and_density_require_bound_handle(pkg):
         assert ei.value.status == pkg.PIMD_ESTATE
     finally:
         pkg.pimd_batch_destroy(b)
+
+
+def test_batch_tuning_host_query(pkg):
+    b = pkg.pimd_batch_create([10, 20], 4, 2, [1.0, 1.0], [1.0, 1.0], 1.0, 3.0, 0.5)
+    try:
+        t = pkg.pimd_batch_tuning(b)
+        assert t["pair_block"] in (64, 128, 256)
+    finally:
+        pkg.pimd_batch_destroy(b)
