@@ -28,7 +28,10 @@
  *    from pimd_last_error (pimd_global_error for failures before a handle
  *    exists).  Device-side failures (a bounded cross-block wait that gave up)
  *    are recorded in the workspace and reported by the next synchronising
- *    call as PIMD_ETIMEOUT.
+ *    call as PIMD_ETIMEOUT.  Every wait gives up after spin_limit polls; where
+ *    a call's configuration leaves spin_limit at 0, or the call takes none
+ *    (the exchange-potential calls), the PIMD_SPIN_LIMIT environment variable
+ *    (a positive integer, read at each call) sets it, else 2^24.
  *  - Bead arrays are slice-major FP64: element (bead j, component c,
  *    particle l) of an array x lives at x[(j*d + c)*n_pad + l], 0-based,
  *    n_pad >= N a multiple of 32; padding entries are never read.
@@ -76,7 +79,8 @@ typedef struct {
     int table_mode;     /* PIMD_TABLE_STORE (default) or PIMD_TABLE_RECOMPUTE           */
     int thermostat;     /* 1 = massive NHC (default), 0 = plain velocity Verlet (NVE)   */
     int helper_ctas;    /* exchange-recursion helper blocks; 0 = one per SM (default)   */
-    int spin_limit;     /* polls before a cross-block wait gives up; 0 = default (~1e7) */
+    int spin_limit;     /* polls before a cross-block wait gives up; 0 = default (2^24,
+                           or PIMD_SPIN_LIMIT)                                          */
     int exchange_arith; /* PIMD_XARITH_DF (default): exchange recursion, probabilities and
                            endpoint forces in double-float (FP32 pairs, ~48-bit mantissa, int32
                            exponent) on the FP32 pipe; PIMD_XARITH_FP64: native FP64 throughout */
@@ -317,6 +321,14 @@ pimd_status pimd_vb_forward(pimd_vb_t h, const double* r1, const double* rP, int
 pimd_status pimd_vb_backward(pimd_vb_t h, const double* r1, const double* rP, int ld,
                              void* work, size_t work_bytes, const double* gV,
                              double* g_r1, double* g_rP, void* stream);
+/* Synchronises `stream` and reports device-side failures of the earlier
+ * pimd_vb_forward / pimd_vb_backward calls on this workspace: PIMD_ETIMEOUT
+ * if a bounded cross-block wait of the recursion gave up (the error word in
+ * the workspace is then cleared, so the next forward starts clean), PIMD_OK
+ * otherwise.  A forward whose wait gave up writes NaN to V_out, and a
+ * backward after it writes NaN gradients, so callers that cannot synchronise
+ * still see invalid results.  work, work_bytes: as given to the calls. */
+pimd_status pimd_vb_sync(pimd_vb_t h, void* work, size_t work_bytes, void* stream);
 void pimd_vb_destroy(pimd_vb_t h);
 
 /* Same value as pimd_vb_forward (V_ends), for callers that cannot allocate
@@ -334,7 +346,10 @@ void pimd_vb_destroy(pimd_vb_t h);
  * device, with that device current), so make that first call before any
  * stream capture.  All calls share the one array and each call overwrites it:
  * calls whose work overlaps on the GPU (different streams, or different host
- * threads) race and give wrong results; serialise them on one stream. */
+ * threads) race and give wrong results; serialise them on one stream.
+ * If a bounded wait of the recursion gives up (see PIMD_SPIN_LIMIT), the
+ * call still returns PIMD_OK (it does not synchronise) but writes NaN to
+ * *V_out, so the failure shows in the result itself. */
 pimd_status pimd_vb_forward_noalloc(int N, int P, int d, double beta, double xi, const double* r1,
                                     const double* rP, int ld, double* V_out, void* stream);
 

@@ -19,7 +19,7 @@ __all__ = [
     "pimd_forces", "pimd_exchange_forces", "pimd_interaction_forces", "pimd_step", "pimd_step_eager",
     "pimd_estimators", "pimd_state_bytes", "pimd_get_state", "pimd_set_state", "pimd_sync",
     "pimd_last_error", "pimd_global_error", "pimd_destroy", "pimd_vb_create", "pimd_vb_workspace_bytes",
-    "pimd_vb_forward", "pimd_vb_backward", "pimd_vb_destroy", "pimd_vb_set_table_mode", "pimd_step_profiled",
+    "pimd_vb_forward", "pimd_vb_backward", "pimd_vb_destroy", "pimd_vb_sync", "pimd_vb_set_table_mode", "pimd_step_profiled",
     "pimd_profile_slot_name", "pimd_vb_forward_noalloc", "System",
     "pimd_batch_create", "pimd_batch_configure", "pimd_batch_layout", "pimd_batch_workspace_bytes",
     "pimd_batch_bind", "pimd_batch_forces", "pimd_batch_capture_graph", "pimd_batch_step",
@@ -105,6 +105,7 @@ _SIGS = {
     "pimd_vb_forward": ([_vp, _vp, _vp, ctypes.c_int, _vp, ctypes.c_size_t, _vp, _vp], ctypes.c_int),
     "pimd_vb_backward": ([_vp, _vp, _vp, ctypes.c_int, _vp, ctypes.c_size_t, _vp, _vp, _vp, _vp], ctypes.c_int),
     "pimd_vb_destroy": ([_vp], None),
+    "pimd_vb_sync": ([_vp, _vp, ctypes.c_size_t, _vp], ctypes.c_int),
     "pimd_step_profiled": ([_vp, ctypes.c_int, _dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "pimd_profile_slot_name": ([_vp, ctypes.c_int], ctypes.c_char_p),
     "pimd_vb_forward_noalloc": ([ctypes.c_int] * 3 + [ctypes.c_double] * 2 + [_vp, _vp, ctypes.c_int, _vp, _vp],
@@ -300,6 +301,10 @@ def pimd_vb_forward(h, r1, rP, ld, work, work_bytes, V_out, stream):
 
 def pimd_vb_backward(h, r1, rP, ld, work, work_bytes, gV, g_r1, g_rP, stream):
     return _check(lib().pimd_vb_backward(h, r1, rP, ld, work, work_bytes, gV, g_r1, g_rP, stream))
+
+
+def pimd_vb_sync(h, work, work_bytes, stream):
+    return _check(lib().pimd_vb_sync(h, work, work_bytes, stream))
 
 
 def pimd_vb_destroy(h):

@@ -11,7 +11,7 @@ pimd_vb_backward); this module only marshals tensors.
 import torch
 
 from . import (pimd_vb_backward, pimd_vb_create, pimd_vb_destroy, pimd_vb_forward, pimd_vb_set_table_mode,
-               pimd_vb_workspace_bytes)
+               pimd_vb_sync, pimd_vb_workspace_bytes)
 
 
 class VB:
@@ -19,10 +19,15 @@ class VB:
 
     table_mode: None (store up to N = 16383, recompute above), or the
     package's TABLE_STORE / TABLE_RECOMPUTE.
+    check: after each forward and backward, synchronise and raise PimdError
+    (PIMD_ETIMEOUT) if a bounded device wait gave up (pimd_vb_sync).  With
+    check=False the calls stay asynchronous and a failed call shows up as
+    NaN in V and the gradients.
     """
 
-    def __init__(self, N, P, d, beta, xi, device="cuda", table_mode=None):
+    def __init__(self, N, P, d, beta, xi, device="cuda", table_mode=None, check=True):
         self.N, self.P, self.d, self.beta, self.xi = N, P, d, beta, xi
+        self.check = check
         self.h = pimd_vb_create(N, P, d, beta, xi)
         if table_mode is not None:
             pimd_vb_set_table_mode(self.h, table_mode)
@@ -47,7 +52,12 @@ class VB:
         pimd_vb_forward(self.h, r1c.data_ptr(), rPc.data_ptr(), self.N, self.work_ptr, self.work_bytes,
                         V.data_ptr(), stream)
         self.generation += 1
+        self._check(stream)
         return self.generation
+
+    def _check(self, stream):
+        if self.check:
+            pimd_vb_sync(self.h, self.work_ptr, self.work_bytes, stream)
 
 
 def _component_major(x, N, d):
@@ -82,6 +92,7 @@ class VBFunction(torch.autograd.Function):
         stream = torch.cuda.current_stream(r1c.device).cuda_stream
         pimd_vb_backward(vb.h, r1c.data_ptr(), rPc.data_ptr(), vb.N, vb.work_ptr, vb.work_bytes, g.data_ptr(),
                          g1.data_ptr(), gP.data_ptr(), stream)
+        vb._check(stream)
         return g1.t(), gP.t(), None
 
 

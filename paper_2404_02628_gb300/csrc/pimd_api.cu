@@ -94,7 +94,7 @@ ExchView exch_view(char* base, const ExchLayout& o, int N, int P, int d, double 
     v.flags = (int*)(base + o.flags);
     v.err = (int*)(base + o.err);
     v.lsum = (double*)(base + o.lsum);
-    v.spin_limit = spin_limit > 0 ? spin_limit : (1 << 24);
+    v.spin_limit = default_spin_limit(spin_limit);
     if (n_help < 2) n_help = 2;
     v.n_help_f = n_help / 2;
     v.n_help_b = n_help - v.n_help_f;
@@ -195,7 +195,7 @@ XView xdf_view(char* base, const XLayout& o, int N, int P, int d, double beta, d
     XP(parth, float); XP(partl, float); XP(parte, int); XP(bandh, float); XP(bandl, float); XP(bande, int);
     XP(flags, int); XP(err, int); XP(lsum, double); XP(lam, double);
 #undef XP
-    v.spin_limit = spin_limit > 0 ? spin_limit : (1 << 24);
+    v.spin_limit = default_spin_limit(spin_limit);
     if (n_help < 2) n_help = 2;
     v.n_help_f = n_help / 2;
     v.n_help_b = n_help - v.n_help_f;
@@ -1202,6 +1202,28 @@ extern "C" pimd_status pimd_vb_backward(pimd_vb_t h, const double* r1, const dou
     o.part = (double*)((char*)work + h->off_fin);
     cudaError_t e = xdf_launch_adjoint(v, o, st, nullptr);
     if (e != cudaSuccess) return fail(nullptr, PIMD_ECUDA, std::string("pimd_vb_backward: ") + cudaGetErrorString(e));
+    return PIMD_OK;
+}
+
+extern "C" pimd_status pimd_vb_sync(pimd_vb_t h, void* work, size_t work_bytes, void* stream)
+{
+    if (!h || !work) return fail(nullptr, PIMD_EINVAL, "pimd_vb_sync: NULL argument");
+    if (((uintptr_t)work & 255) != 0) return fail(nullptr, PIMD_EINVAL, "pimd_vb_sync: workspace not 256-byte aligned");
+    if (work_bytes < h->L.total) return fail(nullptr, PIMD_ENOMEM, "pimd_vb_sync: workspace too small");
+    cudaStream_t st = (cudaStream_t)stream;
+    int* errp = (int*)((char*)work + h->xl.err);
+    cudaError_t e = cudaStreamSynchronize(st);
+    int code = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&code, errp, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail(nullptr, PIMD_ECUDA, std::string("pimd_vb_sync: ") + cudaGetErrorString(e));
+    if (code != 0) {
+        e = cudaMemsetAsync(errp, 0, sizeof(int), st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return fail(nullptr, PIMD_ECUDA, std::string("pimd_vb_sync: ") + cudaGetErrorString(e));
+        char msg[160];
+        snprintf(msg, sizeof msg, "pimd_vb_sync: a device wait gave up (code 0x%08x); the last values are NaN", code);
+        return fail(nullptr, PIMD_ETIMEOUT, msg);
+    }
     return PIMD_OK;
 }
 

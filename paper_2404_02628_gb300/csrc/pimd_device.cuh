@@ -10,6 +10,9 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdlib.h>
+
+#include <mutex>
 
 #define PIMD_TB 32            // exchange tile edge: 32 rows x 32 columns, one warp lane per row
 #define WEF_ZERO_E (-(1 << 29))
@@ -157,4 +160,44 @@ __device__ __forceinline__ void block_reduce(double (&v)[NV], double* smem /* 32
         }
     }
     block_sync();
+}
+
+// ---------------------------------------------------------------------------
+// Host side: one-time set-up per device (kernel attributes such as the
+// dynamic shared-memory opt-in belong to the device that is current when they
+// are set).  set() runs under a lock, with the device current, until it
+// succeeds once on that device.
+
+struct DeviceOnce {
+    std::mutex mu;
+    bool done[128] = {};
+};
+
+template <class F>
+inline cudaError_t device_once(DeviceOnce& o, F&& set)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(o.mu);
+    if (o.done[dev]) return cudaSuccess;
+    e = set();
+    if (e == cudaSuccess) o.done[dev] = true;
+    return e;
+}
+
+// Poll count of the bounded device waits when a call's configuration leaves
+// it at 0: the PIMD_SPIN_LIMIT environment variable if set to a positive
+// integer (lets tests drive the timeout paths of calls that take no
+// configuration), otherwise 2^24.
+inline int default_spin_limit(int configured)
+{
+    if (configured > 0) return configured;
+    const char* s = getenv("PIMD_SPIN_LIMIT");
+    if (s && *s) {
+        const long v = strtol(s, nullptr, 10);
+        if (v > 0 && v < (1L << 30)) return (int)v;
+    }
+    return 1 << 24;
 }

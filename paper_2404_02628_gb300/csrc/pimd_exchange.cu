@@ -678,7 +678,8 @@ __global__ void __launch_bounds__(256) exch_finalize_kernel(ExchView v, Finalize
             }
         }
         if (o.g1) {
-            const double gs = *o.gscale;
+            // a device wait that gave up makes every gradient NaN
+            const double gs = *(volatile int*)v.err != 0 ? __longlong_as_double(0x7ff8000000000000LL) : *o.gscale;
             for (int c = 0; c < v.d; ++c) {
                 o.g1[(size_t)c * o.ldg + l] = -gs * F1[c];
                 o.gP[(size_t)c * o.ldg + l] = -gs * FP[c];
@@ -691,9 +692,15 @@ __global__ void __launch_bounds__(256) exch_finalize_kernel(ExchView v, Finalize
 
 // V_ends = sum_{i<N-1} g(i,i+1)/beta - (N ln xi + ln Z)/beta (xi > 0), or with
 // the xi = 0 product of the diagonal chain.
+// A device wait that gave up during the call (error word set) gives NaN, so
+// a caller that cannot synchronise still sees that the value is invalid.
 __global__ void exch_vb_value_kernel(ExchView v, int nprep, double* V_out)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (*(volatile int*)v.err != 0) {
+        *V_out = __longlong_as_double(0x7ff8000000000000LL);
+        return;
+    }
     double gl = 0.0, l0 = 0.0;
     for (int i = 0; i < nprep; ++i) {
         gl += v.lsum[2 * i];
@@ -730,12 +737,11 @@ cudaError_t exch_launch_forward(const ExchView& v, cudaStream_t st, int coop, Pr
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t smem = exch_recursion_smem();
-    static bool attr_set = false;
-    if (!attr_set) {
-        e = cudaFuncSetAttribute(exch_recursion_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static DeviceOnce attr_once;
+    e = device_once(attr_once, [&] {
+        return cudaFuncSetAttribute(exch_recursion_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    });
+    if (e != cudaSuccess) return e;
     const int grid = 2 + v.n_help_f + v.n_help_b;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);

@@ -583,13 +583,12 @@ cudaError_t launch_density(const BeadView& b, int nbins, double dr, double* hist
     const long long n = (long long)b.P * b.N;
     const int grid = (int)std::min<long long>((n + 255) / 256, 152 * 4);
     const size_t smem = (size_t)nbins * sizeof(unsigned int);
-    static bool attr = false;
-    if (!attr) {
-        const cudaError_t e = cudaFuncSetAttribute(density_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)(DENSITY_MAX_BINS * sizeof(unsigned int)));
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static DeviceOnce attr_once;
+    const cudaError_t e = device_once(attr_once, [] {
+        return cudaFuncSetAttribute(density_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(DENSITY_MAX_BINS * sizeof(unsigned int)));
+    });
+    if (e != cudaSuccess) return e;
     density_kernel<<<grid, 256, smem, st>>>(b, nbins, dr, hist);
     return cudaGetLastError();
 }

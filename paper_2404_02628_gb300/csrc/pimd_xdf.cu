@@ -1412,7 +1412,9 @@ __device__ __forceinline__ void finalize_body(const XView& v, const FinalizeOut&
                 }
             }
             if (o.g1) {
-                const double gs = *o.gscale;
+                // a device wait that gave up makes every gradient NaN
+                const double gs =
+                    *(volatile int*)v.err != 0 ? __longlong_as_double(0x7ff8000000000000LL) : *o.gscale;
                 for (int c = 0; c < D; ++c) {
                     o.g1[(size_t)c * o.ldg + l] = -gs * F1[c];
                     o.gP[(size_t)c * o.ldg + l] = -gs * FP[c];
@@ -1686,9 +1688,14 @@ __global__ void __launch_bounds__(256) finalize_batch(const RepArgs* ra)
 // V_ends = V_xi - sum E_int = (sum_l g(l, l+1) - ln W_N)/beta with
 // ln W_N = N ln xi + ln y[N] (xi = 0: the diagonal chain), from the prep
 // partial sums and the forward solution (Sec. III).
+// A device wait that gave up during the call (error word set) gives NaN.
 __global__ void xdf_vb_value_kernel(XView v, int nprep, double* V_out)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (*(volatile int*)v.err != 0) {
+        *V_out = __longlong_as_double(0x7ff8000000000000LL);
+        return;
+    }
     double gl = 0.0, l0 = 0.0;
     for (int i = 0; i < nprep; ++i) {
         gl += v.lsum[2 * i];
@@ -1725,18 +1732,18 @@ cudaError_t xdf_launch_forward(const XView& v, cudaStream_t st, ProfMarks* pm, c
     const int tgrid = (int)min(nt, (long long)152 * 16);
     xdf_table_kernel<<<tgrid, 256, 0, st>>>(v, nt);
     prof_mark(pm, "exch_table", st);
-    cudaError_t e;
-    static bool attrs = false;
-    if (!attrs) {
-        e = cudaFuncSetAttribute(xdf_blockops_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)blockops_smem());
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(xdf_recursion_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    static DeviceOnce attr_once;
+    cudaError_t e = device_once(attr_once, [] {
+        cudaError_t r = cudaFuncSetAttribute(xdf_blockops_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)blockops_smem());
+        if (r == cudaSuccess)
+            r = cudaFuncSetAttribute(xdf_recursion_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)xdf_recursion_smem(XDF_MAXW));
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(xdf_band_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)band_smem(8));
-        if (e != cudaSuccess) return e;
-        attrs = true;
-    }
+        if (r == cudaSuccess)
+            r = cudaFuncSetAttribute(xdf_band_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)band_smem(8));
+        return r;
+    });
+    if (e != cudaSuccess) return e;
     // two blocks per diagonal block while 2 nb blocks fit one wave (two 1024-thread blocks per SM)
     xdf_blockops_kernel<<<dim3(v.nb, v.nb <= 152 ? 2 : 1), XDF_BLOCKOPS_T, blockops_smem(), st>>>(v);
     prof_mark(pm, "exch_blockops", st);
@@ -1795,17 +1802,16 @@ size_t xsolo_smem() { return XS_SLOTS * sizeof(DfwTile) + sizeof(SoloS); }
 
 cudaError_t batch_launch_exchange(const RepArgs* ra, const BatchGrid& g, cudaStream_t st, ProfMarks* pm)
 {
-    static bool attrs = false;
-    cudaError_t e;
-    if (!attrs) {
-        e = cudaFuncSetAttribute(xsolo_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsolo_smem());
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(band_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)band_smem(8));
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(blockops_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)blockops_smem());
-        if (e != cudaSuccess) return e;
-        attrs = true;
-    }
+    static DeviceOnce attr_once;
+    cudaError_t e = device_once(attr_once, [] {
+        cudaError_t r = cudaFuncSetAttribute(xsolo_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsolo_smem());
+        if (r == cudaSuccess)
+            r = cudaFuncSetAttribute(band_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)band_smem(8));
+        if (r == cudaSuccess)
+            r = cudaFuncSetAttribute(blockops_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)blockops_smem());
+        return r;
+    });
+    if (e != cudaSuccess) return e;
     prep_batch<<<dim3(g.gx_prep, 1, g.R), XDF_SMALL_T, 0, st>>>(ra);
     prof_mark(pm, "batch_exch_prep", st);
     table_batch<<<dim3(g.gx_table, 1, g.R), 256, 0, st>>>(ra);

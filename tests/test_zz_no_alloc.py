@@ -42,7 +42,10 @@ def test_noalloc_matches_workspace_entry_point_twice():
     torch = pytest.importorskip("torch")
     pkg.load()
     stream = torch.cuda.current_stream().cuda_stream
-    cases = [(300, 8, 2, 2.0, 1.0, 11), (257, 6, 2, 1.5, 0.4, 12)]
+    # the documented limit N = 1024, a ragged N, d = 3 and the xi = 0 branch
+    # (V from the diagonal chain only)
+    cases = [(300, 8, 2, 2.0, 1.0, 11), (257, 6, 2, 1.5, 0.4, 12), (1024, 8, 2, 2.0, 1.0, 13),
+             (333, 6, 3, 1.5, 0.0, 14)]
     for N, P, d, beta, xi, seed in cases:
         r1, rP = _endpoints(torch, N, P, d, seed)
         ref = _with_workspace(torch, N, P, d, beta, xi, r1, rP, stream)
@@ -51,6 +54,27 @@ def test_noalloc_matches_workspace_entry_point_twice():
         torch.cuda.synchronize()
         got = float(V.item())
         assert abs(got - ref) <= TOL * abs(ref), (N, got, ref)
+
+
+def test_noalloc_timeout_writes_nan_then_recovers(monkeypatch):
+    """A bounded wait that gives up (one-poll limit via PIMD_SPIN_LIMIT) makes
+    the call write NaN, since the call itself does not synchronise; the next
+    call with the normal limit gives the right value from the same scratch."""
+    torch = pytest.importorskip("torch")
+    pkg.load()
+    stream = torch.cuda.current_stream().cuda_stream
+    N, P, d, beta, xi = 1024, 4, 2, 2.0, 1.0
+    r1, rP = _endpoints(torch, N, P, d, 15)
+    V = torch.zeros(1, dtype=torch.float64, device="cuda")
+    monkeypatch.setenv("PIMD_SPIN_LIMIT", "1")
+    pkg.pimd_vb_forward_noalloc(N, P, d, beta, xi, r1.data_ptr(), rP.data_ptr(), N, V.data_ptr(), stream)
+    torch.cuda.synchronize()
+    assert np.isnan(float(V.item()))
+    monkeypatch.delenv("PIMD_SPIN_LIMIT")
+    ref = _with_workspace(torch, N, P, d, beta, xi, r1, rP, stream)
+    pkg.pimd_vb_forward_noalloc(N, P, d, beta, xi, r1.data_ptr(), rP.data_ptr(), N, V.data_ptr(), stream)
+    torch.cuda.synchronize()
+    assert abs(float(V.item()) - ref) <= TOL * abs(ref)
 
 
 def test_noalloc_rejects_oversized_problem():
