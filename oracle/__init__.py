@@ -25,8 +25,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "pimd_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liborc.so")
+_LIB_LD = os.path.join(_BUILD, "liborc_ld.so")
 _lock = threading.Lock()
 _lib = None
+_lib_ld = None
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
@@ -48,19 +50,27 @@ class Estimates(ctypes.Structure):
 ESTIMATE_FIELDS = [f[0] for f in Estimates._fields_]
 
 
+def _compile(out, defines, force):
+    if (not force and os.path.exists(out)
+            and os.path.getmtime(out) >= os.path.getmtime(_SRC)):
+        return out
+    tmp = out + ".%d.tmp" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared"] + defines + [
+        "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle (plain C, -O2, no FMA contraction) into oracle/_build."""
+    """Compile the oracle (plain C, -O2, no FMA contraction) into oracle/_build:
+    the FP64 library and its extended-precision twin (same source, every
+    quantity ``long double``: 64-bit significand on x86-64, IEEE binary128 on
+    aarch64)."""
     with _lock:
         os.makedirs(_BUILD, exist_ok=True)
-        if (not force and os.path.exists(_LIB)
-                and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
-            return _LIB
-        tmp = _LIB + ".%d.tmp" % os.getpid()
-        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-               "-o", tmp, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB)
-        return _LIB
+        _compile(_LIB_LD, ["-DORC_REAL=long double"], force)
+        return _compile(_LIB, [], force)
 
 
 def lib():
@@ -268,3 +278,63 @@ def radial_density(r, nbins, r_max):
     else:
         vol = 4.0 / 3.0 * np.pi * (edges[1:] ** 3 - edges[:-1] ** 3)
     return counts / (N * P * vol), counts
+
+
+# --------------------------------------------------------------------------
+# Extended-precision twin (same C source, every quantity long double): how far
+# FP64 evaluations of the exchange part sit from the exact value of the same
+# formulas.  Inputs are converted exactly (float64 -> long double).
+
+_ldp = ctypes.POINTER(ctypes.c_longdouble)
+
+
+def lib_ld():
+    global _lib_ld
+    if _lib_ld is None:
+        build()
+        L = ctypes.CDLL(_LIB_LD)
+        L.orc_cycle_energies.argtypes = [ctypes.c_int] * 3 + [_ldp, ctypes.c_longdouble, _ldp]
+        L.orc_V_forward.argtypes = [ctypes.c_int, _ldp, ctypes.c_longdouble, ctypes.c_longdouble, _ldp]
+        L.orc_V_backward.argtypes = [ctypes.c_int, _ldp, ctypes.c_longdouble, ctypes.c_longdouble, _ldp]
+        L.orc_connection_probabilities.argtypes = [ctypes.c_int, _ldp, _ldp, _ldp, ctypes.c_longdouble,
+                                                   ctypes.c_longdouble, _ldp]
+        L.orc_exchange_forces.argtypes = [ctypes.c_int] * 3 + [_ldp, ctypes.c_longdouble, _ldp, _ldp]
+        L.orc_spring_expectation.restype = ctypes.c_longdouble
+        L.orc_spring_expectation.argtypes = [ctypes.c_int] * 3 + [_ldp, ctypes.c_longdouble, _ldp]
+        _lib_ld = L
+    return _lib_ld
+
+
+def _pl(a):
+    return a.ctypes.data_as(_ldp)
+
+
+def extended_significand_bits():
+    """Significand bits of the extended twin's type (53 would mean no gain)."""
+    return int(np.finfo(np.longdouble).nmant) + 1
+
+
+def exchange_extended(r, beta, xi):
+    """Exchange part in extended precision: (F, info) with F = -grad V_xi
+    (shape (N, P, d), np.longdouble) and info holding V_xi, V_xi_bwd and the
+    expected spring energy as np.longdouble; same formulas and order as the
+    FP64 oracle (Sec. III)."""
+    r64 = _conf(r)
+    N, P, d = r64.shape
+    L = lib_ld()
+    rl = np.ascontiguousarray(r64, dtype=np.longdouble)
+    b = ctypes.c_longdouble(beta)
+    x = ctypes.c_longdouble(xi)
+    E = np.zeros((N, N), dtype=np.longdouble)
+    L.orc_cycle_energies(N, P, d, _pl(rl), b, _pl(E))
+    Vf = np.zeros(N + 1, dtype=np.longdouble)
+    Vb = np.zeros(N + 1, dtype=np.longdouble)
+    L.orc_V_forward(N, _pl(E), b, x, _pl(Vf))
+    L.orc_V_backward(N, _pl(E), b, x, _pl(Vb))
+    Pr = np.zeros((N, N + 1), dtype=np.longdouble)
+    L.orc_connection_probabilities(N, _pl(E), _pl(Vf), _pl(Vb), b, x, _pl(Pr))
+    del E
+    F = np.zeros_like(rl)
+    L.orc_exchange_forces(N, P, d, _pl(rl), b, _pl(Pr), _pl(F))
+    spring = L.orc_spring_expectation(N, P, d, _pl(rl), b, _pl(Pr))
+    return F, {"V_xi": Vf[N], "V_xi_bwd": Vb[0], "spring": np.longdouble(spring)}

@@ -28,18 +28,28 @@
  *  - massive Nose-Hoover chains (Sec. IV A cites them; parameters are not
  *    given): chain length M, Q = kT/omega_P^2, one MTK Trotter half step per side.
  */
-#include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#include <tgmath.h>
+
+/* Floating-point type of every quantity.  The oracle is built as written in
+ * FP64; the same source built with -DORC_REAL="long double" (type-generic
+ * math from <tgmath.h>, nothing else changed) gives an extended-precision
+ * twin, used only to measure how far FP64 evaluations -- this oracle's and
+ * the GPU's -- sit from the exact result of the same formulas. */
+#ifndef ORC_REAL
+#define ORC_REAL double
+#endif
+typedef ORC_REAL real;
 
 #define R(r, l, j, c) (r)[(((size_t)(l)) * P + (j)) * d + (c)]
 
 /* |r_a^ja - r_b^jb|^2 */
-static double dist2(const double* r, int P, int d, int la, int ja, int lb, int jb)
+static real dist2(const real* r, int P, int d, int la, int ja, int lb, int jb)
 {
-    double s = 0.0;
+    real s = 0.0;
     for (int c = 0; c < d; ++c) {
-        double x = R(r, la, ja, c) - R(r, lb, jb, c);
+        real x = R(r, la, ja, c) - R(r, lb, jb, c);
         s += x * x;
     }
     return s;
@@ -47,12 +57,12 @@ static double dist2(const double* r, int P, int d, int la, int ja, int lb, int j
 
 /* Neumaier-compensated sum of exp(t[i] - m): the plain log-sum-exp of the
  * recursions, made exact to rounding for long sums. */
-static double sum_exp_shifted(const double* t, int n, double m)
+static real sum_exp_shifted(const real* t, int n, real m)
 {
-    double s = 0.0, comp = 0.0;
+    real s = 0.0, comp = 0.0;
     for (int i = 0; i < n; ++i) {
-        double x = exp(t[i] - m);
-        double tt = s + x;
+        real x = exp(t[i] - m);
+        real tt = s + x;
         if (fabs(s) >= fabs(x)) comp += (s - tt) + x;
         else comp += (x - tt) + s;
         s = tt;
@@ -60,9 +70,9 @@ static double sum_exp_shifted(const double* t, int n, double m)
     return s + comp;
 }
 
-static double log_sum_exp(const double* t, int n)
+static real log_sum_exp(const real* t, int n)
 {
-    double m = -INFINITY;
+    real m = -INFINITY;
     for (int i = 0; i < n; ++i)
         if (t[i] > m) m = t[i];
     if (m == -INFINITY) return -INFINITY;
@@ -70,7 +80,7 @@ static double log_sum_exp(const double* t, int n)
 }
 
 /* ln(xi^n) with the convention 0^0 = 1 (Sec. II). */
-static double log_xi_pow(double xi, int n)
+static real log_xi_pow(real xi, int n)
 {
     if (n == 0) return 0.0;
     if (xi == 0.0) return -INFINITY;
@@ -81,10 +91,10 @@ static double log_xi_pow(double xi, int n)
 /* Cycle energies (Sec. III).                                                */
 
 /* E_int^(v) = 1/2 m omega_P^2 sum_{j=1}^{P-1} (r_v^{j+1} - r_v^j)^2 */
-double orc_E_int(int P, int d, const double* r, double beta, int v /* 1-based */)
+real orc_E_int(int P, int d, const real* r, real beta, int v /* 1-based */)
 {
-    const double k = P / (beta * beta);
-    double s = 0.0;
+    const real k = P / (beta * beta);
+    real s = 0.0;
     for (int j = 0; j < P - 1; ++j) s += dist2(r, P, d, v - 1, j + 1, v - 1, j);
     return 0.5 * k * s;
 }
@@ -94,16 +104,16 @@ double orc_E_int(int P, int d, const double* r, double beta, int v /* 1-based */
  *   E^[u,v] = E^[u+1,v] - 1/2 k (r_v^P - r_{u+1}^1)^2 + 1/2 k (r_u^P - r_{u+1}^1)^2
  *             + 1/2 k (r_v^P - r_u^1)^2 + E_int^(u)
  * Output E[(u-1)*N + (v-1)]; entries with u > v are left untouched. */
-void orc_cycle_energies(int N, int P, int d, const double* r, double beta, double* E)
+void orc_cycle_energies(int N, int P, int d, const real* r, real beta, real* E)
 {
-    const double k = P / (beta * beta);
-    double* Eint = (double*)malloc(sizeof(double) * (size_t)N);
+    const real k = P / (beta * beta);
+    real* Eint = (real*)malloc(sizeof(real) * (size_t)N);
     for (int v = 1; v <= N; ++v) Eint[v - 1] = orc_E_int(P, d, r, beta, v);
     for (int v = 1; v <= N; ++v) {
         E[(size_t)(v - 1) * N + (v - 1)] =
             Eint[v - 1] + 0.5 * k * dist2(r, P, d, v - 1, P - 1, v - 1, 0);
         for (int u = v - 1; u >= 1; --u) {
-            double prev = E[(size_t)u * N + (v - 1)]; /* E^[u+1,v] */
+            real prev = E[(size_t)u * N + (v - 1)]; /* E^[u+1,v] */
             E[(size_t)(u - 1) * N + (v - 1)] =
                 prev - 0.5 * k * dist2(r, P, d, v - 1, P - 1, u, 0)
                 + 0.5 * k * dist2(r, P, d, u - 1, P - 1, u, 0)
@@ -119,16 +129,16 @@ void orc_cycle_energies(int N, int P, int d, const double* r, double beta, doubl
 /* Forward recursion, written for every l (the printed one is l = N):
  *   e^{-beta V^[1,l]} = (1/l) sum_{k=1}^{l} xi^{k-1} e^{-beta (E^[l-k+1,l] + V^[1,l-k])}
  * with V^[1,0] = 0.  Output Vf[l] = V^[1,l] for l = 0..N. */
-void orc_V_forward(int N, const double* E, double beta, double xi, double* Vf)
+void orc_V_forward(int N, const real* E, real beta, real xi, real* Vf)
 {
-    double* t = (double*)malloc(sizeof(double) * (size_t)(N + 1));
+    real* t = (real*)malloc(sizeof(real) * (size_t)(N + 1));
     Vf[0] = 0.0;
     for (int l = 1; l <= N; ++l) {
         for (int k = 1; k <= l; ++k) {
-            double Ec = E[(size_t)(l - k) * N + (l - 1)]; /* E^[l-k+1,l] */
+            real Ec = E[(size_t)(l - k) * N + (l - 1)]; /* E^[l-k+1,l] */
             t[k - 1] = log_xi_pow(xi, k - 1) - beta * (Ec + Vf[l - k]);
         }
-        Vf[l] = -(log_sum_exp(t, l) - log((double)l)) / beta;
+        Vf[l] = -(log_sum_exp(t, l) - log((real)l)) / beta;
     }
     free(t);
 }
@@ -136,15 +146,15 @@ void orc_V_forward(int N, const double* E, double beta, double xi, double* Vf)
 /* Backward recursion:
  *   e^{-beta V^[u,N]} = sum_{l=u}^{N} xi^{l-u} (1/l) e^{-beta (E^[u,l] + V^[l+1,N])}
  * with V^[N+1,N] = 0.  Output Vb[u-1] = V^[u,N] for u = 1..N+1. */
-void orc_V_backward(int N, const double* E, double beta, double xi, double* Vb)
+void orc_V_backward(int N, const real* E, real beta, real xi, real* Vb)
 {
-    double* t = (double*)malloc(sizeof(double) * (size_t)(N + 1));
+    real* t = (real*)malloc(sizeof(real) * (size_t)(N + 1));
     Vb[N] = 0.0;
     for (int u = N; u >= 1; --u) {
         int n = 0;
         for (int l = u; l <= N; ++l) {
-            double Ec = E[(size_t)(u - 1) * N + (l - 1)]; /* E^[u,l] */
-            t[n++] = log_xi_pow(xi, l - u) - log((double)l) - beta * (Ec + Vb[l]);
+            real Ec = E[(size_t)(u - 1) * N + (l - 1)]; /* E^[u,l] */
+            t[n++] = log_xi_pow(xi, l - u) - log((real)l) - beta * (Ec + Vb[l]);
         }
         Vb[u - 1] = -log_sum_exp(t, n) / beta;
     }
@@ -156,16 +166,16 @@ void orc_V_backward(int N, const double* E, double beta, double xi, double* Vb)
  *   l' = l+1: Pr[G(l)=l+1] = 1 - e^{-beta (V^[1,l] + V^[l+1,N])} / e^{-beta V^[1,N]}
  *   otherwise 0.
  * Output Pr[(l-1)*(N+1) + (l'-1)] for l = 1..N, l' = 1..N+1. */
-void orc_connection_probabilities(int N, const double* E, const double* Vf, const double* Vb,
-                                  double beta, double xi, double* Pr)
+void orc_connection_probabilities(int N, const real* E, const real* Vf, const real* Vb,
+                                  real beta, real xi, real* Pr)
 {
-    const double VN = Vf[N];
+    const real VN = Vf[N];
     for (int l = 1; l <= N; ++l) {
-        double* row = Pr + (size_t)(l - 1) * (N + 1);
+        real* row = Pr + (size_t)(l - 1) * (N + 1);
         for (int lp = 1; lp <= N + 1; ++lp) row[lp - 1] = 0.0;
         for (int lp = 1; lp <= l; ++lp) {
-            double Ec = E[(size_t)(lp - 1) * N + (l - 1)]; /* E^[l',l] */
-            double lw = log_xi_pow(xi, l - lp) - log((double)l)
+            real Ec = E[(size_t)(lp - 1) * N + (l - 1)]; /* E^[l',l] */
+            real lw = log_xi_pow(xi, l - lp) - log((real)l)
                         - beta * (Vf[lp - 1] + Ec + Vb[l]) + beta * VN;
             row[lp - 1] = exp(lw);
         }
@@ -179,19 +189,19 @@ void orc_connection_probabilities(int N, const double* E, const double* Vf, cons
  *   interior:      -m w_P^2 (2 r_l^j - r_l^{j+1} - r_l^{j-1})
  * (l' runs over 1..N; Pr[G(N)=N+1] is zero).  Requires P >= 2.  For P = 2 the
  * two exterior formulas are the whole force. */
-void orc_exchange_forces(int N, int P, int d, const double* r, double beta,
-                         const double* Pr, double* F)
+void orc_exchange_forces(int N, int P, int d, const real* r, real beta,
+                         const real* Pr, real* F)
 {
-    const double k = P / (beta * beta);
+    const real k = P / (beta * beta);
     for (int l = 1; l <= N; ++l) {
         for (int c = 0; c < d; ++c) {
             for (int j = 2; j <= P - 1; ++j)
                 R(F, l - 1, j - 1, c) = -k * (2.0 * R(r, l - 1, j - 1, c) - R(r, l - 1, j, c)
                                               - R(r, l - 1, j - 2, c));
-            double f1 = 0.0, fP = 0.0;
+            real f1 = 0.0, fP = 0.0;
             for (int lp = 1; lp <= N; ++lp) {
-                double p_in = Pr[(size_t)(lp - 1) * (N + 1) + (l - 1)];  /* Pr[G(l')=l] */
-                double p_out = Pr[(size_t)(l - 1) * (N + 1) + (lp - 1)]; /* Pr[G(l)=l'] */
+                real p_in = Pr[(size_t)(lp - 1) * (N + 1) + (l - 1)];  /* Pr[G(l')=l] */
+                real p_out = Pr[(size_t)(l - 1) * (N + 1) + (lp - 1)]; /* Pr[G(l)=l'] */
                 f1 -= p_in * k * (2.0 * R(r, l - 1, 0, c) - R(r, l - 1, 1, c) - R(r, lp - 1, P - 1, c));
                 fP -= p_out * k * (2.0 * R(r, l - 1, P - 1, c) - R(r, l - 1, P - 2, c) - R(r, lp - 1, 0, c));
             }
@@ -205,14 +215,14 @@ void orc_exchange_forces(int N, int P, int d, const double* r, double beta,
  *   sum_l E_int^(l) + sum_{l,l'} Pr[G(l)=l'] 1/2 k (r_l^P - r_{l'}^1)^2
  * which equals -d(beta V_xi)/d(beta) at fixed beads (the primitive estimator's
  * exchange part). */
-double orc_spring_expectation(int N, int P, int d, const double* r, double beta, const double* Pr)
+real orc_spring_expectation(int N, int P, int d, const real* r, real beta, const real* Pr)
 {
-    const double k = P / (beta * beta);
-    double s = 0.0;
+    const real k = P / (beta * beta);
+    real s = 0.0;
     for (int l = 1; l <= N; ++l) s += orc_E_int(P, d, r, beta, l);
     for (int l = 1; l <= N; ++l)
         for (int lp = 1; lp <= N; ++lp) {
-            double p = Pr[(size_t)(l - 1) * (N + 1) + (lp - 1)];
+            real p = Pr[(size_t)(l - 1) * (N + 1) + (lp - 1)];
             if (p != 0.0) s += p * 0.5 * k * dist2(r, P, d, l - 1, P - 1, lp - 1, 0);
         }
     return s;
@@ -224,22 +234,22 @@ double orc_spring_expectation(int N, int P, int d, const double* r, double beta,
 /* V(slice j) = sum_l 1/2 omega^2 |r_l^j|^2 + 1/2 sum_{i != k} A exp(-|r_i^j - r_k^j|^2 / s^2)
  * Writes U = sum_j V(slice j), F = -grad (U/P) (overwrites), and the virial
  * sum_{l,j} r_l^j . grad_{r_l^j} U. */
-void orc_interaction(int N, int P, int d, const double* r, double omega, double A, double s,
-                     double* U_out, double* F, double* virial_out)
+void orc_interaction(int N, int P, int d, const real* r, real omega, real A, real s,
+                     real* U_out, real* F, real* virial_out)
 {
-    double U = 0.0, vir = 0.0;
-    const double inv_s2 = 1.0 / (s * s);
+    real U = 0.0, vir = 0.0;
+    const real inv_s2 = 1.0 / (s * s);
     for (int j = 0; j < P; ++j) {
         for (int i = 0; i < N; ++i) {
-            double g[3] = {0.0, 0.0, 0.0};
-            double r2 = 0.0;
+            real g[3] = {0.0, 0.0, 0.0};
+            real r2 = 0.0;
             for (int c = 0; c < d; ++c) r2 += R(r, i, j, c) * R(r, i, j, c);
             U += 0.5 * omega * omega * r2;
             for (int c = 0; c < d; ++c) g[c] += omega * omega * R(r, i, j, c);
             for (int kk = 0; kk < N; ++kk) {
                 if (kk == i || A == 0.0) continue;
-                double q2 = dist2(r, P, d, i, j, kk, j);
-                double e = A * exp(-q2 * inv_s2);
+                real q2 = dist2(r, P, d, i, j, kk, j);
+                real e = A * exp(-q2 * inv_s2);
                 U += 0.5 * e;
                 for (int c = 0; c < d; ++c)
                     g[c] += -2.0 * inv_s2 * e * (R(r, i, j, c) - R(r, kk, j, c));
@@ -258,24 +268,24 @@ void orc_interaction(int N, int P, int d, const double* r, double omega, double 
 /* Whole force field for one configuration.                                   */
 
 typedef struct {
-    double V_xi;      /* V_xi^[1,N] (forward value)                    */
-    double V_xi_bwd;  /* V_xi^[1,N] from the backward recursion         */
-    double U_over_P;  /* U/P (trap + pairs)                             */
-    double spring;    /* expected connected spring energy               */
-    double virial;    /* sum r . grad U                                 */
+    real V_xi;      /* V_xi^[1,N] (forward value)                    */
+    real V_xi_bwd;  /* V_xi^[1,N] from the backward recursion         */
+    real U_over_P;  /* U/P (trap + pairs)                             */
+    real spring;    /* expected connected spring energy               */
+    real virial;    /* sum r . grad U                                 */
 } orc_force_info;
 
 /* F = -grad(V_xi + U/P).  Returns 0 on success, -1 on bad input / no memory.
  * Pr_out (N*(N+1)) may be NULL. */
-int orc_forces(int N, int P, int d, const double* r, double beta, double xi, double omega,
-               double A, double s, double* F, orc_force_info* info, double* Pr_out)
+int orc_forces(int N, int P, int d, const real* r, real beta, real xi, real omega,
+               real A, real s, real* F, orc_force_info* info, real* Pr_out)
 {
     if (N < 1 || P < 2 || d < 1 || d > 3 || !(beta > 0.0) || xi < 0.0 || xi > 1.0) return -1;
-    double* E = (double*)calloc((size_t)N * N, sizeof(double));
-    double* Vf = (double*)malloc(sizeof(double) * (size_t)(N + 1));
-    double* Vb = (double*)malloc(sizeof(double) * (size_t)(N + 1));
-    double* Pr = Pr_out ? Pr_out : (double*)malloc(sizeof(double) * (size_t)N * (N + 1));
-    double* Fi = (double*)malloc(sizeof(double) * (size_t)N * P * d);
+    real* E = (real*)calloc((size_t)N * N, sizeof(real));
+    real* Vf = (real*)malloc(sizeof(real) * (size_t)(N + 1));
+    real* Vb = (real*)malloc(sizeof(real) * (size_t)(N + 1));
+    real* Pr = Pr_out ? Pr_out : (real*)malloc(sizeof(real) * (size_t)N * (N + 1));
+    real* Fi = (real*)malloc(sizeof(real) * (size_t)N * P * d);
     if (!E || !Vf || !Vb || !Pr || !Fi) {
         free(E); free(Vf); free(Vb); if (!Pr_out) free(Pr); free(Fi);
         return -1;
@@ -285,7 +295,7 @@ int orc_forces(int N, int P, int d, const double* r, double beta, double xi, dou
     orc_V_backward(N, E, beta, xi, Vb);
     orc_connection_probabilities(N, E, Vf, Vb, beta, xi, Pr);
     orc_exchange_forces(N, P, d, r, beta, Pr, F);
-    double U, vir;
+    real U, vir;
     orc_interaction(N, P, d, r, omega, A, s, &U, Fi, &vir);
     for (size_t i = 0; i < (size_t)N * P * d; ++i) F[i] += Fi[i];
     if (info) {
@@ -304,32 +314,32 @@ int orc_forces(int N, int P, int d, const double* r, double beta, double xi, dou
 /* (Sec. IV A cites Nose, Hoover, Martyna-Klein-Tuckerman, Jang-Voth).        */
 
 typedef struct {
-    double E_prim;     /* PdN/(2 beta) - spring + U/P                          */
-    double E_vir;      /* U/P + virial/(2P)                                    */
-    double V_xi;
-    double U_over_P;
-    double kinetic;    /* sum p^2 / (2 m')                                      */
-    double spring;
-    double H_conserved;/* kinetic + V_xi + U/P + sum (p_eta^2/(2Q) + kT eta)      */
-    double virial;
+    real E_prim;     /* PdN/(2 beta) - spring + U/P                          */
+    real E_vir;      /* U/P + virial/(2P)                                    */
+    real V_xi;
+    real U_over_P;
+    real kinetic;    /* sum p^2 / (2 m')                                      */
+    real spring;
+    real H_conserved;/* kinetic + V_xi + U/P + sum (p_eta^2/(2Q) + kT eta)      */
+    real virial;
 } orc_estimates;
 
 /* One MTK half step of length tau for a single degree of freedom with a chain
  * of M thermostats (positions eta[0..M-1], momenta pe[0..M-1], equal masses Q). */
-static void nhc_half(double* p, double m, double* eta, double* pe, int M, double Q, double kT, double tau)
+static void nhc_half(real* p, real m, real* eta, real* pe, int M, real Q, real kT, real tau)
 {
-    double G;
+    real G;
     G = (M >= 2 ? pe[M - 2] * pe[M - 2] / Q : (*p) * (*p) / m) - kT;
     pe[M - 1] += 0.5 * tau * G;
     for (int k = M - 2; k >= 0; --k) {
-        double a = exp(-0.25 * tau * pe[k + 1] / Q);
+        real a = exp(-0.25 * tau * pe[k + 1] / Q);
         G = (k == 0 ? (*p) * (*p) / m : pe[k - 1] * pe[k - 1] / Q) - kT;
         pe[k] = pe[k] * a * a + 0.5 * tau * G * a;
     }
     *p *= exp(-tau * pe[0] / Q);
     for (int k = 0; k < M; ++k) eta[k] += tau * pe[k] / Q;
     for (int k = 0; k <= M - 2; ++k) {
-        double a = exp(-0.25 * tau * pe[k + 1] / Q);
+        real a = exp(-0.25 * tau * pe[k + 1] / Q);
         G = (k == 0 ? (*p) * (*p) / m : pe[k - 1] * pe[k - 1] / Q) - kT;
         pe[k] = pe[k] * a * a + 0.5 * tau * G * a;
     }
@@ -337,12 +347,12 @@ static void nhc_half(double* p, double m, double* eta, double* pe, int M, double
     pe[M - 1] += 0.5 * tau * G;
 }
 
-static void fill_estimates(int N, int P, int d, double beta, int M, double Q, double mass,
-                           const double* p, const double* eta, const double* pe,
+static void fill_estimates(int N, int P, int d, real beta, int M, real Q, real mass,
+                           const real* p, const real* eta, const real* pe,
                            const orc_force_info* fi, int thermostat, orc_estimates* est)
 {
     const size_t ndof = (size_t)N * P * d;
-    double K = 0.0, th = 0.0;
+    real K = 0.0, th = 0.0;
     for (size_t i = 0; i < ndof; ++i) K += 0.5 * p[i] * p[i] / mass;
     if (thermostat)
         for (size_t i = 0; i < ndof * M; ++i) th += 0.5 * pe[i] * pe[i] / Q + eta[i] / beta;
@@ -362,13 +372,13 @@ static void fill_estimates(int N, int P, int d, double beta, int M, double Q, do
  *   NHC(dt/2); p += F dt/2; r += p dt/m'; F = F(r); p += F dt/2; NHC(dt/2).
  * thermostat = 0 runs plain NVE velocity Verlet.  est (nsteps entries, may be
  * NULL) gets the estimators after each step. */
-int orc_md_run(int N, int P, int d, double beta, double xi, double omega, double A, double s,
-               double dt, int M, double Q, double mass, int thermostat,
-               double* r, double* p, double* eta, double* peta, double* F, int* have_forces,
+int orc_md_run(int N, int P, int d, real beta, real xi, real omega, real A, real s,
+               real dt, int M, real Q, real mass, int thermostat,
+               real* r, real* p, real* eta, real* peta, real* F, int* have_forces,
                int nsteps, orc_estimates* est)
 {
     const size_t ndof = (size_t)N * P * d;
-    const double kT = 1.0 / beta;
+    const real kT = 1.0 / beta;
     orc_force_info fi;
     if (M < 1) return -1;
     if (!*have_forces) {
@@ -392,12 +402,12 @@ int orc_md_run(int N, int P, int d, double beta, double xi, double omega, double
 }
 
 /* Estimators of the current state without stepping (forces recomputed). */
-int orc_estimators(int N, int P, int d, double beta, double xi, double omega, double A, double s,
-                   int M, double Q, double mass, int thermostat, const double* r, const double* p,
-                   const double* eta, const double* peta, orc_estimates* est)
+int orc_estimators(int N, int P, int d, real beta, real xi, real omega, real A, real s,
+                   int M, real Q, real mass, int thermostat, const real* r, const real* p,
+                   const real* eta, const real* peta, orc_estimates* est)
 {
     orc_force_info fi;
-    double* F = (double*)malloc(sizeof(double) * (size_t)N * P * d);
+    real* F = (real*)malloc(sizeof(real) * (size_t)N * P * d);
     if (!F) return -1;
     int rc = orc_forces(N, P, d, r, beta, xi, omega, A, s, F, &fi, NULL);
     free(F);

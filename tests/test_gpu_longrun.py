@@ -63,3 +63,37 @@ def test_long_run_energy_matches_exact(xi):
         assert se < 0.03 * E_exact, (se, E_exact)
         assert abs(mean - E_exact) < 4 * se, (mean, se, E_exact)
         print(f"xi={xi}: mean {mean:.4f} +- {se:.4f}, exact {E_exact:.4f}")
+
+
+def test_batch_fp32_thermostat_long_run_matches_exact():
+    """The batched workload's FP32 thermostat (nhc_fp32, mixed precision) over
+    long runs of ideal trapped particles (g = 0) at the batched workload's
+    temperatures and exchange parameters: each replica's block-averaged E_prim
+    and E_vir agree with the exact finite-P energy for its (beta, xi) within 4
+    standard errors."""
+    import paper_2404_02628_gb300 as pkg
+    N, P, d = 16, 32, 2
+    reps = [(1.0, 0.0), (2.0, 1.0), (3.0, 0.4), (4.0, 0.8), (2.0, 0.6), (3.0, 1.0)]
+    rs = [beads(N, P, d, 2100 + q) for q in range(len(reps))]
+    ps = [momenta(N, P, d, b, 2100 + q) for q, (b, _) in enumerate(reps)]
+    B = pkg.Batch([N] * len(reps), P, d, [b for b, _ in reps], [x for _, x in reps], 1.0, 0.0, 0.5, rs=rs, ps=ps,
+                  precision=pkg.PREC_MIXED, nhc_len=4, dt=0.01, nhc_fp32=1)
+    B.step(10000)
+    n_samples, stride = 20000, 10
+    Ep = np.empty((n_samples, len(reps)))
+    Ev = np.empty((n_samples, len(reps)))
+    for i in range(n_samples):
+        B.step(stride)
+        est = B.estimators()
+        Ep[i] = [e["E_prim"] for e in est]
+        Ev[i] = [e["E_vir"] for e in est]
+    B.close()
+    for q, (beta, xi) in enumerate(reps):
+        E_exact = exact.energy(N, beta, P=P, d=d, xi=xi)
+        for series in (Ev[:, q], Ep[:, q]):
+            blocks = series.reshape(20, -1).mean(axis=1)
+            mean = blocks.mean()
+            se = blocks.std(ddof=1) / np.sqrt(len(blocks))
+            print(f"beta={beta} xi={xi}: mean {mean:.4f} +- {se:.4f}, exact {E_exact:.4f}")
+            assert se < 0.05 * E_exact, (q, se, E_exact)
+            assert abs(mean - E_exact) < 4 * se, (q, mean, se, E_exact)
