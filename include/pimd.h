@@ -229,6 +229,17 @@ pimd_status pimd_autotune(pimd_t ctx, const char* cache_path);
  * pairs run as kernels of their own).  helpers and force_blocks may be NULL. */
 pimd_status pimd_tuning(pimd_t ctx, int* exch_band, int* pair_block, int* helpers, int* force_blocks);
 
+/* Debug cross-check (Sec. III, the O(N^3 P) evaluation the paper replaces
+ * by its quadratic algorithm): every cycle energy E^[u,v], 1 <= u <= v <= N,
+ * of the bound positions straight from its definition -- the springs of the
+ * ring made of particles u..v, bead j to j+1 inside each particle, bead P of
+ * w to bead 1 of w+1, bead P of v to bead 1 of u, times 1/2 m omega_P^2 =
+ * P/(2 beta^2) -- one GPU thread per entry, FP64.  Writes E^[u,v] to
+ * E_out[(u-1)*ldE + (v-1)] (device, caller-owned, at least N*ldE doubles);
+ * entries with u > v are not written.  ldE >= N, N <= 65535.  Not used by the
+ * MD step, whose recursion never forms E.  Stream-ordered, asynchronous. */
+pimd_status pimd_cycle_energies_naive(pimd_t ctx, double* E_out, int ldE);
+
 /* Synchronises the bound stream and reports device-side errors. */
 pimd_status pimd_sync(pimd_t ctx);
 
@@ -352,6 +363,25 @@ void pimd_vb_destroy(pimd_vb_t h);
  * *V_out, so the failure shows in the result itself. */
 pimd_status pimd_vb_forward_noalloc(int N, int P, int d, double beta, double xi, const double* r1,
                                     const double* rP, int ld, double* V_out, void* stream);
+
+/* ---- xi extrapolation (host only) ------------------------------------------ */
+/*
+ * Fictitious-particle thermodynamics (Sec. I and Sec. IV D): an observable is
+ * simulated at xi in [0, 1], where exp(-beta (V_xi + U/P)) is a probability
+ * density, and carried to the fermionic value xi = -1 by a fit in xi.  The
+ * paper does not print the fitting form; this call fits a polynomial of the
+ * given degree (2: the quadratic form of the xi-extrapolation literature the
+ * paper cites) by weighted least squares, weights 1/sigma_i^2, and evaluates it
+ * at xi_target.
+ *   n points (xi[i], E[i], sigma[i] > 0), n >= degree + 1, 0 <= degree <= 6;
+ *   *value: the fitted polynomial at xi_target; *value_sigma (nullable): its
+ *   standard error from the parameters' covariance; *chi2 (nullable): the
+ *   weighted residual sum of squares; coef (nullable, degree + 1 entries):
+ *   coefficients in powers of xi, constant term first.
+ * PIMD_EINVAL on bad input or when the points do not determine the
+ * polynomial (fewer distinct xi than degree + 1).  Host only; no GPU work. */
+pimd_status pimd_xi_extrapolate(int n, const double* xi, const double* E, const double* sigma, int degree,
+                                double xi_target, double* value, double* value_sigma, double* chi2, double* coef);
 
 #ifdef __cplusplus
 }

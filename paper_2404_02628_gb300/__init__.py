@@ -26,7 +26,7 @@ __all__ = [
     "pimd_batch_step_eager", "pimd_batch_step_profiled", "pimd_batch_profile_slot_name",
     "pimd_batch_estimators", "pimd_batch_sync", "pimd_batch_last_error", "pimd_batch_destroy",
     "pimd_batch_autotune", "pimd_autotune", "pimd_tuning", "pimd_init_state", "pimd_batch_init_state",
-    "pimd_density_accumulate", "pimd_batch_tuning",
+    "pimd_density_accumulate", "pimd_batch_tuning", "pimd_cycle_energies_naive", "pimd_xi_extrapolate",
 ]
 
 PIMD_OK, PIMD_EINVAL, PIMD_ENOMEM, PIMD_ECUDA, PIMD_ETIMEOUT, PIMD_ENONFINITE, PIMD_ESTATE = range(7)
@@ -133,6 +133,9 @@ _SIGS = {
     "pimd_batch_init_state": ([_vp, ctypes.c_ulonglong], ctypes.c_int),
     "pimd_tuning": ([_vp] + [ctypes.POINTER(ctypes.c_int)] * 4, ctypes.c_int),
     "pimd_batch_autotune": ([_vp, ctypes.c_char_p], ctypes.c_int),
+    "pimd_cycle_energies_naive": ([_vp, _vp, ctypes.c_int], ctypes.c_int),
+    "pimd_xi_extrapolate": ([ctypes.c_int, _dp, _dp, _dp, ctypes.c_int, ctypes.c_double, _dp, _dp, _dp, _dp],
+                            ctypes.c_int),
 }
 
 
@@ -413,6 +416,25 @@ def pimd_batch_init_state(h, seed):
     return _bcheck(lib().pimd_batch_init_state(h, int(seed) & 0xFFFFFFFFFFFFFFFF), h)
 
 
+def pimd_cycle_energies_naive(h, E_ptr, ldE):
+    return _check(lib().pimd_cycle_energies_naive(h, E_ptr, int(ldE)), h)
+
+
+def pimd_xi_extrapolate(xi, E, sigma, degree=2, xi_target=-1.0):
+    """Weighted least-squares polynomial in xi evaluated at xi_target (host
+    call): returns (value, value_sigma, chi2, coef[constant first])."""
+    n = len(xi)
+    arr = ctypes.c_double * n
+    v, vs, c2 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    coef = (ctypes.c_double * (degree + 1))()
+    st = lib().pimd_xi_extrapolate(n, arr(*map(float, xi)), arr(*map(float, E)), arr(*map(float, sigma)),
+                                   int(degree), float(xi_target), ctypes.byref(v), ctypes.byref(vs),
+                                   ctypes.byref(c2), coef)
+    if st != PIMD_OK:
+        raise PimdError(st, "pimd_xi_extrapolate: bad input or too few distinct xi for the degree")
+    return v.value, vs.value, c2.value, list(coef)
+
+
 def pimd_autotune(h, cache_path=None):
     return _check(lib().pimd_autotune(h, cache_path.encode() if cache_path else None), h)
 
@@ -593,6 +615,13 @@ class System:
             hist = self.torch.zeros(nbins, dtype=self.torch.float64, device=self.r.device)
         pimd_density_accumulate(self.h, nbins, r_max, hist.data_ptr())
         return hist
+
+    def cycle_energies_naive(self):
+        """E[u-1, v-1] = E^[u,v] for u <= v from the definition, one GPU thread
+        per entry (pimd_cycle_energies_naive); zeros below the diagonal."""
+        E = self.torch.zeros((self.N, self.N), dtype=self.torch.float64, device=self.r.device)
+        pimd_cycle_energies_naive(self.h, E.data_ptr(), self.N)
+        return E.cpu().numpy()
 
     def init_state(self, seed):
         """Seeded beads and momenta on the device (pimd_init_state)."""

@@ -1096,6 +1096,19 @@ extern "C" pimd_status pimd_init_state(pimd_t c, unsigned long long seed)
     return enqueue_forces(c, c->st, c->buf.f, true, true);
 }
 
+cudaError_t launch_cycle_naive(const BeadView& b, double ks, double* E, int ldE, cudaStream_t st);
+
+extern "C" pimd_status pimd_cycle_energies_naive(pimd_t c, double* E_out, int ldE)
+{
+    if (!c || !E_out) return fail(c, PIMD_EINVAL, "pimd_cycle_energies_naive: NULL argument");
+    if (!c->bound) return fail(c, PIMD_ESTATE, "pimd_cycle_energies_naive: not bound");
+    if (ldE < c->N) return fail(c, PIMD_EINVAL, "pimd_cycle_energies_naive: ldE < N");
+    if (c->N > 65535) return fail(c, PIMD_EINVAL, "pimd_cycle_energies_naive: N > 65535");
+    cudaError_t e = launch_cycle_naive(c->bv, c->P / (c->beta * c->beta), E_out, ldE, c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pimd_cycle_energies_naive");
+    return PIMD_OK;
+}
+
 extern "C" pimd_status pimd_sync(pimd_t c)
 {
     if (!c) return fail(c, PIMD_EINVAL, "pimd_sync: NULL handle");
