@@ -109,7 +109,7 @@ typedef struct {
 typedef struct {
     double E_prim;      /* P d N/(2 beta) - spring + U/P                                 */
     double E_vir;       /* U/P + (1/2P) sum_{l,j} r_l^j . grad U                          */
-    double V_xi;        /* V_xi^[1,N] from the forward recursion                          */
+    double V_xi;        /* V_xi^[1,N] from the forward recursion (summed over species)    */
     double U_over_P;    /* (trap + pair energy summed over slices) / P                   */
     double kinetic;     /* sum p^2 / (2 m')                                               */
     double spring;      /* expected connected spring energy sum E_int + sum Pr 1/2 k |dr|^2 */
@@ -127,6 +127,21 @@ typedef struct {
  * handle.  PIMD_EINVAL on a bad argument.  Host only; no GPU work. */
 pimd_status pimd_create(int N, int P, int d, double beta, double omega, double g, double s,
                         double xi, pimd_t* out);
+
+/* Several particle species (Sec. II, closing paragraph: the spin-polarised
+ * case generalises to coexisting spins, e.g. spin-unpolarised fermions or
+ * bosons).  Particles of one species are identical among themselves and
+ * distinguishable from the others, so each species gets an exchange
+ * potential V_xi of its own over its particles (Sec. III recursions, same
+ * beta, P and xi), V_exchange = sum over species; the trap and the Gaussian
+ * pair interaction act between all particles alike.  Species s holds the
+ * counts[s] consecutive particles after those of species 0..s-1 (so bead
+ * arrays keep their layout).  n_species in [1, 4], counts[s] >= 1, sum = N.
+ * Call before pimd_workspace_bytes and pimd_bind (PIMD_ESTATE after bind);
+ * the default is one species of N.  With several species the springs and
+ * pairs run as kernels of their own (not folded into the recursion launch)
+ * and the species' recursions run one after another.  Host only. */
+pimd_status pimd_set_species(pimd_t ctx, int n_species, const int* counts);
 
 /* Fills *cfg with the defaults listed in pimd_config. */
 void pimd_default_config(pimd_config* cfg);

@@ -207,6 +207,32 @@ def forces(r, beta, xi, omega=1.0, A=0.0, s=1.0, want_pr=False):
     return F, out
 
 
+def forces_species(r, counts, beta, xi, omega=1.0, A=0.0, s=1.0):
+    """Several species (Sec. II, closing paragraph): each species -- counts[k]
+    consecutive particles -- carries its own exchange potential from the
+    Sec. III recursions over its own particles; the trap and the pairs act
+    between all particles.  F = -grad(sum_k V_xi(species k) + U/P) and a dict
+    of scalars (V_xi and spring summed over species, per-species V_xi in
+    "V_species")."""
+    r = _conf(r)
+    N, P, d = r.shape
+    if sum(counts) != N or min(counts) < 1:
+        raise ValueError("species counts must be positive and add up to N")
+    F = np.zeros_like(r)
+    V, spring, Vs = 0.0, 0.0, []
+    off = 0
+    for n in counts:
+        Fk, ik = forces(r[off:off + n], beta, xi, 0.0, 0.0, s)  # exchange part only (no trap, no pairs)
+        F[off:off + n] += Fk
+        V += ik["V_xi"]
+        spring += ik["spring"]
+        Vs.append(ik["V_xi"])
+        off += n
+    U, Fi, vir = interaction(r, omega, A, s)
+    F += Fi
+    return F, {"V_xi": V, "spring": spring, "U_over_P": U / P, "virial": vir, "V_species": Vs}
+
+
 class MDState:
     """Oracle MD state: r, p of shape (N, P, d); eta, peta of shape (N, P, d, M)."""
 

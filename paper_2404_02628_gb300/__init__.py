@@ -27,6 +27,7 @@ __all__ = [
     "pimd_batch_estimators", "pimd_batch_sync", "pimd_batch_last_error", "pimd_batch_destroy",
     "pimd_batch_autotune", "pimd_autotune", "pimd_tuning", "pimd_init_state", "pimd_batch_init_state",
     "pimd_density_accumulate", "pimd_batch_tuning", "pimd_cycle_energies_naive", "pimd_xi_extrapolate",
+    "pimd_set_species",
 ]
 
 PIMD_OK, PIMD_EINVAL, PIMD_ENOMEM, PIMD_ECUDA, PIMD_ETIMEOUT, PIMD_ENONFINITE, PIMD_ESTATE = range(7)
@@ -134,6 +135,7 @@ _SIGS = {
     "pimd_tuning": ([_vp] + [ctypes.POINTER(ctypes.c_int)] * 4, ctypes.c_int),
     "pimd_batch_autotune": ([_vp, ctypes.c_char_p], ctypes.c_int),
     "pimd_cycle_energies_naive": ([_vp, _vp, ctypes.c_int], ctypes.c_int),
+    "pimd_set_species": ([_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "pimd_xi_extrapolate": ([ctypes.c_int, _dp, _dp, _dp, ctypes.c_int, ctypes.c_double, _dp, _dp, _dp, _dp],
                             ctypes.c_int),
 }
@@ -186,6 +188,11 @@ def pimd_create(N, P, d, beta, omega, g, s, xi):
     h = _vp()
     _check(lib().pimd_create(N, P, d, beta, omega, g, s, xi, ctypes.byref(h)))
     return h
+
+
+def pimd_set_species(h, counts):
+    n = len(counts)
+    return _check(lib().pimd_set_species(h, n, (ctypes.c_int * n)(*[int(x) for x in counts])), h)
 
 
 def pimd_default_config():
@@ -542,11 +549,13 @@ class System:
 
     ``r`` and ``p`` are given particle-major, shape (N, P, d) (host numpy or
     torch); the device copies live in slice-major (P, d, n_pad) float64
-    tensors.  All arithmetic happens in the C ABI's kernels.
+    tensors.  ``species``: particle counts of consecutive species, each with
+    its own exchange recursion (None: one species).  All arithmetic happens
+    in the C ABI's kernels.
     """
 
     def __init__(self, N, P, d, beta, omega=1.0, g=0.0, s=0.5, xi=1.0, r=None, p=None, device="cuda",
-                 stream=None, **cfg_kw):
+                 stream=None, species=None, **cfg_kw):
         import torch
 
         self.torch = torch
@@ -557,6 +566,8 @@ class System:
         for k, v in cfg_kw.items():
             setattr(cfg, k, v)
         pimd_configure(self.h, cfg)
+        if species is not None:  # particle counts per species, consecutive (pimd_set_species)
+            pimd_set_species(self.h, list(species))
         self.cfg = cfg
         self.n_pad = (N + 31) // 32 * 32
         dev = torch.device(device)

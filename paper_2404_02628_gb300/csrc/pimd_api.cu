@@ -220,8 +220,10 @@ struct pimd_ctx {
     bool graph_failed = false;
     long long steps = 0;
     Layout L;
-    ExchLayout ex;
-    XLayout xl;
+    int nsp = 1;                         // species with exchange recursions of their own (pimd_set_species)
+    int sp_n[PIMD_MAXSP] = {}, sp_off[PIMD_MAXSP] = {};  // particles and first particle of each species
+    ExchLayout exs[PIMD_MAXSP];
+    XLayout xls[PIMD_MAXSP];
     bool use_df = true;
     size_t off_spr, off_pair, off_fin, off_md, off_sc, off_flag;
     int n_help;
@@ -232,8 +234,8 @@ struct pimd_ctx {
         double sc[SC_COUNT];
     }* host_rep = nullptr;
     int fused_gx = 0;  // particle blocks per slice of the last folded force evaluation (0: not folded)
-    ExchView xv;
-    XView xd;
+    ExchView xvs[PIMD_MAXSP];  // per species; species 0 holds the error word and exp table all share
+    XView xds[PIMD_MAXSP];
     BeadView bv;
     ForceParams fp;
     MDParams mp;
@@ -315,7 +317,31 @@ extern "C" pimd_status pimd_create(int N, int P, int d, double beta, double omeg
     c->xi = xi;
     pimd_default_config(&c->cfg);
     c->A = g / (M_PI * s * s);
+    c->nsp = 1;
+    c->sp_n[0] = N;
+    c->sp_off[0] = 0;
     *out = c;
+    return PIMD_OK;
+}
+
+extern "C" pimd_status pimd_set_species(pimd_t c, int n_species, const int* counts)
+{
+    if (!c || !counts) return fail(c, PIMD_EINVAL, "pimd_set_species: NULL argument");
+    if (c->bound) return fail(c, PIMD_ESTATE, "pimd_set_species: context already bound");
+    if (n_species < 1 || n_species > PIMD_MAXSP) return fail(c, PIMD_EINVAL, "pimd_set_species: n_species must be in [1, 4]");
+    long long tot = 0;
+    for (int sp = 0; sp < n_species; ++sp) {
+        if (counts[sp] < 1) return fail(c, PIMD_EINVAL, "pimd_set_species: every species needs at least one particle");
+        tot += counts[sp];
+    }
+    if (tot != c->N) return fail(c, PIMD_EINVAL, "pimd_set_species: counts must add up to N");
+    c->nsp = n_species;
+    int off = 0;
+    for (int sp = 0; sp < n_species; ++sp) {
+        c->sp_n[sp] = counts[sp];
+        c->sp_off[sp] = off;
+        off += counts[sp];
+    }
     return PIMD_OK;
 }
 
@@ -346,11 +372,17 @@ static void ctx_layout(pimd_ctx* c)
 {
     c->L = Layout();
     c->use_df = c->cfg.exchange_arith == PIMD_XARITH_DF;
-    if (c->use_df) xdf_layout(c->L, c->xl, c->N, EX_STREAMS, cfg_band(c->cfg), c->cfg.table_mode == PIMD_TABLE_STORE);
-    else exch_layout(c->L, c->ex, c->N, EX_STREAMS, c->cfg.table_mode == PIMD_TABLE_STORE);
+    for (int sp = 0; sp < c->nsp; ++sp) {
+        if (c->use_df)
+            xdf_layout(c->L, c->xls[sp], c->sp_n[sp], EX_STREAMS, cfg_band(c->cfg), c->cfg.table_mode == PIMD_TABLE_STORE);
+        else
+            exch_layout(c->L, c->exs[sp], c->sp_n[sp], EX_STREAMS, c->cfg.table_mode == PIMD_TABLE_STORE);
+    }
     c->off_spr = c->L.add((size_t)springs_grid_x(c->N) * c->P * sizeof(double));
     c->off_pair = c->L.add((size_t)pair_grid_x(c->N, PAIR_T_MIN) * c->P * 2 * sizeof(double));
-    c->off_fin = c->L.add((size_t)std::max(exch_finalize_blocks(c->N), xdf_finalize_blocks(c->N)) * sizeof(double));
+    // finalize partials of every species, one after the other
+    c->off_fin = c->L.add((size_t)(std::max(exch_finalize_blocks(c->N), xdf_finalize_blocks(c->N)) + PIMD_MAXSP) *
+                          sizeof(double));
     c->off_md = c->L.add((size_t)md_blocks(c->N, c->P, c->d) * 2 * sizeof(double));
     c->off_sc = c->L.add(SC_COUNT * sizeof(double));
     c->off_flag = c->L.add(4 * sizeof(int));
@@ -365,19 +397,37 @@ extern "C" pimd_status pimd_workspace_bytes(pimd_t c, int n_pad, size_t* bytes)
     return PIMD_OK;
 }
 
-// Exchange views of the bound buffers under the current configuration.
+// Exchange views of the bound buffers under the current configuration: one
+// per species, over that species' particles (beads 1 and P offset by its
+// first particle).  Every species reports into species 0's error word and
+// reads species 0's exp table.
 static void ctx_views(pimd_ctx* c)
 {
     const pimd_buffers* b = &c->buf;
     const int np = b->n_pad;
-    if (c->use_df)
-        c->xd = xdf_view((char*)b->work, c->xl, c->N, c->P, c->d, c->beta, c->xi, EX_STREAMS, cfg_band(c->cfg),
-                         c->cfg.table_mode == PIMD_TABLE_STORE, b->r + (size_t)(c->P - 1) * c->d * np, b->r, np, np,
-                         c->cfg.spin_limit, c->n_help);
-    else
-        c->xv = exch_view((char*)b->work, c->ex, c->N, c->P, c->d, c->beta, c->xi, EX_STREAMS,
-                          c->cfg.table_mode == PIMD_TABLE_STORE, b->r + (size_t)(c->P - 1) * c->d * np, b->r, np,
-                          np, c->cfg.spin_limit, c->n_help);
+    for (int sp = 0; sp < c->nsp; ++sp) {
+        const double* rP = b->r + (size_t)(c->P - 1) * c->d * np + c->sp_off[sp];
+        const double* r1 = b->r + c->sp_off[sp];
+        if (c->use_df) {
+            c->xds[sp] = xdf_view((char*)b->work, c->xls[sp], c->sp_n[sp], c->P, c->d, c->beta, c->xi, EX_STREAMS,
+                                  cfg_band(c->cfg), c->cfg.table_mode == PIMD_TABLE_STORE, rP, r1, np, np,
+                                  c->cfg.spin_limit, c->n_help);
+            if (sp > 0) {
+                c->xds[sp].err = c->xds[0].err;
+                c->xds[sp].tab = c->xds[0].tab;
+            }
+        } else {
+            c->xvs[sp] = exch_view((char*)b->work, c->exs[sp], c->sp_n[sp], c->P, c->d, c->beta, c->xi, EX_STREAMS,
+                                   c->cfg.table_mode == PIMD_TABLE_STORE, rP, r1, np, np, c->cfg.spin_limit, c->n_help);
+            if (sp > 0) c->xvs[sp].err = c->xvs[0].err;
+        }
+    }
+}
+
+// Finalize blocks of one species.
+static int fin_blocks(const pimd_ctx* c, int n)
+{
+    return c->use_df ? xdf_finalize_blocks(n) : exch_finalize_blocks(n);
 }
 
 static pimd_status enqueue_forces(pimd_ctx* c, cudaStream_t st, double* f, bool exch, bool inter,
@@ -388,7 +438,7 @@ static pimd_status enqueue_forces(pimd_ctx* c, cudaStream_t st, double* f, bool 
     fp.accumulate = 0;
     char* base = (char*)c->buf.work;
     c->fused_gx = 0;
-    if (exch && inter && c->use_df && c->xi != 0.0 && c->n_force > 0) {
+    if (exch && inter && c->use_df && c->xi != 0.0 && c->n_force > 0 && c->nsp == 1) {
         // springs and trap + pairs run as force workers inside the recursion launch
         ForceWork fw;
         memset(&fw, 0, sizeof fw);
@@ -400,7 +450,7 @@ static pimd_status enqueue_forces(pimd_ctx* c, cudaStream_t st, double* f, bool 
         fw.gx = (c->N + XDF_THREADS - 1) / XDF_THREADS;
         fw.counter = (int*)(base + c->off_flag) + 1;
         e = cudaMemsetAsync(fw.counter, 0, sizeof(int), st);
-        if (e == cudaSuccess) e = xdf_launch_forward(c->xd, st, pm, &fw, c->n_force);
+        if (e == cudaSuccess) e = xdf_launch_forward(c->xds[0], st, pm, &fw, c->n_force);
         if (e != cudaSuccess) return cuda_fail(c, e, "exchange recursion with force workers");
         FinalizeOut o;
         memset(&o, 0, sizeof(o));
@@ -408,7 +458,7 @@ static pimd_status enqueue_forces(pimd_ctx* c, cudaStream_t st, double* f, bool 
         o.ldf = c->buf.n_pad;
         o.P = c->P;
         o.part = (double*)(base + c->off_fin);
-        e = xdf_launch_adjoint(c->xd, o, st, pm);
+        e = xdf_launch_adjoint(c->xds[0], o, st, pm);
         if (e != cudaSuccess) return cuda_fail(c, e, "exchange forces");
         c->fused_gx = fw.gx;
         return PIMD_OK;
@@ -431,22 +481,27 @@ static pimd_status enqueue_forces(pimd_ctx* c, cudaStream_t st, double* f, bool 
         if (e != cudaSuccess) return cuda_fail(c, e, "zero kernel");
     }
     if (exch) {
-        FinalizeOut o;
-        memset(&o, 0, sizeof(o));
-        o.f = f;
-        o.ldf = c->buf.n_pad;
-        o.P = c->P;
-        o.part = (double*)(base + c->off_fin);
-        if (c->use_df) {
-            e = xdf_launch_forward(c->xd, st, pm);
-            if (e != cudaSuccess) return cuda_fail(c, e, "exchange recursion");
-            e = xdf_launch_adjoint(c->xd, o, st, pm);
-        } else {
-            e = exch_launch_forward(c->xv, st, 1, pm);
-            if (e != cudaSuccess) return cuda_fail(c, e, "exchange recursion");
-            e = exch_launch_adjoint(c->xv, o, exch_finalize_blocks(c->N), st, pm);
+        // one exchange recursion per species, each over its own particles
+        int fin_off = 0;
+        for (int sp = 0; sp < c->nsp; ++sp) {
+            FinalizeOut o;
+            memset(&o, 0, sizeof(o));
+            o.f = f + c->sp_off[sp];
+            o.ldf = c->buf.n_pad;
+            o.P = c->P;
+            o.part = (double*)(base + c->off_fin) + fin_off;
+            if (c->use_df) {
+                e = xdf_launch_forward(c->xds[sp], st, pm);
+                if (e != cudaSuccess) return cuda_fail(c, e, "exchange recursion");
+                e = xdf_launch_adjoint(c->xds[sp], o, st, pm);
+            } else {
+                e = exch_launch_forward(c->xvs[sp], st, 1, pm);
+                if (e != cudaSuccess) return cuda_fail(c, e, "exchange recursion");
+                e = exch_launch_adjoint(c->xvs[sp], o, exch_finalize_blocks(c->sp_n[sp]), st, pm);
+            }
+            if (e != cudaSuccess) return cuda_fail(c, e, "exchange forces");
+            fin_off += fin_blocks(c, c->sp_n[sp]);
         }
-        if (e != cudaSuccess) return cuda_fail(c, e, "exchange forces");
     }
     return PIMD_OK;
 }
@@ -460,20 +515,24 @@ static pimd_status enqueue_scalars(pimd_ctx* c, cudaStream_t st)
     memset(&s, 0, sizeof(s));
     s.springs = (double*)(base + c->off_spr);
     s.n_springs = (c->fused_gx ? c->fused_gx : springs_grid_x(c->N)) * c->P;
-    s.lsum = c->use_df ? c->xd.lsum : c->xv.lsum;
-    s.n_lsum = c->use_df ? xdf_prep_blocks(c->xd.npad) : exch_prep_blocks(c->N);
-    s.n_fin = c->use_df ? xdf_finalize_blocks(c->N) : exch_finalize_blocks(c->N);
-    s.lam = c->use_df ? c->xd.lam : nullptr;
+    s.nsp = c->nsp;
+    s.n_fin = 0;
+    for (int sp = 0; sp < c->nsp; ++sp) {
+        s.lsum[sp] = c->use_df ? c->xds[sp].lsum : c->xvs[sp].lsum;
+        s.n_lsum[sp] = c->use_df ? xdf_prep_blocks(c->xds[sp].npad) : exch_prep_blocks(c->sp_n[sp]);
+        s.lam[sp] = c->use_df ? c->xds[sp].lam : nullptr;
+        s.y_m[sp] = c->xvs[sp].y_m;
+        s.y_e[sp] = c->xvs[sp].y_e;
+        s.c_m[sp] = c->xvs[sp].c_m;
+        s.c_e[sp] = c->xvs[sp].c_e;
+        s.N[sp] = c->sp_n[sp];
+        s.n_fin += fin_blocks(c, c->sp_n[sp]);
+    }
     s.pair = (double*)(base + c->off_pair);
     s.n_pair = (c->fused_gx ? c->fused_gx : pair_grid_x(c->N, c->pair_t)) * c->P;
     s.fin = (double*)(base + c->off_fin);
     s.md = (double*)(base + c->off_md);
     s.n_md = md_blocks(c->N, c->P, c->d);
-    s.y_m = c->xv.y_m;
-    s.y_e = c->xv.y_e;
-    s.c_m = c->xv.c_m;
-    s.c_e = c->xv.c_e;
-    s.N = c->N;
     s.xi_zero = (c->xi == 0.0);
     s.log_xi = (c->xi > 0.0) ? log(c->xi) : 0.0;
     s.out = (double*)(base + c->off_sc);
@@ -501,7 +560,7 @@ static pimd_status check_device_error(pimd_ctx* c)
     char* base = (char*)c->buf.work;
     cudaError_t e = cudaStreamSynchronize(c->st);
     if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
-    int* errp = c->use_df ? c->xd.err : c->xv.err;
+    int* errp = c->use_df ? c->xds[0].err : c->xvs[0].err;
     e = cudaMemcpy(&h[0], errp, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(c, e, "error word read");
     e = cudaMemcpy(&h[1], base + c->off_flag, sizeof(int), cudaMemcpyDeviceToHost);
@@ -540,7 +599,7 @@ extern "C" pimd_status pimd_bind(pimd_t c, const pimd_buffers* b, void* stream)
     }
     c->n_help = default_helpers(c->cfg);
     c->n_force = 0;
-    if (c->use_df && c->A != 0.0 && c->xi != 0.0) {
+    if (c->use_df && c->A != 0.0 && c->xi != 0.0 && c->nsp == 1) {
         // SMs the recursion's helpers do not need take the springs and pairs
         const int sms = device_sms(), nb = (c->N + 1 + 31) / 32;
         if (c->cfg.helper_ctas <= 0) c->n_help = std::max(4, std::min(sms - 2 - 8, nb));
@@ -581,10 +640,10 @@ extern "C" pimd_status pimd_bind(pimd_t c, const pimd_buffers* b, void* stream)
         if (e == cudaSuccess) e = cudaMemsetAsync(b->peta, 0, n * sizeof(double), c->st);
         if (e != cudaSuccess) return cuda_fail(c, e, "pimd_bind: thermostat reset");
     }
-    e = cudaMemsetAsync(c->use_df ? c->xd.err : c->xv.err, 0, 4 * sizeof(int), c->st);
+    e = cudaMemsetAsync(c->use_df ? c->xds[0].err : c->xvs[0].err, 0, 4 * sizeof(int), c->st);
     if (e != cudaSuccess) return cuda_fail(c, e, "pimd_bind: error word reset");
     if (c->use_df) {
-        e = xdf_upload_table((float2*)c->xd.tab, c->st);
+        e = xdf_upload_table((float2*)c->xds[0].tab, c->st);
         if (e != cudaSuccess) return cuda_fail(c, e, "pimd_bind: exp table upload");
     }
     e = cudaMemsetAsync((char*)b->work + c->off_flag, 0, 4 * sizeof(int), c->st);
@@ -833,18 +892,29 @@ static void drop_graph(pimd_ctx* c)
     c->graph_failed = false;
 }
 
+// Bytes of the double-float exchange regions of every species for band width W.
+static size_t xdf_footprint(const pimd_ctx* c, int W)
+{
+    Layout L;
+    for (int sp = 0; sp < c->nsp; ++sp) {
+        XLayout xl;
+        xdf_layout(L, xl, c->sp_n[sp], EX_STREAMS, W, c->cfg.table_mode == PIMD_TABLE_STORE);
+    }
+    return L.total;
+}
+
 extern "C" pimd_status pimd_autotune(pimd_t c, const char* cache_path)
 {
     if (!c) return fail(c, PIMD_EINVAL, "pimd_autotune: NULL handle");
     if (!c->bound) return fail(c, PIMD_ESTATE, "pimd_autotune: not bound");
     char kb[256];
-    snprintf(kb, sizeof kb, "single N=%d P=%d d=%d prec=%d arith=%d table=%d xi0=%d g0=%d", c->N, c->P, c->d,
-             c->cfg.precision, c->cfg.exchange_arith, c->cfg.table_mode, c->xi == 0.0, c->A == 0.0);
+    snprintf(kb, sizeof kb, "single N=%d P=%d d=%d prec=%d arith=%d table=%d xi0=%d g0=%d sp=%d", c->N, c->P, c->d,
+             c->cfg.precision, c->cfg.exchange_arith, c->cfg.table_mode, c->xi == 0.0, c->A == 0.0, c->nsp);
     const std::string key = device_key() + " " + kb;
     std::string val;
     int bestW = cfg_band(c->cfg), bestT = c->pair_t, bestH = c->n_help, bestF = c->n_force;
     const int sms = device_sms();
-    const bool can_fold = c->use_df && c->A != 0.0 && c->xi != 0.0;
+    const bool can_fold = c->use_df && c->A != 0.0 && c->xi != 0.0 && c->nsp == 1;
     if (cache_lookup(cache_path, key, val)) {
         bestW = cache_field(val, "W", bestW);
         bestT = cache_field(val, "pair_t", bestT);
@@ -853,12 +923,9 @@ extern "C" pimd_status pimd_autotune(pimd_t c, const char* cache_path)
     } else {
         std::vector<int> Ws, Ts;
         if (c->use_df && c->xi != 0.0) {
-            for (int W = 2; W <= XDF_MAXW; ++W) {
-                Layout L;
-                XLayout xl;
-                xdf_layout(L, xl, c->N, EX_STREAMS, W, c->cfg.table_mode == PIMD_TABLE_STORE);
-                if (L.total <= c->L.total) Ws.push_back(W);  // candidate fits the bound workspace
-            }
+            const size_t bound = xdf_footprint(c, cfg_band(c->cfg));
+            for (int W = 2; W <= XDF_MAXW; ++W)
+                if (xdf_footprint(c, W) <= bound) Ws.push_back(W);  // candidate fits the bound workspace
         }
         if (Ws.empty()) Ws.push_back(bestW);
         if (c->A != 0.0) Ts = {64, 128, 256};
@@ -908,12 +975,8 @@ extern "C" pimd_status pimd_autotune(pimd_t c, const char* cache_path)
     if (bestW < 2 || bestW > XDF_MAXW || !pair_block_ok(bestT) || bestH < 2 || bestF < 0 ||
         (bestF > 0 && (!can_fold || 2 + bestH + bestF > sms)))
         return fail(c, PIMD_EINVAL, "pimd_autotune: bad cache entry");
-    {
-        Layout L;
-        XLayout xl;
-        xdf_layout(L, xl, c->N, EX_STREAMS, bestW, c->cfg.table_mode == PIMD_TABLE_STORE);
-        if (c->use_df && L.total > c->L.total) bestW = cfg_band(c->cfg);  // cached choice does not fit this workspace
-    }
+    if (c->use_df && xdf_footprint(c, bestW) > xdf_footprint(c, cfg_band(c->cfg)))
+        bestW = cfg_band(c->cfg);  // cached choice does not fit this workspace
     c->cfg.exch_band = bestW;
     c->pair_t = bestT;
     c->n_help = bestH;
@@ -977,7 +1040,7 @@ extern "C" pimd_status pimd_estimators(pimd_t c, pimd_estimates* out)
     if (e != cudaSuccess) return cuda_fail(c, e, "pimd_estimators: scan");
     // error word, flag and scalars in one round trip through the pinned buffer
     pimd_ctx::HostReport* hr = c->host_rep;
-    int* errp = c->use_df ? c->xd.err : c->xv.err;
+    int* errp = c->use_df ? c->xds[0].err : c->xvs[0].err;
     e = cudaMemcpyAsync(&hr->err, errp, sizeof(int), cudaMemcpyDeviceToHost, c->st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hr->flag, base + c->off_flag, sizeof(int), cudaMemcpyDeviceToHost, c->st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(hr->sc, base + c->off_sc, sizeof hr->sc, cudaMemcpyDeviceToHost, c->st);
@@ -1504,18 +1567,19 @@ extern "C" pimd_status pimd_batch_bind(pimd_batch_t b, const pimd_batch_buffers*
         ScalarSources& ss = a.ss;
         ss.springs = a.part_spr;
         ss.n_springs = b->grid.gx_spr * P;
-        ss.lsum = a.xv.lsum;
-        ss.n_lsum = b->grid.gx_prep;
+        ss.nsp = 1;
+        ss.lsum[0] = a.xv.lsum;
+        ss.n_lsum[0] = b->grid.gx_prep;
         ss.pair = a.part_pair;
         ss.n_pair = b->grid.gx_pair * P;
         ss.fin = a.fo.part;
         ss.n_fin = b->grid.gx_fin;
         ss.md = a.part_md;
         ss.n_md = b->grid.gx_md;
-        ss.N = N;
+        ss.N[0] = N;
         ss.xi_zero = b->xi[r] == 0.0;
         ss.log_xi = b->xi[r] > 0.0 ? log(b->xi[r]) : 0.0;
-        ss.lam = a.xv.lam;
+        ss.lam[0] = a.xv.lam;
         ss.out = (double*)(base + b->off_sc) + (size_t)r * SC_COUNT;
     }
     cudaError_t e = cudaMemcpyAsync(base + b->off_args, b->args.data(), b->args.size() * sizeof(RepArgs),

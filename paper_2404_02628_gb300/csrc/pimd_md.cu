@@ -329,10 +329,11 @@ __device__ __forceinline__ void scalars_body(const ScalarSources& s)
     double t[SC_COUNT];
     for (int q = 0; q < SC_COUNT; ++q) t[q] = 0.0;
     for (int i = 0; i < s.n_springs; ++i) t[SC_EINT] += s.springs[i];
-    for (int i = 0; i < s.n_lsum; ++i) {
-        t[SC_GLINK] += s.lsum[2 * i];
-        t[SC_L0] += s.lsum[2 * i + 1];
-    }
+    for (int sp = 0; sp < s.nsp; ++sp)
+        for (int i = 0; i < s.n_lsum[sp]; ++i) {
+            t[SC_GLINK] += s.lsum[sp][2 * i];
+            t[SC_L0] += s.lsum[sp][2 * i + 1];
+        }
     for (int i = 0; i < s.n_pair; ++i) {
         t[SC_U] += s.pair[2 * i];
         t[SC_VIRIAL] += s.pair[2 * i + 1];
@@ -345,12 +346,18 @@ __device__ __forceinline__ void scalars_body(const ScalarSources& s)
     if (s.xi_zero) {
         t[SC_LAMBDA] = t[SC_L0];
         t[SC_LAMBDA_B] = t[SC_L0];
-    } else if (s.lam) {
-        t[SC_LAMBDA] = s.lam[0];
-        t[SC_LAMBDA_B] = s.lam[1];
     } else {
-        t[SC_LAMBDA] = s.N * s.log_xi + wef_log(Wef{s.y_m[s.N], s.y_e[s.N]});
-        t[SC_LAMBDA_B] = s.N * s.log_xi + wef_log(Wef{s.c_m[0], s.c_e[0]});
+        // the species' recursions are independent: their ln W_N add
+        for (int sp = 0; sp < s.nsp; ++sp) {
+            if (s.lam[sp]) {
+                t[SC_LAMBDA] += s.lam[sp][0];
+                t[SC_LAMBDA_B] += s.lam[sp][1];
+            } else {
+                const int n = s.N[sp];
+                t[SC_LAMBDA] += n * s.log_xi + wef_log(Wef{s.y_m[sp][n], s.y_e[sp][n]});
+                t[SC_LAMBDA_B] += n * s.log_xi + wef_log(Wef{s.c_m[sp][0], s.c_e[sp][0]});
+            }
+        }
     }
     for (int q = 0; q < SC_COUNT; ++q) s.out[q] = t[q];
 }

@@ -65,17 +65,25 @@ enum {
     SC_COUNT
 };
 
+// Most particle species with exchange recursions of their own (pimd_set_species).
+#define PIMD_MAXSP 4
+
 struct ScalarSources {
     const double* springs; int n_springs;   // [n] E_int partials
-    const double* lsum; int n_lsum;         // [n][2]
     const double* pair; int n_pair;         // [n][2]: energy, virial
     const double* fin; int n_fin;           // [n]
     const double* md; int n_md;             // [n][2]: kinetic, thermostat
-    const double* y_m; const int* y_e;      // forward Z at index N
-    const double* c_m; const int* c_e;      // backward Z at index 0
-    int N, xi_zero;
+    int nsp;                                // species, each with its own exchange recursion
+    const double* lsum[PIMD_MAXSP];         // per species: prep partials [n][2]
+    int n_lsum[PIMD_MAXSP];
+    const double* y_m[PIMD_MAXSP];          // per species: forward Z at index N_s (FP64 path)
+    const int* y_e[PIMD_MAXSP];
+    const double* c_m[PIMD_MAXSP];          // per species: backward Z at index 0 (FP64 path)
+    const int* c_e[PIMD_MAXSP];
+    const double* lam[PIMD_MAXSP];          // per species, if set: [2] ln W_N forward/backward (double-float path)
+    int N[PIMD_MAXSP];                      // particles per species
+    int xi_zero;
     double log_xi;
-    const double* lam;                      // if set: [2] ln W_N forward/backward (double-float path)
     double* out;                            // [SC_COUNT]
 };
 

@@ -201,3 +201,23 @@ def test_batch_tuning_host_query(pkg):
         assert t["pair_block"] in (64, 128, 256)
     finally:
         pkg.pimd_batch_destroy(b)
+
+
+def test_species_host_logic(pkg):
+    """pimd_set_species: counts must be positive and add up to N, at most four
+    species, only before bind; the workspace holds one exchange region per
+    species (smaller in store mode, since N_A^2 + N_B^2 < N^2)."""
+    h = pkg.pimd_create(1000, 8, 2, 2.0, 1.0, 3.0, 0.5, 1.0)
+    try:
+        one = pkg.pimd_workspace_bytes(h, 1024)
+        for bad in ([500, 499], [0, 1000], [200] * 5, [1001]):
+            with pytest.raises(pkg.PimdError) as ei:
+                pkg.pimd_set_species(h, bad)
+            assert ei.value.status == pkg.PIMD_EINVAL
+        pkg.pimd_set_species(h, [400, 600])
+        two = pkg.pimd_workspace_bytes(h, 1024)
+        assert 0 < two < one
+        pkg.pimd_set_species(h, [1000])
+        assert pkg.pimd_workspace_bytes(h, 1024) == one
+    finally:
+        pkg.pimd_destroy(h)
