@@ -28,8 +28,7 @@ sys.path.insert(0, ROOT)
 
 L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
 METRIC = "PIMD steps/s at N=1600 & N=10000 (P=32); batched replica-steps/s vs plain FP64"
-FP64_NOMINAL_TFLOPS = 1.25   # GB300 dense FP64 (profiling recipe's nominal table)
-FP32_TFLOPS_DERIVED = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FMA/clk x 2 x 2.07 GHz
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 dense FP64 (profiling recipe's nominal table; used only without the probe)
 
 
 def parse():
@@ -177,38 +176,73 @@ def measured_peaks():
         return {}
 
 
-def kernel_work(name, w):
-    """(bound, work per launch, unit, peak, peak_source) for a kernel slot.
+def kernel_work(name, w, rates=None):
+    """(bound, work per launch, unit, peak, peak_source) for a kernel slot, or
+    None for kernels bound by latency only.
 
+    rates: measured device rates (pimd_probe_rates); without them the FP64
+    nominal figure and an FP32 / MUFU estimate from the SM count stand in.
     Exchange terms T = N(N+1)/2 (all cycle factors exp(-kappa|r^P_l - r^1_u|^2)).
     """
     N, P, d = w["N"], w["P"], w["d"]
     T = N * (N + 1) / 2
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs")
-    hbm_src = "of measured" if hbm else "of fallback"
+    hbm_src = "of measured (MEASURED_PEAKS.json copy)" if hbm else "of fallback"
     hbm = hbm or 6800.0
     dof = N * P * d
-    if name in ("exch_recursion", "batch_exch_recursion"):
+    if rates:
+        fp64, fp64_src = rates["fp64_tflops"], "of measured (pimd_probe_rates FP64 FMA)"
+        ex2, ex2_src = rates["ex2_per_s"] / 1e12, "of measured (pimd_probe_rates MUFU ex2)"
+    else:
+        fp64, fp64_src = FP64_NOMINAL_TFLOPS, "FP64 nominal (recipe)"
+        ex2, ex2_src = 152 * 32 * 2.07e9 / 1e12, "MUFU estimate (152 SM x 32 ex2/clk x 2.07 GHz)"
+    if name == "exch_recursion":
         # forward and backward passes: per term one multiply-add for the
         # recursion and d for the weighted endpoint sums, FP64-accurate
         flops = 2 * T * (1 + d) * 2
-        return "alu", flops / 1e12, "TFLOP/s", FP64_NOMINAL_TFLOPS, "FP64 nominal (recipe)"
+        return "alu", flops / 1e12, "TFLOP/s", fp64, fp64_src
     if name == "exch_table":
-        # per term: d differences, d squares, one scale -> 3d+1 flops, plus one exp
-        flops = T * (3 * d + 2)
-        return "alu", flops / 1e12, "TFLOP/s", FP64_NOMINAL_TFLOPS, "FP64 nominal (recipe)"
+        # HBM floor of the stored table: 12 bytes per factor written
+        return "hbm", T * 12 / 1e9, "GB/s", hbm, hbm_src
     if name in ("pair", "batch_pair"):
-        pairs = P * N * N
-        flops = pairs * (3 * d + 2 * d + 2)
-        return "alu", flops / 1e12, "TFLOP/s", FP32_TFLOPS_DERIVED, "FP32 derived (152 SM x 128 FMA x 2.07 GHz)"
+        # one ex2 per ordered pair and slice (the kernels evaluate every ordered pair)
+        return "mufu", P * N * N / 1e12, "Tex2/s", ex2, ex2_src
     if name in ("md_pre", "md_post", "batch_md_pre", "batch_md_post"):
         M = w["M"]
         byts = dof * 8 * (3 + 2 * M) * 2 - dof * 8 * (1 if name.endswith("md_post") else 0)
         return "hbm", byts / 1e9, "GB/s", hbm, hbm_src
     if name in ("springs", "batch_springs"):
         return "hbm", dof * 8 * 2 / 1e9, "GB/s", hbm, hbm_src
-    return "hbm", dof * 8 / 1e9, "GB/s", hbm, hbm_src
+    return None
+
+
+def chain_floor(pkg, w, clk_mhz):
+    """Latency floor of the recursion launch: nb chain blocks per direction
+    (both directions run at once) times the measured cycles of one block's
+    dependent core (pimd_probe_chain with the chain's split: Q and G each over
+    two warps), at the SM clock sampled during the timed region."""
+    cyc, _, _ = pkg.probe_chain_latency(split=2, nblk=4, n_iter=400)
+    nb = (w["N"] + 1 + 31) // 32
+    us_block = cyc / clk_mhz
+    return {"nb": nb, "cycles_per_block": round(cyc, 1), "us_per_block": round(us_block, 4),
+            "floor_us": round(nb * us_block, 3), "sm_mhz": clk_mhz,
+            "source": "pimd_probe_chain: 32x32 double-float Q and G segment products over 2+2 warps, warp-0 sum, "
+                      "two named barriers per block, all in shared memory"}
+
+
+def kernel_fractions(kernels_us, w, rates):
+    """Per-kernel roofline fractions for the kernels with an algorithmic floor."""
+    out = {}
+    for name, us in kernels_us.items():
+        kw = kernel_work(name, w, rates)
+        if kw is None or us <= 0:
+            continue
+        bound, work, unit, peak, src = kw
+        ach = work / (us * 1e-6)
+        out[name] = {"bound": bound, "achieved": round(ach, 4), "peak": round(peak, 4), "unit": unit,
+                     "frac": round(ach / peak, 4), "peak_source": src}
+    return out
 
 
 def mixed_force_error(pkg, S, w, device, snapshots=10, stride=20):
@@ -236,6 +270,26 @@ def mixed_force_error(pkg, S, w, device, snapshots=10, stride=20):
             "what": "|F_mixed - F_fp64|_inf / |F_fp64|_inf on snapshots of the timed trajectory"}
 
 
+def thermostat_deviation(pkg, w, device, steps=20):
+    """FP32 thermostat-chain arithmetic (nhc_fp32) against the double-float
+    thermostat from the same state: relative infinity-norm differences of
+    positions and momenta and of the conserved energy after `steps` steps."""
+    out = []
+    for nf in (0, 1):
+        S = make_system(pkg, dict(w, nhc_fp32=nf), device)
+        S.step(steps)
+        est = S.estimators()
+        out.append((S.positions(), S.momenta(), est["H_conserved"]))
+        S.close()
+    (x0, p0, h0), (x1, p1, h1) = out
+    import numpy as np
+
+    return {"steps": steps, "positions_rel_inf": float("%.3e" % (np.abs(x1 - x0).max() / np.abs(x0).max())),
+            "momenta_rel_inf": float("%.3e" % (np.abs(p1 - p0).max() / np.abs(p0).max())),
+            "H_conserved_rel": float("%.3e" % (abs(h1 - h0) / abs(h0))),
+            "what": "nhc_fp32=1 against the double-float thermostat, same initial state and forces path"}
+
+
 def small_workload(pkg, w, device, flush, stream, K):
     """Steps/s of one of the small reference workloads (graph-replayed, L2
     flushed between steps like the main line)."""
@@ -249,7 +303,8 @@ def small_workload(pkg, w, device, flush, stream, K):
     S.close()
     return {"value": round(K / (ms / 1e3), 3), "unit": "steps/s", "steps": K, "ms_per_step": round(ms / K, 4),
             "config": {"N": w["N"], "P": w["P"], "d": w["d"], "beta": w["beta"], "xi": w["xi"], "g": w["g"],
-                       "s": w["s"], "precision": w["precision"], "autotuned": tuning}}
+                       "s": w["s"], "precision": w["precision"], "nhc_fp32": w.get("nhc_fp32", 0),
+                       "autotuned": tuning}}
 
 
 def memory_sweep(pkg, device, Ns=(10000, 20000, 30000, 40000), K=3):
@@ -282,7 +337,7 @@ def memory_sweep(pkg, device, Ns=(10000, 20000, 30000, 40000), K=3):
     return out
 
 
-def run_batch(pkg, device, flush, stream, K, warmup):
+def run_batch(pkg, device, flush, stream, K, warmup, rates=None):
     """Batched 64-replica workload (uneven N, beta, xi) against the plain FP64
     single-system form run replica by replica on the same GPU."""
     import torch
@@ -317,8 +372,19 @@ def run_batch(pkg, device, flush, stream, K, warmup):
         tot_ms += timed_steps(S, K1, flush, stream) / K1
         S.close()
     plain = R / (tot_ms / 1e3)
+    # per-kernel fractions: linear kernels from sum N, the pairs from sum N^2
+    sumN = sum(r["N"] for r in reps)
+    sumN2 = sum(r["N"] ** 2 for r in reps)
+    wl = dict(N=sumN, P=P, d=d, M=cfg["M"])
+    fr = kernel_fractions({k: v for k, v in kernels.items() if k != "batch_pair"}, wl, rates)
+    if "batch_pair" in kernels and rates:
+        terms = P * sumN2
+        ach = terms / (kernels["batch_pair"] * 1e-6) / 1e12
+        fr["batch_pair"] = {"bound": "mufu", "achieved": round(ach, 4), "peak": round(rates["ex2_per_s"] / 1e12, 4),
+                            "unit": "Tex2/s", "frac": round(ach / (rates["ex2_per_s"] / 1e12), 4),
+                            "peak_source": "of measured (pimd_probe_rates MUFU ex2)"}
     return {"value": round(batched, 1), "unit": "replica-steps/s", "steps": K, "ms_per_step": round(ms / K, 4),
-            "kernels_us_per_step": kernels,
+            "kernels_us_per_step": kernels, "kernel_fractions": fr,
             "plain_fp64_single": {"value": round(plain, 1), "unit": "replica-steps/s",
                                   "ms_per_replica_step": round(tot_ms / R, 4),
                                   "form": "one System per replica, FP64 pairs/springs/thermostat, "
@@ -340,7 +406,7 @@ def make_system(pkg, w, device, seed_offset=0):
     p = momenta(w["N"], w["P"], w["d"], w["beta"], w["seed"] + seed_offset)
     prec = pkg.PREC_MIXED if w["precision"] == "mixed" else pkg.PREC_FP64
     return pkg.System(w["N"], w["P"], w["d"], w["beta"], w["omega"], w["g"], w["s"], w["xi"], r=r, p=p,
-                      device=device, precision=prec, nhc_len=w["M"], dt=w["dt"])
+                      device=device, precision=prec, nhc_len=w["M"], dt=w["dt"], nhc_fp32=w.get("nhc_fp32", 0))
 
 
 def timed_steps(S, K, flush, stream):
@@ -402,9 +468,11 @@ def run_ours(args):
     n_kernels = len(prof)
     dom = max(per, key=lambda k: per[k][0])
     avg_ms = per[dom][0] / (per[dom][1] * K_prof)
-    bound, work, unit, peak, peak_src = kernel_work(dom, w)
-    achieved = work / (avg_ms / 1e3)
     kernels = {k: round(v[0] / K_prof * 1e3, 2) for k, v in sorted(per.items(), key=lambda x: -x[1][0])}
+    sink = torch.zeros(8, dtype=torch.float64, device=device)
+    rates = pkg.pimd_probe_rates(sink.data_ptr(), stream.cuda_stream)
+    clk_mhz = (clk or {}).get("sm_mhz") or measured_peaks().get("sm_max_mhz") or 2070.0
+    roof = roofline_entry(pkg, dom, avg_ms, w, rates, clk_mhz, per, K_prof)
 
     # end to end through the C ABI with host buffers (pinned), each step:
     # H2D of the full state, one step, D2H of the estimators
@@ -437,10 +505,11 @@ def run_ours(args):
         extra["ideal10000"] = {"value": round(K3 / (ms2 / 1e3), 3), "unit": "steps/s", "steps": K3,
                                "ms_per_step": round(ms2 / K3, 4),
                                "config": {"N": 10000, "P": 32, "d": 2, "beta": 3.0, "xi": 1.0, "g": 0.0,
-                                          "precision": "fp64 exchange + fp32 springs"}}
+                                          "precision": "f64-accurate exchange + fp32 springs and thermostat chain"}}
         S2.close()
-        extra["batch64"] = run_batch(pkg, device, flush, stream, max(10, min(args.steps // 4, 50)), args.warmup)
+        extra["batch64"] = run_batch(pkg, device, flush, stream, max(10, min(args.steps // 4, 50)), args.warmup, rates)
         extra["mixed_vs_fp64_forces"] = mixed_force_error(pkg, S, w, device)
+        extra["fp32_thermostat_vs_df"] = thermostat_deviation(pkg, w, device)
         for name in ("ideal16", "gauss100"):
             extra[name] = small_workload(pkg, WORKLOADS[name], device, flush, stream, max(20, min(args.steps, 500)))
         # the paper's timing workloads; its RTX 4090 figures (about 2.6 and 0.24 steps/s) are context only
@@ -458,14 +527,13 @@ def run_ours(args):
             "metric": METRIC, "value": round(value, 3), "unit": "steps/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 5),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 pairs/springs + f64-accurate exchange", "data": "synthetic",
+            "dtype": "f32 pairs/springs/thermostat chain + f64-accurate exchange and estimators", "data": "synthetic",
             "config": workload_config(w, ws),
             "tuning": tuning,
-            "roofline": {"kernel": dom, "bound": bound, "achieved": round(achieved, 6), "peak": peak,
-                         "unit": unit, "frac": round(achieved / peak, 6), "traffic": ncu_traffic(dom),
-                         "traffic_unit": "bytes per launch (ncu capture, same workload)",
-                         "peak_source": peak_src, "avg_launch_ms": round(avg_ms, 5)},
+            "roofline": roof,
             "kernels_us_per_step": kernels,
+            "kernel_fractions": kernel_fractions(kernels, w, rates),
+            "rates_measured": {k: (round(v, 4) if isinstance(v, float) else v) for k, v in rates.items()},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": n_kernels * args.steps,
@@ -536,6 +604,45 @@ def oracle_throughput(w, cores, warmup, steps_cap, budget_s):
     return sum(n / dt for n, dt in res), sum(n for n, _ in res), res
 
 
+def roofline_entry(pkg, dom, avg_ms, w, rates, clk_mhz, per, K_prof):
+    """Roofline line of the dominant kernel.  The exchange recursion is bound
+    by its serial chain: achieved = chain blocks per microsecond along one
+    direction (nb / launch time), peak = 1 / (measured dependent core of one
+    block), so frac = latency floor / launch time.  Its FP64-equivalent
+    arithmetic and the pair work folded into the same launch are reported
+    beside it against the measured FP64 and MUFU rates."""
+    traffic = ncu_traffic(dom)
+    if dom != "exch_recursion":
+        kw = kernel_work(dom, w, rates)
+        bound, work, unit, peak, src = kw if kw else ("latency", 0.0, "-", 1.0, "-")
+        ach = work / (avg_ms / 1e3)
+        return {"kernel": dom, "bound": bound, "achieved": round(ach, 6), "peak": peak, "unit": unit,
+                "frac": round(ach / peak, 6), "traffic": traffic,
+                "traffic_unit": "bytes per launch (ncu capture, same workload)", "peak_source": src,
+                "avg_launch_ms": round(avg_ms, 5)}
+    fl = chain_floor(pkg, w, clk_mhz)
+    launch_us = avg_ms * 1e3
+    ach = fl["nb"] / launch_us
+    peak = 1.0 / fl["us_per_block"]
+    _, flops, _, fp64, fp64_src = kernel_work("exch_recursion", w, rates)
+    N, P = w["N"], w["P"]
+    folded = {}
+    if w["g"] != 0.0 and "pair" not in per:  # pairs computed by force workers inside this launch
+        ex2 = P * N * N
+        folded = {"pair_terms": ex2, "ex2_per_s": round(ex2 / (avg_ms / 1e3), 1),
+                  "peak_ex2_per_s": round(rates["ex2_per_s"], 1),
+                  "frac": round(ex2 / (avg_ms / 1e3) / rates["ex2_per_s"], 4),
+                  "note": "every ordered pair and slice, one ex2 each, over the whole launch time"}
+    return {"kernel": dom, "bound": "latency", "achieved": round(ach, 4), "peak": round(peak, 4),
+            "unit": "chain blocks/us", "frac": round(ach / peak, 4),
+            "latency_floor_us": fl["floor_us"], "frac_latency": round(fl["floor_us"] / launch_us, 4),
+            "floor": fl, "traffic": traffic, "traffic_unit": "bytes per launch (ncu capture, same workload)",
+            "avg_launch_ms": round(avg_ms, 5),
+            "alu_fp64_equiv": {"achieved_tflops": round(flops / (avg_ms / 1e3), 5), "peak_tflops": round(fp64, 4),
+                               "frac": round(flops / (avg_ms / 1e3) / fp64, 4), "peak_source": fp64_src},
+            "folded_pair_work": folded}
+
+
 def cpu_baseline(w, budget_s=10.0):
     """The oracle timed on the host: one core, and every core of the process's
     affinity set (independent replicas, one per core)."""
@@ -557,7 +664,8 @@ L2_NOTE = ("CUDA arm: L2 flushed between timed steps (512 MB device write); "
 def workload_config(w, ws):
     """The workload keys both arms report (same metric, same configuration)."""
     return {"workload": "gauss1600: N=1600 trapped bosons, d=2, P=32, beta=3, xi=1, "
-                        "Gaussian g=1 s=0.5, NHC M=4, dt=0.01, mixed precision",
+                        "Gaussian g=1 s=0.5, NHC M=4, dt=0.01, mixed precision (FP32 springs, pairs and "
+                        "thermostat-chain arithmetic; FP64-accurate exchange and estimators)",
             "N": w["N"], "P": w["P"], "d": w["d"], "beta": w["beta"], "xi": w["xi"],
             "g": w["g"], "s": w["s"], "amp": "g/(pi s^2)", "parallelism": "replicas x%d" % ws,
             "l2": L2_NOTE}

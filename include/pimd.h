@@ -379,6 +379,37 @@ void pimd_vb_destroy(pimd_vb_t h);
 pimd_status pimd_vb_forward_noalloc(int N, int P, int d, double beta, double xi, const double* r1,
                                     const double* rP, int ld, double* V_out, void* stream);
 
+/* ---- measurement probes (roofline denominators) ------------------------------ */
+/* The paper has no counterpart: these calls measure, on the current device,
+ * what bounds the hot path's kernels, for the roofline fractions that
+ * bench.py reports. */
+typedef struct {
+    double fp64_tflops;  /* FP64 FMA throughput, 2 flops per FMA                       */
+    double fp32_tflops;  /* FP32 FMA throughput, 2 flops per FMA                       */
+    double ex2_per_s;    /* MUFU ex2.approx.f32 results per second (whole device)     */
+    int sms;             /* streaming multiprocessors                                  */
+} pimd_rates;
+/* Runs three throughput kernels (eight independent FMA / ex2 chains per
+ * thread, four 256-thread blocks per SM, a warm-up launch then one timed
+ * launch each, CUDA events) and fills *out.  sink: caller-owned device
+ * buffer of at least 8 bytes (never written in practice; keeps the
+ * arithmetic alive).  Synchronises the stream.  Takes about 0.1 s. */
+pimd_status pimd_probe_rates(double* sink, pimd_rates* out, void* stream);
+
+/* Latency of the recursion chain's dependent core (Sec. III forward
+ * recursion in the factorised form y_J = Q_J y_{J-1} + G_J s_J): one
+ * 256-thread block iterates y_it = Q_k y_{it-1} + G_k s, k = it mod nblk, for
+ * n_iter iterations with the chain's own double-float segment products
+ * (split warps per tile, 32/split columns each; split in {1, 2, 4}), warp-0
+ * sum and two named barriers per iteration, everything in shared memory.
+ * Q, G: device, nblk row-major 32x32 FP64 tiles (entries >= 0); y0, s:
+ * device, 32 entries >= 0; nblk in [1, 8].  Writes the final iterate to
+ * y_out (device, 32 doubles; numerically the product the chain computes) and
+ * the clock64 cycles of the iteration loop to *cycles (device).
+ * Stream-ordered, asynchronous. */
+pimd_status pimd_probe_chain(int nblk, int n_iter, int split, const double* Q, const double* G, const double* y0,
+                             const double* s, double* y_out, long long* cycles, void* stream);
+
 /* ---- xi extrapolation (host only) ------------------------------------------ */
 /*
  * Fictitious-particle thermodynamics (Sec. I and Sec. IV D): an observable is

@@ -27,7 +27,7 @@ __all__ = [
     "pimd_batch_estimators", "pimd_batch_sync", "pimd_batch_last_error", "pimd_batch_destroy",
     "pimd_batch_autotune", "pimd_autotune", "pimd_tuning", "pimd_init_state", "pimd_batch_init_state",
     "pimd_density_accumulate", "pimd_batch_tuning", "pimd_cycle_energies_naive", "pimd_xi_extrapolate",
-    "pimd_set_species",
+    "pimd_set_species", "pimd_probe_rates", "pimd_probe_chain", "probe_chain_latency",
 ]
 
 PIMD_OK, PIMD_EINVAL, PIMD_ENOMEM, PIMD_ECUDA, PIMD_ETIMEOUT, PIMD_ENONFINITE, PIMD_ESTATE = range(7)
@@ -65,6 +65,11 @@ class BatchBuffers(ctypes.Structure):
     _fields_ = [("r", ctypes.c_void_p), ("p", ctypes.c_void_p), ("f", ctypes.c_void_p),
                 ("eta", ctypes.c_void_p), ("peta", ctypes.c_void_p), ("work", ctypes.c_void_p),
                 ("work_bytes", ctypes.c_size_t)]
+
+
+class Rates(ctypes.Structure):
+    _fields_ = [("fp64_tflops", ctypes.c_double), ("fp32_tflops", ctypes.c_double), ("ex2_per_s", ctypes.c_double),
+                ("sms", ctypes.c_int)]
 
 
 class Estimates(ctypes.Structure):
@@ -136,6 +141,8 @@ _SIGS = {
     "pimd_batch_autotune": ([_vp, ctypes.c_char_p], ctypes.c_int),
     "pimd_cycle_energies_naive": ([_vp, _vp, ctypes.c_int], ctypes.c_int),
     "pimd_set_species": ([_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "pimd_probe_rates": ([_vp, ctypes.POINTER(Rates), _vp], ctypes.c_int),
+    "pimd_probe_chain": ([ctypes.c_int] * 3 + [_vp] * 7, ctypes.c_int),
     "pimd_xi_extrapolate": ([ctypes.c_int, _dp, _dp, _dp, ctypes.c_int, ctypes.c_double, _dp, _dp, _dp, _dp],
                             ctypes.c_int),
 }
@@ -193,6 +200,22 @@ def pimd_create(N, P, d, beta, omega, g, s, xi):
 def pimd_set_species(h, counts):
     n = len(counts)
     return _check(lib().pimd_set_species(h, n, (ctypes.c_int * n)(*[int(x) for x in counts])), h)
+
+
+def pimd_probe_rates(sink_ptr, stream):
+    """Measured FP64 / FP32 FMA and MUFU ex2 throughput of the current device."""
+    out = Rates()
+    st = lib().pimd_probe_rates(sink_ptr, ctypes.byref(out), stream)
+    if st != PIMD_OK:
+        raise PimdError(st, "pimd_probe_rates failed")
+    return {f: getattr(out, f) for f, _ in Rates._fields_}
+
+
+def pimd_probe_chain(nblk, n_iter, split, Q, G, y0, s, y_out, cycles, stream):
+    st = lib().pimd_probe_chain(nblk, n_iter, split, Q, G, y0, s, y_out, cycles, stream)
+    if st != PIMD_OK:
+        raise PimdError(st, "pimd_probe_chain: bad argument or launch failure")
+    return st
 
 
 def pimd_default_config():
@@ -450,6 +473,30 @@ def pimd_tuning(h):
     W, T, H, F = (ctypes.c_int() for _ in range(4))
     _check(lib().pimd_tuning(h, ctypes.byref(W), ctypes.byref(T), ctypes.byref(H), ctypes.byref(F)), h)
     return {"exch_band": W.value, "pair_block": T.value, "helpers": H.value, "force_blocks": F.value}
+
+
+def probe_chain_latency(split=2, nblk=4, n_iter=400, seed=0, device="cuda"):
+    """Cycles per iteration of the recursion chain's dependent core
+    (pimd_probe_chain) on seeded non-negative tiles scaled so the iterate stays
+    O(1).  Returns (cycles_per_iteration, y_out, inputs) -- the inputs let a
+    test recompute y_out in FP64."""
+    import numpy as np
+    import torch
+
+    rng = np.random.default_rng(seed)
+    Q = rng.random((nblk, 32, 32)) / 32.0
+    G = rng.random((nblk, 32, 32)) / 32.0
+    y0 = rng.random(32)
+    s = rng.random(32)
+    dev = torch.device(device)
+    t = [torch.tensor(a, dtype=torch.float64, device=dev) for a in (Q, G, y0, s)]
+    y = torch.zeros(32, dtype=torch.float64, device=dev)
+    cyc = torch.zeros(1, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    pimd_probe_chain(nblk, n_iter, split, t[0].data_ptr(), t[1].data_ptr(), t[2].data_ptr(), t[3].data_ptr(),
+                     y.data_ptr(), cyc.data_ptr(), stream)
+    torch.cuda.synchronize(dev)
+    return float(cyc.item()) / n_iter, y.cpu().numpy(), (Q, G, y0, s)
 
 
 class Batch:

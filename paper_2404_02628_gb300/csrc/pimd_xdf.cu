@@ -1705,7 +1705,82 @@ __global__ void xdf_vb_value_kernel(XView v, int nprep, double* V_out)
     *V_out = (gl - lam) / v.beta;
 }
 
+// ------------------------------------------------------------------------
+// Latency probe of the recursion chain: the dependent core of one block
+// iteration, y_it = Q_k y_{it-1} + G_k s with k = it mod nblk (the chain's
+// y_J = Q_J y_{J-1} + G_J s_J).  The Q and G tiles sit in shared memory as
+// wide-exponent double-float tiles; the two products are split over
+// 2*split warps exactly as the chain's phase 1 splits them (split warps per
+// tile, 32/split columns each, compensated segment dots), warp 0 sums the
+// partials into the new solution block (phase 2), and two named barriers
+// close each iteration.  No global memory, helper partials, tile copies or
+// publication: what is left is the work every block of the chain has to do
+// in sequence, so nb times its cycle count is a floor under the chain.
+__global__ void __launch_bounds__(XDF_THREADS, 1)
+    xdf_probe_chain_kernel(const double* Q, const double* G, const double* y0, const double* sv, int nblk, int n_iter,
+                           int split, double* y_out, long long* cycles)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    DfwTile* TQ = reinterpret_cast<DfwTile*>(smem_raw);
+    DfwTile* TG = TQ + nblk;
+    __shared__ float4 xv[2][32];
+    __shared__ float4 sx[32];
+    __shared__ float4 rp[XDF_WARPS][32];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    for (int q = tid; q < nblk * 1024; q += blockDim.x) {
+        const int k = q >> 10, rr = (q >> 5) & 31, cc = q & 31;
+        tile_put(&TQ[k], rr, cc, dfw_norm(df_from_double(Q[q]), 0));
+        tile_put(&TG[k], rr, cc, dfw_norm(df_from_double(G[q]), 0));
+    }
+    if (tid < 32) {
+        xv[0][tid] = dfw_pack(dfw_norm(df_from_double(y0[tid]), 0));
+        sx[tid] = dfw_pack(dfw_norm(df_from_double(sv[tid]), 0));
+    }
+    block_sync();
+    const int nw = 2 * split, cw = 32 / split;
+    const long long t0 = clock64();
+    if (w < nw) {
+        const bool isq = w < split;
+        const int c0 = (isq ? w : w - split) * cw;
+        for (int it = 0; it < n_iter; ++it) {
+            const int k = it % nblk;
+            const dfw p = isq ? dot_seg<false>(&TQ[k], lane, xv[it & 1], c0, c0 + cw)
+                              : dot_seg<false>(&TG[k], lane, sx, c0, c0 + cw);
+            rp[w][lane] = dfw_pack(p);
+            __syncwarp();
+            asm volatile("bar.sync 1, %0;" ::"r"(nw * 32) : "memory");
+            if (w == 0) {
+                dfw t[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) t[i] = i < nw ? dfw_unpack(rp[i][lane]) : dfw_zero();
+                xv[(it + 1) & 1][lane] = dfw_pack(dfw_sum8(t, nw));
+            }
+            __syncwarp();
+            asm volatile("bar.sync 1, %0;" ::"r"(nw * 32) : "memory");
+        }
+    }
+    const long long t1 = clock64();
+    block_sync();
+    if (tid == 0) *cycles = t1 - t0;
+    if (tid < 32) y_out[tid] = dfw_to_double(dfw_unpack(xv[n_iter & 1][tid]));
+}
+
 }  // namespace
+
+cudaError_t xdf_launch_probe_chain(const double* Q, const double* G, const double* y0, const double* s, int nblk,
+                                   int n_iter, int split, double* y_out, long long* cycles, cudaStream_t st)
+{
+    if (nblk < 1 || nblk > 8 || n_iter < 1 || (split != 1 && split != 2 && split != 4)) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)2 * nblk * sizeof(DfwTile);
+    static DeviceOnce attr_once;
+    cudaError_t e = device_once(attr_once, [] {
+        return cudaFuncSetAttribute(xdf_probe_chain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(16 * sizeof(DfwTile)));
+    });
+    if (e != cudaSuccess) return e;
+    xdf_probe_chain_kernel<<<1, XDF_THREADS, smem, st>>>(Q, G, y0, s, nblk, n_iter, split, y_out, cycles);
+    return cudaGetLastError();
+}
 
 // prep and finalize do FP64 work per particle: 64-thread blocks spread it over more SMs
 constexpr int XDF_SMALL_T = 64;

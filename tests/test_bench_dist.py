@@ -55,9 +55,14 @@ def test_kernel_work_table():
     from workloads import WORKLOADS
 
     w = WORKLOADS["gauss1600"]
-    for name in ("exch_recursion", "exch_table", "pair", "md_pre", "md_post", "springs", "other"):
-        bound, work, unit, peak, src = bench.kernel_work(name, w)
-        assert bound in ("alu", "hbm") and work > 0 and peak > 0
+    rates = {"fp64_tflops": 1.2, "fp32_tflops": 74.0, "ex2_per_s": 1.0e13, "sms": 152}
+    for name in ("exch_recursion", "exch_table", "pair", "md_pre", "md_post", "springs"):
+        for r in (None, rates):
+            bound, work, unit, peak, src = bench.kernel_work(name, w, r)
+            assert bound in ("alu", "hbm", "mufu") and work > 0 and peak > 0
+    assert bench.kernel_work("exch_finalize", w, rates) is None
+    fr = bench.kernel_fractions({"md_pre": 15.0, "exch_band": 12.0, "exch_table": 16.0}, w, rates)
+    assert set(fr) == {"md_pre", "exch_table"} and 0 < fr["md_pre"]["frac"] < 1
 
 
 def test_reference_arm_line(capsys):

@@ -1,7 +1,8 @@
 """Oracle parity on the exact configurations bench.py times.
 
 - gauss1600 (N=1600, P=32, beta=3, xi=1, Gaussian g=1, s=0.5): mixed precision
-  with the autotuned launch shape against the FP64 oracle at 1e-5; the same
+  (FP32 springs, pairs and thermostat chain) with the autotuned launch shape
+  against the FP64 oracle at 1e-5, forces and three MD steps; the same
   workload in FP64 mode, both exchange arithmetics, against the oracle's
   extended-precision twin at 1e-10.  The FP64 oracle itself sits about 1e-9
   from the extended result here (its probability exponents are differences
@@ -29,6 +30,7 @@ def _system(pkg, w, **kw):
     r = beads(w["N"], w["P"], w["d"], w["seed"])
     p = momenta(w["N"], w["P"], w["d"], w["beta"], w["seed"])
     prec = kw.pop("precision", pkg.PREC_MIXED if w["precision"] == "mixed" else pkg.PREC_FP64)
+    kw.setdefault("nhc_fp32", w.get("nhc_fp32", 0))
     S = pkg.System(w["N"], w["P"], w["d"], w["beta"], w["omega"], w["g"], w["s"], w["xi"], r=r, p=p,
                    precision=prec, nhc_len=w["M"], dt=w["dt"], **kw)
     return S, r
@@ -68,7 +70,7 @@ def test_gauss1600_fp64_against_extended_oracle(gauss1600_extended, arith):
     import paper_2404_02628_gb300 as pkg
     ref = gauss1600_extended
     w = WORKLOADS["gauss1600"]
-    S, r = _system(pkg, w, precision=pkg.PREC_FP64, exchange_arith=arith)
+    S, r = _system(pkg, w, precision=pkg.PREC_FP64, exchange_arith=arith, nhc_fp32=0)
     S.autotune(None)
     S.forces()
     F = S.forces_array().astype(np.longdouble)
@@ -83,6 +85,29 @@ def test_gauss1600_fp64_against_extended_oracle(gauss1600_extended, arith):
     assert abs(est["spring"] - float(ref["spring"])) < TOL64 * abs(float(ref["spring"]))
     assert abs(est["U_over_P"] - ref["U_over_P"]) < TOL64 * abs(ref["U_over_P"])
     S.close()
+
+
+def test_gauss1600_md_steps_as_benched():
+    """Three MD steps of the benched gauss1600 system (mixed precision with the
+    FP32 thermostat chain, autotuned) against three FP64 steps of the oracle
+    from the same state: positions within 1e-7 and momenta within 1e-5
+    (infinity norm, relative), the energies within 1e-5."""
+    import paper_2404_02628_gb300 as pkg
+    w = WORKLOADS["gauss1600"]
+    S, r = _system(pkg, w)
+    S.autotune(None)
+    S.forces()
+    S.step(3)
+    x, p, est = S.positions(), S.momenta(), S.estimators()
+    S.close()
+    st = oracle.MDState(r, momenta(w["N"], w["P"], w["d"], w["beta"], w["seed"]), w["M"])
+    oest = oracle.md_run(st, w["beta"], w["xi"], w["omega"], amplitude(w["g"], w["s"]), w["s"], w["dt"],
+                         w["beta"] / w["P"], 3)
+    assert rel_inf(x, st.r) < 1e-7
+    assert rel_inf(p, st.p) < 1e-5
+    for k in ("E_prim", "E_vir", "H_conserved"):
+        ref = oest[-1, oracle.ESTIMATE_FIELDS.index(k)]
+        assert abs(est[k] - ref) < 1e-5 * abs(ref), k
 
 
 def test_ideal10000_as_benched():

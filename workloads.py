@@ -10,6 +10,7 @@ arXiv 2404.02628 Sec. IV with P = 32 / 64 instead of 72):
   ideal16      N=16,    P=32, beta=2, xi=1, g=0        FP64, 20000 steps
   gauss100     N=100,   P=64, beta=3, xi=1, g=3, s=0.5 FP64
   gauss1600    N=1600,  P=32, beta=3, xi=1, g=1, s=0.5 mixed precision
+               (FP32 springs, pairs and thermostat-chain arithmetic)
   batch64      64 replicas, N ~ U{32..512}, P=32, beta in {1,2,3,4},
                xi in {0,0.2,...,1}, g=3, s=0.5        mixed precision
   ideal10000   N=10000, P=32, beta=3, xi=1, g=0        FP64 exchange + FP32 springs
@@ -27,14 +28,14 @@ WORKLOADS = {
     "gauss100": dict(N=100, P=64, d=2, beta=3.0, xi=1.0, g=3.0, s=0.5, omega=1.0,
                      precision="fp64", M=4, dt=0.01, seed=2),
     "gauss1600": dict(N=1600, P=32, d=2, beta=3.0, xi=1.0, g=1.0, s=0.5, omega=1.0,
-                      precision="mixed", M=4, dt=0.01, seed=3),
+                      precision="mixed", nhc_fp32=1, M=4, dt=0.01, seed=3),
     "ideal10000": dict(N=10000, P=32, d=2, beta=3.0, xi=1.0, g=0.0, s=0.5, omega=1.0,
-                       precision="mixed", M=4, dt=0.01, seed=5),
+                       precision="mixed", nhc_fp32=1, M=4, dt=0.01, seed=5),
     # the paper's own timing runs (Sec. IV A: ideal trapped bosons at beta = 6, P = 72)
     "paper1600": dict(N=1600, P=72, d=2, beta=6.0, xi=1.0, g=0.0, s=0.5, omega=1.0,
-                      precision="mixed", M=4, dt=0.01, seed=6),
+                      precision="mixed", nhc_fp32=1, M=4, dt=0.01, seed=6),
     "paper10000": dict(N=10000, P=72, d=2, beta=6.0, xi=1.0, g=0.0, s=0.5, omega=1.0,
-                       precision="mixed", M=4, dt=0.01, seed=7),
+                       precision="mixed", nhc_fp32=1, M=4, dt=0.01, seed=7),
 }
 
 BATCH64 = dict(R=64, N_lo=32, N_hi=512, P=32, d=2, betas=(1.0, 2.0, 3.0, 4.0),
