@@ -836,8 +836,12 @@ __device__ void xchain(const XView& v, DfwTile* Tall, ChainS* cs)
     block_sync();
 
     if (w == XDF_WARPS - 1) {
-        // ---- publisher.  The endpoint coordinates of the next block are
-        // loaded while the current one is awaited.
+        // ---- publisher and tile-set refills.  The endpoint coordinates of the
+        // next block are loaded while the current one is awaited.  Every set of
+        // the run is issued, also after an abort, so that every phase of every
+        // slot completes.
+        if (lane < W)
+            for (int i = 0; i < min(NS, nb); ++i) chain_issue_tile<DIR>(v, Tall, cs, i, NS, lane);
         df e[3];
         auto load_e = [&](int it) {
             const int n = 32 * chain_block<DIR>(v, it) + lane;
@@ -849,29 +853,48 @@ __device__ void xchain(const XView& v, DfwTile* Tall, ChainS* cs)
             }
         };
         load_e(0);
+        bool ok = true;
         for (int it = 0; it < nb; ++it) {
-            if (!smem_wait_ge(&cs->y_ready, it, cs, lim, v.err, 0x560000 + it)) break;
-            const int J = chain_block<DIR>(v, it), xs = it % XDF_XR, n = 32 * J + lane;
-            const dfw xw = dfw_unpack(C.xv[xs][lane]);
-            const df xm = df{xw.h, xw.l};
-            (DIR == 0 ? v.yh : v.ch)[n] = xm.h;
-            (DIR == 0 ? v.yl : v.cl)[n] = xm.l;
-            (DIR == 0 ? v.ye : v.ce)[n] = xw.e;
-            for (int c = 0; c < v.d; ++c) {
-                const df u = df_mul(xm, e[c]);
-                (DIR == 0 ? v.uh : v.wh)[(size_t)c * v.npad + n] = u.h;
-                (DIR == 0 ? v.ul : v.wl)[(size_t)c * v.npad + n] = u.l;
+            if (ok) ok = smem_wait_ge(&cs->y_ready, it, cs, lim, v.err, 0x560000 + it);
+            if (ok) {
+                const int J = chain_block<DIR>(v, it), xs = it % XDF_XR, n = 32 * J + lane;
+                const dfw xw = dfw_unpack(C.xv[xs][lane]);
+                const df xm = df{xw.h, xw.l};
+                (DIR == 0 ? v.yh : v.ch)[n] = xm.h;
+                (DIR == 0 ? v.yl : v.cl)[n] = xm.l;
+                (DIR == 0 ? v.ye : v.ce)[n] = xw.e;
+                for (int c = 0; c < v.d; ++c) {
+                    const df u = df_mul(xm, e[c]);
+                    (DIR == 0 ? v.uh : v.wh)[(size_t)c * v.npad + n] = u.h;
+                    (DIR == 0 ? v.ul : v.wl)[(size_t)c * v.npad + n] = u.l;
+                }
+                // the warp barrier orders every lane's stores before lane 0's
+                // release (cumulative), so one release publishes the block
+                __syncwarp();
+                if (lane == 0) {
+                    st_release(&flag_chain[J], 1);
+                    vstore(&cs->published, it);
+                }
+                __syncwarp();
+                if (it + 1 < nb) load_e(it + 1);
             }
-            // the warp barrier orders every lane's stores before lane 0's
-            // release (cumulative), so one release publishes the block
-            __syncwarp();
-            if (lane == 0) {
-                st_release(&flag_chain[J], 1);
-                vstore(&cs->published, it);
+            // y of iteration it is ready, so phase 1 of iteration it -- the
+            // only reader of its tile set -- is over: the slot takes the set of
+            // it + NS once its previous copies have landed
+            if (it + NS < nb) {
+                if (lane == 0)
+                    mbar_wait(&cs->mb_set[it % NS], (unsigned)(it / NS), lim, v.err, &cs->abort, 0x5f4000 + it, true);
+                __syncwarp();
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                if (lane < W) chain_issue_tile<DIR>(v, Tall, cs, it + NS, NS, lane);
             }
-            __syncwarp();
-            if (it + 1 < nb) load_e(it + 1);
         }
+        // every issued bulk copy lands before the block's shared memory is released
+        if (lane == 0)
+            for (int q = 0; q < NS && q < nb; ++q) {
+                const int last = q + ((nb - 1 - q) / NS) * NS;
+                mbar_wait(&cs->mb_set[q], (unsigned)(last / NS), lim, v.err, &cs->abort, 0x5f8000 + q, true);
+            }
         return;
     }
     if (w == XDF_WARPS - 2) {
@@ -948,10 +971,6 @@ __device__ void xchain(const XView& v, DfwTile* Tall, ChainS* cs)
         for (int i = 0; i < 6; ++i) ridx[i] = cs->red_idx[w][i];
         rn = cs->red_n[w];
     }
-    // warp 5 issues the tile copies, lane m for tile m, every set of the run
-    // (also after an abort, so that every set's phase completes)
-    if (w == 5 && lane < W)
-        for (int i = 0; i < min(NS, nb); ++i) chain_issue_tile<DIR>(v, Tall, cs, i, NS, lane);
     for (int it = 0; it < nb; ++it) {
         const int J = chain_block<DIR>(v, it), slot = it % NS;
         DfwTile* T = Tall + slot * W;
@@ -1008,16 +1027,6 @@ __device__ void xchain(const XView& v, DfwTile* Tall, ChainS* cs)
             const int sl = J % W;
             cput(C.hh, C.hl, C.he, sl, lane, dfw_zero());
             cput(C.ph, C.pl, C.pe, sl, lane, dfw_zero());
-        } else if (w == 5) {
-            // the slot this iteration's phase 1 consumed takes the set of it + NS;
-            // its previous copies have landed (waited for again in case the
-            // block aborted and phase 1 skipped the wait)
-            if (it + NS < nb) {
-                if (lane == 0)
-                    mbar_wait(&cs->mb_set[slot], (unsigned)(it / NS), lim, v.err, &cs->abort, 0x5f4000 + it, true);
-                __syncwarp();
-                if (lane < W) chain_issue_tile<DIR>(v, Tall, cs, it + NS, NS, lane);
-            }
         } else if (w <= 3) {
             const int m = w + 1;
             if (m < W && it >= 1 && chain_tile_on<DIR>(v, it, m)) {
@@ -1036,12 +1045,6 @@ __device__ void xchain(const XView& v, DfwTile* Tall, ChainS* cs)
         }
         __syncwarp();
     }
-    // every issued bulk copy lands before the block's shared memory is released
-    if (w == 5 && lane == 0)
-        for (int q = 0; q < NS && q < nb; ++q) {
-            const int last = q + ((nb - 1 - q) / NS) * NS;
-            mbar_wait(&cs->mb_set[q], (unsigned)(last / NS), lim, v.err, &cs->abort, 0x5f8000 + q, true);
-        }
 }
 
 // Running weighted sums of one lane over the tiles of a helper item:
