@@ -89,7 +89,15 @@ typedef struct {
                            diagonal itself, helper blocks the rest */
     int nhc_fp32;       /* 1: thermostat chain arithmetic in FP32 (state stays FP64, the
                            momentum scaling is applied in FP64); 0: FP64 (default)        */
+    int batch_schedule; /* batched replicas only: PIMD_BATCH_PERSISTENT (default 0): the
+                           exchange part of a step (prep, factor table, block operators,
+                           recursion, band sums of every replica) is one persistent launch
+                           working through a dependency-ordered list, beside a grid-stride
+                           launch of the springs and pair units on a second stream;
+                           PIMD_BATCH_KERNELS: one launch per kernel                      */
 } pimd_config;
+
+enum { PIMD_BATCH_PERSISTENT = 0, PIMD_BATCH_KERNELS = 1 };
 
 enum { PIMD_XARITH_DF = 0, PIMD_XARITH_FP64 = 1 };
 
@@ -267,9 +275,14 @@ void pimd_destroy(pimd_t ctx);
  * R independent systems of uneven particle number N_r <= 2047, inverse
  * temperature beta_r and exchange parameter xi_r (for instance the xi and
  * temperature scans of Sec. II's fictitious-particle method), sharing P, d,
- * omega, g, s and one pimd_config.  Each step runs every replica with one
- * launch per kernel (the exchange recursion one block per replica and
- * direction, no cross-block waits), replayed as one CUDA graph.
+ * omega, g, s and one pimd_config.  A step is replayed as one CUDA graph:
+ * the thermostat half step, then (batch_schedule = PIMD_BATCH_PERSISTENT)
+ * one persistent launch that works through the exchange part of every
+ * replica -- prep, factor tiles, block operators, the recursion (one block
+ * per replica and direction, longest replicas first), band sums -- in
+ * dependency order, while a grid-stride launch on a second stream computes
+ * the springs and pair forces; then the endpoint forces and the second half
+ * step.  With PIMD_BATCH_KERNELS each part is one launch over all replicas.
  * table_mode, exchange_arith, exch_band and helper_ctas are ignored: the
  * batch always stores the factor table and uses the double-float recursion.
  * nhc_Q <= 0 selects beta_r/P per replica.
@@ -312,11 +325,15 @@ pimd_status pimd_batch_step_profiled(pimd_batch_t b, int nsteps, double* ms_out,
 const char* pimd_batch_profile_slot_name(pimd_batch_t b, int slot);
 /* out: host array of R estimates (synchronises). */
 pimd_status pimd_batch_estimators(pimd_batch_t b, pimd_estimates* out);
-/* Autotuner of the batched step (as pimd_autotune): the pair-kernel block of
- * 64, 128 or 256 particles, cached by device and (R, sum N, sum N^2, P, d). */
+/* Autotuner of the batched step (as pimd_autotune): the pair block of 64, 128
+ * or 256 particles and the schedule (persistent or one launch per kernel),
+ * cached by device and (R, sum N, sum N^2, P, d). */
 pimd_status pimd_batch_autotune(pimd_batch_t b, const char* cache_path);
 /* The batch's current pair-kernel block (host only; any time after create). */
 pimd_status pimd_batch_tuning(pimd_batch_t b, int* pair_block);
+/* The batch's current schedule, PIMD_BATCH_PERSISTENT or PIMD_BATCH_KERNELS
+ * (host only; the autotuner may change it). */
+pimd_status pimd_batch_schedule(pimd_batch_t b, int* schedule);
 pimd_status pimd_batch_sync(pimd_batch_t b);
 const char* pimd_batch_last_error(pimd_batch_t b);
 void pimd_batch_destroy(pimd_batch_t b);

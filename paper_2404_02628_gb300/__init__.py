@@ -26,7 +26,8 @@ __all__ = [
     "pimd_batch_step_eager", "pimd_batch_step_profiled", "pimd_batch_profile_slot_name",
     "pimd_batch_estimators", "pimd_batch_sync", "pimd_batch_last_error", "pimd_batch_destroy",
     "pimd_batch_autotune", "pimd_autotune", "pimd_tuning", "pimd_init_state", "pimd_batch_init_state",
-    "pimd_density_accumulate", "pimd_batch_tuning", "pimd_cycle_energies_naive", "pimd_xi_extrapolate",
+    "pimd_density_accumulate", "pimd_batch_tuning", "pimd_batch_schedule", "pimd_cycle_energies_naive",
+    "pimd_xi_extrapolate",
     "pimd_set_species", "pimd_probe_rates", "pimd_probe_chain", "probe_chain_latency",
 ]
 
@@ -37,6 +38,7 @@ PREC_FP64, PREC_MIXED = 0, 1
 AMP_PAPER, AMP_RAW = 0, 1
 TABLE_STORE, TABLE_RECOMPUTE = 0, 1
 XARITH_DF, XARITH_FP64 = 0, 1
+BATCH_PERSISTENT, BATCH_KERNELS = 0, 1
 
 LIB_PATH = _build.LIB
 
@@ -52,7 +54,7 @@ class Config(ctypes.Structure):
                 ("mass", ctypes.c_double), ("precision", ctypes.c_int), ("amp_convention", ctypes.c_int),
                 ("table_mode", ctypes.c_int), ("thermostat", ctypes.c_int), ("helper_ctas", ctypes.c_int),
                 ("spin_limit", ctypes.c_int), ("exchange_arith", ctypes.c_int), ("exch_band", ctypes.c_int),
-                ("nhc_fp32", ctypes.c_int)]
+                ("nhc_fp32", ctypes.c_int), ("batch_schedule", ctypes.c_int)]
 
 
 class Buffers(ctypes.Structure):
@@ -135,6 +137,7 @@ _SIGS = {
     "pimd_autotune": ([_vp, ctypes.c_char_p], ctypes.c_int),
     "pimd_density_accumulate": ([_vp, ctypes.c_int, ctypes.c_double, _vp], ctypes.c_int),
     "pimd_batch_tuning": ([_vp, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "pimd_batch_schedule": ([_vp, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "pimd_init_state": ([_vp, ctypes.c_ulonglong], ctypes.c_int),
     "pimd_batch_init_state": ([_vp, ctypes.c_ulonglong], ctypes.c_int),
     "pimd_tuning": ([_vp] + [ctypes.POINTER(ctypes.c_int)] * 4, ctypes.c_int),
@@ -435,7 +438,15 @@ def pimd_density_accumulate(h, nbins, r_max, hist_ptr):
 def pimd_batch_tuning(h):
     T = ctypes.c_int()
     _bcheck(lib().pimd_batch_tuning(h, ctypes.byref(T)), h)
-    return {"pair_block": T.value}
+    S = ctypes.c_int()
+    _bcheck(lib().pimd_batch_schedule(h, ctypes.byref(S)), h)
+    return {"pair_block": T.value, "schedule": "persistent" if S.value == BATCH_PERSISTENT else "kernels"}
+
+
+def pimd_batch_schedule(h):
+    S = ctypes.c_int()
+    _bcheck(lib().pimd_batch_schedule(h, ctypes.byref(S)), h)
+    return S.value
 
 
 def pimd_init_state(h, seed):

@@ -291,6 +291,8 @@ extern "C" void pimd_default_config(pimd_config* cfg)
     cfg->spin_limit = 0;
     cfg->exchange_arith = PIMD_XARITH_DF;
     cfg->exch_band = 0;
+    cfg->nhc_fp32 = 0;
+    cfg->batch_schedule = PIMD_BATCH_PERSISTENT;
 }
 
 extern "C" pimd_status pimd_create(int N, int P, int d, double beta, double omega, double g, double s, double xi,
@@ -1333,7 +1335,71 @@ struct pimd_batch {
     size_t off_args = 0, off_err = 0, off_sc = 0, off_tab = 0, off_flag = 0;
     std::vector<RepArgs> args;
     const char* slot_names[64] = {};
+    // persistent schedule: work list, per-replica phase counts, force-unit prefix
+    int sched = PIMD_BATCH_PERSISTENT;
+    std::vector<BatchItem> items;
+    std::vector<int> need, prefix;
+    size_t off_items = 0, off_need = 0, off_cnt = 0, off_prefix = 0;
+    std::vector<size_t> off_parts;  // per replica: springs and pair partial regions
+    size_t parts_bytes = 0;
+    cudaStream_t side = nullptr;    // second stream of the step (springs and pairs)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
+
+// Table tiles per work item of the persistent schedule.
+constexpr int BATCH_TABLE_CHUNK = 8;
+
+// The persistent schedule's work list (see BatchItem): phase by phase; the
+// exchange phases take replicas longest first, the band sums shortest first
+// (their recursions end first).  need[r][phase] counts the items of each phase.
+static void batch_items(pimd_batch* b)
+{
+    std::vector<int> order(b->R);
+    for (int r = 0; r < b->R; ++r) order[r] = r;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->N[x] > b->N[y]; });
+    auto nbof = [&](int r) { return (b->N[r] + 1 + 31) / 32; };
+    auto chunks = [&](int r) {
+        const long long nt = xdf_ntiles(nbof(r), nbof(r), 1);
+        return (int)((nt + BATCH_TABLE_CHUNK - 1) / BATCH_TABLE_CHUNK);
+    };
+    b->items.clear();
+    b->need.assign((size_t)b->R * 4, 0);
+    for (int r : order) {
+        b->items.push_back({BI_PREP, r, b->grid.gx_prep, 0});
+        b->need[r * 4 + BI_PREP] = 1;
+    }
+    for (int r : order) {
+        if (b->xi[r] == 0.0) continue;  // no exchange recursion at xi = 0
+        const int K = chunks(r);
+        for (int k = 0; k < K; ++k) b->items.push_back({BI_TABLE, r, k, K});
+        b->need[r * 4 + BI_TABLE] = K;
+    }
+    for (int r : order) {
+        if (b->xi[r] == 0.0) continue;
+        for (int J = 0; J < nbof(r); ++J) b->items.push_back({BI_BLOCKOPS, r, J, 0});
+        b->need[r * 4 + BI_BLOCKOPS] = nbof(r);
+    }
+    for (int r : order) {
+        if (b->xi[r] == 0.0) continue;
+        b->items.push_back({BI_REC, r, 0, 0});
+        b->items.push_back({BI_REC, r, 1, 0});
+        b->need[r * 4 + BI_REC] = 2;
+    }
+    for (int q = b->R - 1; q >= 0; --q) {
+        const int r = order[q];
+        if (b->xi[r] == 0.0) continue;
+        for (int J = 0; J < nbof(r); ++J)
+            for (int dir = 0; dir < 2; ++dir) b->items.push_back({BI_BAND, r, J, dir});
+    }
+}
+
+// First force unit of every replica for the current pair block (R + 1 entries).
+static void batch_prefix(pimd_batch* b)
+{
+    b->prefix.assign(b->R + 1, 0);
+    for (int r = 0; r < b->R; ++r)
+        b->prefix[r + 1] = b->prefix[r] + b->P * pair_grid_x(b->N[r], b->grid.pair_t);
+}
 
 static pimd_status bfail(pimd_batch_t b, pimd_status s, const std::string& m)
 {
@@ -1395,6 +1461,8 @@ extern "C" pimd_status pimd_batch_configure(pimd_batch_t b, const pimd_config* c
         return bfail(b, PIMD_EINVAL, "pimd_batch_configure: unknown precision");
     if (cfg->amp_convention != PIMD_AMP_PAPER && cfg->amp_convention != PIMD_AMP_RAW)
         return bfail(b, PIMD_EINVAL, "pimd_batch_configure: unknown amplitude convention");
+    if (cfg->batch_schedule != PIMD_BATCH_PERSISTENT && cfg->batch_schedule != PIMD_BATCH_KERNELS)
+        return bfail(b, PIMD_EINVAL, "pimd_batch_configure: unknown batch_schedule");
     b->cfg = *cfg;
     b->A = cfg->amp_convention == PIMD_AMP_RAW ? b->g : b->g / (M_PI * b->s * b->s);
     return PIMD_OK;
@@ -1436,7 +1504,7 @@ static void batch_layout(pimd_batch* b, std::vector<XLayout>& xl, std::vector<si
     for (int r = 0; r < b->R; ++r) {
         const int nb = (b->N[r] + 1 + 31) / 32;
         xdf_layout(b->L, xl[r], b->N[r], 1, nb, 1);
-        offs[5 * r + 0] = b->L.add((size_t)g.gx_spr * b->P * sizeof(double));
+        offs[5 * r + 0] = b->L.add((size_t)std::max(g.gx_spr, g.gx_pair_max) * b->P * sizeof(double));
         offs[5 * r + 1] = b->L.add((size_t)g.gx_pair_max * b->P * 2 * sizeof(double));
         offs[5 * r + 2] = b->L.add((size_t)g.gx_fin * sizeof(double));
         offs[5 * r + 3] = b->L.add((size_t)g.gx_md * 2 * sizeof(double));
@@ -1447,7 +1515,33 @@ static void batch_layout(pimd_batch* b, std::vector<XLayout>& xl, std::vector<si
     b->off_tab = b->L.add(256 * sizeof(float2));
     b->off_err = b->L.add(4 * sizeof(int));
     b->off_flag = b->L.add(4 * sizeof(int));
+    batch_items(b);
+    b->off_items = b->L.add(b->items.size() * sizeof(BatchItem));
+    b->off_need = b->L.add((size_t)b->R * 4 * sizeof(int));
+    b->off_cnt = b->L.add(((size_t)b->R * 4 + 1) * sizeof(int));
+    b->off_prefix = b->L.add(((size_t)b->R + 1) * sizeof(int));
 }
+
+// Per-replica springs and pair partial sums: slots a schedule does not write
+// must read zero, so they are cleared whenever the partial layout changes
+// (bind, schedule or pair block).
+static cudaError_t batch_clear_parts(pimd_batch* b)
+{
+    char* base = (char*)b->buf.work;
+    cudaError_t e = cudaSuccess;
+    for (int r = 0; r < b->R && e == cudaSuccess; ++r) {
+        e = cudaMemsetAsync(b->args[r].part_spr, 0,
+                            (size_t)std::max(b->grid.gx_spr, b->grid.gx_pair_max) * b->P * sizeof(double), b->st);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(b->args[r].part_pair, 0, (size_t)b->grid.gx_pair_max * b->P * 2 * sizeof(double), b->st);
+    }
+    (void)base;
+    return e;
+}
+
+// Partial-sum counts of the scalar reduction for the current schedule and
+// pair block, then uploads the replica arguments and the force-unit prefix.
+static pimd_status batch_upload_args(pimd_batch* b);
 
 extern "C" pimd_status pimd_batch_workspace_bytes(pimd_batch_t b, size_t* bytes)
 {
@@ -1461,11 +1555,54 @@ extern "C" pimd_status pimd_batch_workspace_bytes(pimd_batch_t b, size_t* bytes)
 
 static pimd_status batch_enqueue_forces(pimd_batch* b, cudaStream_t st, ProfMarks* pm = nullptr)
 {
-    const RepArgs* ra = (const RepArgs*)((char*)b->buf.work + b->off_args);
-    cudaError_t e = batch_launch_forces(ra, b->grid, st, pm);
-    if (e != cudaSuccess) return bcuda(b, e, "batch springs/pair kernels");
-    e = batch_launch_exchange(ra, b->grid, st, pm);
-    if (e != cudaSuccess) return bcuda(b, e, "batch exchange kernels");
+    char* base = (char*)b->buf.work;
+    const RepArgs* ra = (const RepArgs*)(base + b->off_args);
+    cudaError_t e;
+    if (b->sched == PIMD_BATCH_KERNELS) {
+        e = batch_launch_forces(ra, b->grid, st, pm);
+        if (e != cudaSuccess) return bcuda(b, e, "batch springs/pair kernels");
+        e = batch_launch_exchange(ra, b->grid, st, pm);
+        if (e != cudaSuccess) return bcuda(b, e, "batch exchange kernels");
+        return PIMD_OK;
+    }
+    BatchSched sc;
+    sc.items = (const BatchItem*)(base + b->off_items);
+    sc.n_items = (int)b->items.size();
+    sc.done = (int*)(base + b->off_cnt);
+    sc.next = sc.done + (size_t)b->R * 4;
+    sc.need = (const int*)(base + b->off_need);
+    sc.err = (int*)(base + b->off_err);
+    sc.spin_limit = default_spin_limit(b->cfg.spin_limit);
+    ForceUnits fu;
+    fu.prefix = (const int*)(base + b->off_prefix);
+    fu.R = b->R;
+    fu.gx = b->grid.gx_pair;
+    const int sms = std::max(1, device_sms());
+    // the side stream only when not profiling: per-kernel event times need one stream
+    const bool fork = (pm == nullptr);
+    e = cudaMemsetAsync(base + b->off_cnt, 0, ((size_t)b->R * 4 + 1) * sizeof(int), st);
+    if (e != cudaSuccess) return bcuda(b, e, "batch schedule reset");
+    if (fork) {
+        e = cudaEventRecord(b->ev_fork, st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->ev_fork, 0);
+        if (e != cudaSuccess) return bcuda(b, e, "batch fork");
+    }
+    // the exchange launch first, one block per SM, so that its blocks are
+    // resident before the force units fill the SMs' remaining room
+    e = batch_launch_exchange_persistent(ra, sc, sms, st);
+    prof_mark(pm, "batch_exch_persistent", st);
+    if (e != cudaSuccess) return bcuda(b, e, "batch persistent exchange");
+    e = batch_launch_force_units(ra, fu, b->grid, 4 * sms, fork ? b->side : st);
+    prof_mark(pm, "batch_force_units", st);
+    if (e != cudaSuccess) return bcuda(b, e, "batch force units");
+    if (fork) {
+        e = cudaEventRecord(b->ev_join, b->side);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, b->ev_join, 0);
+        if (e != cudaSuccess) return bcuda(b, e, "batch join");
+    }
+    e = batch_launch_finalize(ra, b->grid, st);
+    prof_mark(pm, "batch_exch_finalize", st);
+    if (e != cudaSuccess) return bcuda(b, e, "batch endpoint forces");
     return PIMD_OK;
 }
 
@@ -1582,8 +1719,17 @@ extern "C" pimd_status pimd_batch_bind(pimd_batch_t b, const pimd_batch_buffers*
         ss.lam[0] = a.xv.lam;
         ss.out = (double*)(base + b->off_sc) + (size_t)r * SC_COUNT;
     }
-    cudaError_t e = cudaMemcpyAsync(base + b->off_args, b->args.data(), b->args.size() * sizeof(RepArgs),
-                                    cudaMemcpyHostToDevice, b->st);
+    cudaError_t e = cudaSuccess;
+    b->sched = b->cfg.batch_schedule;
+    if (!b->side) e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !b->ev_fork) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess && !b->ev_join) e = cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming);
+    if (e != cudaSuccess) return bcuda(b, e, "pimd_batch_bind: side stream");
+    // the work list and phase counts never change after bind
+    e = cudaMemcpy(base + b->off_items, b->items.data(), b->items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(base + b->off_need, b->need.data(), b->need.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bcuda(b, e, "pimd_batch_bind: work list");
     if (e == cudaSuccess && b->cfg.thermostat) {
         const size_t n = (size_t)M * b->off[b->R];
         e = cudaMemsetAsync(bf->eta, 0, n * sizeof(double), b->st);
@@ -1592,6 +1738,8 @@ extern "C" pimd_status pimd_batch_bind(pimd_batch_t b, const pimd_batch_buffers*
     if (e == cudaSuccess) e = cudaMemsetAsync(base + b->off_err, 0, 8 * sizeof(int), b->st);
     if (e == cudaSuccess) e = xdf_upload_table((float2*)(base + b->off_tab), b->st);
     if (e != cudaSuccess) return bcuda(b, e, "pimd_batch_bind: setup");
+    pimd_status us = batch_upload_args(b);
+    if (us != PIMD_OK) return us;
     b->bound = true;
     b->steps = 0;
     pimd_status s = batch_enqueue_forces(b, b->st);
@@ -1729,9 +1877,20 @@ extern "C" const char* pimd_batch_profile_slot_name(pimd_batch_t b, int slot)
 // tuning change) and uploads them.
 static pimd_status batch_upload_args(pimd_batch* b)
 {
-    for (auto& a : b->args) a.ss.n_pair = b->grid.gx_pair * b->P;
-    cudaError_t e = cudaMemcpyAsync((char*)b->buf.work + b->off_args, b->args.data(), b->args.size() * sizeof(RepArgs),
+    // springs partials: kernel layout (128-particle blocks) or force-unit layout
+    // (pair-block units, stride gx_pair); pair partials stride gx_pair in both
+    for (auto& a : b->args) {
+        a.ss.n_springs = (b->sched == PIMD_BATCH_KERNELS ? b->grid.gx_spr : b->grid.gx_pair) * b->P;
+        a.ss.n_pair = b->grid.gx_pair * b->P;
+    }
+    batch_prefix(b);
+    char* base = (char*)b->buf.work;
+    cudaError_t e = cudaMemcpyAsync(base + b->off_args, b->args.data(), b->args.size() * sizeof(RepArgs),
                                     cudaMemcpyHostToDevice, b->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(base + b->off_prefix, b->prefix.data(), b->prefix.size() * sizeof(int),
+                            cudaMemcpyHostToDevice, b->st);
+    if (e == cudaSuccess) e = batch_clear_parts(b);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
     return e == cudaSuccess ? PIMD_OK : bcuda(b, e, "batch argument upload");
 }
@@ -1751,6 +1910,13 @@ extern "C" pimd_status pimd_batch_tuning(pimd_batch_t b, int* pair_block)
     return PIMD_OK;
 }
 
+extern "C" pimd_status pimd_batch_schedule(pimd_batch_t b, int* schedule)
+{
+    if (!b || !schedule) return bfail(b, PIMD_EINVAL, "pimd_batch_schedule: NULL argument");
+    *schedule = b->bound ? b->sched : b->cfg.batch_schedule;
+    return PIMD_OK;
+}
+
 extern "C" pimd_status pimd_batch_autotune(pimd_batch_t b, const char* cache_path)
 {
     if (!b) return bfail(b, PIMD_EINVAL, "pimd_batch_autotune: NULL handle");
@@ -1765,29 +1931,37 @@ extern "C" pimd_status pimd_batch_autotune(pimd_batch_t b, const char* cache_pat
              b->cfg.precision, b->A == 0.0);
     const std::string key = device_key() + " " + kb;
     std::string val;
-    int bestT = b->grid.pair_t;
+    int bestT = b->grid.pair_t, bestS = b->sched;
     if (cache_lookup(cache_path, key, val)) {
         bestT = cache_field(val, "pair_t", bestT);
-    } else if (b->A != 0.0) {
+        bestS = cache_field(val, "sched", bestS);
+    } else {
         double best = 1e30;
-        for (int T : {64, 128, 256}) {
-            batch_set_pair_t(b, T);
-            pimd_status st = batch_upload_args(b);
-            if (st != PIMD_OK) return st;
-            const double ms = time_ms(b->st, 3, [&] {
-                if (st == PIMD_OK) st = batch_enqueue_forces(b, b->st);
-            });
-            if (st != PIMD_OK) return st;
-            if (ms < best) {
-                best = ms;
-                bestT = T;
+        std::vector<int> Ts = {64, 128, 256};
+        if (b->A == 0.0) Ts = {bestT};
+        for (int S : {PIMD_BATCH_PERSISTENT, PIMD_BATCH_KERNELS})
+            for (int T : Ts) {
+                b->sched = S;
+                batch_set_pair_t(b, T);
+                pimd_status st = batch_upload_args(b);
+                if (st != PIMD_OK) return st;
+                const double ms = time_ms(b->st, 3, [&] {
+                    if (st == PIMD_OK) st = batch_enqueue_forces(b, b->st);
+                });
+                if (st != PIMD_OK) return st;
+                if (ms < best) {
+                    best = ms;
+                    bestT = T;
+                    bestS = S;
+                }
             }
-        }
         char vb[64];
-        snprintf(vb, sizeof vb, "pair_t=%d", bestT);
+        snprintf(vb, sizeof vb, "pair_t=%d;sched=%d", bestT, bestS);
         cache_store(cache_path, key, vb);
     }
-    if (!pair_block_ok(bestT)) return bfail(b, PIMD_EINVAL, "pimd_batch_autotune: bad cache entry");
+    if (!pair_block_ok(bestT) || (bestS != PIMD_BATCH_PERSISTENT && bestS != PIMD_BATCH_KERNELS))
+        return bfail(b, PIMD_EINVAL, "pimd_batch_autotune: bad cache entry");
+    b->sched = bestS;
     batch_set_pair_t(b, bestT);
     pimd_status s = batch_upload_args(b);
     if (s != PIMD_OK) return s;
@@ -1842,6 +2016,9 @@ extern "C" void pimd_batch_destroy(pimd_batch_t b)
     if (!b) return;
     if (b->graph) cudaGraphExecDestroy(b->graph);
     if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->side) cudaStreamDestroy(b->side);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_join) cudaEventDestroy(b->ev_join);
     delete b;
 }
 

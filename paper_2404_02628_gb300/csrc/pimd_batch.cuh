@@ -26,7 +26,39 @@ struct BatchGrid {
     int gx_pair_max;  // pair partial-sum blocks per slice allocated (for the smallest block)
 };
 
+// Work list of the batched exchange step run as one persistent launch: each
+// block claims the next item, waits (bounded) until every item of the
+// replica's previous phase is done, runs it, and counts it done.  Items are
+// listed phase by phase (prep, factor table, block operators, recursion,
+// band sums), so every item depends only on items listed before it, which
+// were claimed by blocks already running: the launch needs no co-residency.
+enum { BI_PREP = 0, BI_TABLE = 1, BI_BLOCKOPS = 2, BI_REC = 3, BI_BAND = 4 };
+struct BatchItem {
+    int type, r, a, b;  // phase, replica, and per phase: table chunk/chunks, block, direction, block/direction
+};
+struct BatchSched {
+    const BatchItem* items;
+    int n_items;
+    int* next;        // next item to claim (zeroed before each launch)
+    int* done;        // [R][4] finished items of prep, table, block operators, recursion (zeroed before each launch)
+    const int* need;  // [R][4] items of each of those phases
+    int* err;
+    int spin_limit;
+};
+
+// Springs and trap + pairs of every replica as (replica, slice, particle
+// block) units taken grid-stride from a flat list: prefix[r] is the first unit
+// of replica r (R + 1 entries), gx the partial-sum stride per slice.
+struct ForceUnits {
+    const int* prefix;
+    int R, gx;
+};
+
 int batch_md_blocks(int nmax, int P, int d);
+cudaError_t batch_launch_exchange_persistent(const RepArgs* ra, const BatchSched& sc, int blocks, cudaStream_t st);
+cudaError_t batch_launch_force_units(const RepArgs* ra, const ForceUnits& fu, const BatchGrid& g, int blocks,
+                                     cudaStream_t st);
+cudaError_t batch_launch_finalize(const RepArgs* ra, const BatchGrid& g, cudaStream_t st);
 cudaError_t batch_launch_md(const RepArgs* ra, const BatchGrid& g, bool pre, cudaStream_t st);
 cudaError_t batch_launch_forces(const RepArgs* ra, const BatchGrid& g, cudaStream_t st, ProfMarks* pm);
 cudaError_t batch_launch_exchange(const RepArgs* ra, const BatchGrid& g, cudaStream_t st, ProfMarks* pm);

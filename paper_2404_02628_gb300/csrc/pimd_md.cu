@@ -396,6 +396,36 @@ __global__ void __launch_bounds__(MD_T) md_batch(const RepArgs* ra)
     md_body<PRE, M>(a.bv, a.mp);
 }
 
+// Springs and trap + pairs of every replica from the flat unit list (see
+// ForceUnits): unit u of replica r covers slice j = k / gx_r and particles
+// [bx PT, bx PT + PT), k = u - prefix[r], bx = k mod gx_r, gx_r = ceil(N_r / PT);
+// partial sums go to slot j * fu.gx + bx.  Grid-stride, so the launch can be
+// sized to leave room on every SM for the concurrent exchange step.
+template <int D, bool MIXED, int PT>
+__global__ void __launch_bounds__(PT) force_units_batch(const RepArgs* ra, ForceUnits fu)
+{
+    __shared__ double red[96];
+    __shared__ __align__(16) unsigned char sx[D * PT * sizeof(double)];
+    const int total = fu.prefix[fu.R];
+    for (int u = blockIdx.x; u < total; u += gridDim.x) {
+        int lo = 0, hi = fu.R - 1;  // last replica whose first unit is <= u
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (fu.prefix[mid] <= u) lo = mid;
+            else hi = mid - 1;
+        }
+        const RepArgs& a = ra[lo];
+        const int gxr = (a.bv.N + PT - 1) / PT, k = u - fu.prefix[lo], j = k / gxr, bx = k - j * gxr;
+        ForceParams fs = a.fp, fq = a.fp;
+        fs.accumulate = 0;
+        fq.accumulate = 1;
+        springs_unit(a.bv, fs, a.bv.f, a.part_spr, bx, j, fu.gx, red + 64);
+        if (MIXED) pair_unit_f32<D, PT>(a.bv, fq, a.bv.f, a.part_pair, bx, j, fu.gx, reinterpret_cast<float2*>(sx), red);
+        else pair_unit_f64<D, PT>(a.bv, fq, a.bv.f, a.part_pair, bx, j, fu.gx, reinterpret_cast<double*>(sx), red);
+        __syncthreads();  // shared scratch is reused by the next unit
+    }
+}
+
 __global__ void __launch_bounds__(MD_T) md_energy_batch(const RepArgs* ra)
 {
     const RepArgs& a = ra[blockIdx.z];
@@ -660,6 +690,32 @@ cudaError_t batch_launch_forces(const RepArgs* ra, const BatchGrid& g, cudaStrea
     }
 #undef PIMD_PB
     prof_mark(pm, "batch_pair", st);
+    return cudaGetLastError();
+}
+
+cudaError_t batch_launch_force_units(const RepArgs* ra, const ForceUnits& fu, const BatchGrid& g, int blocks,
+                                     cudaStream_t st)
+{
+    const int d = g.d;
+    const bool mixed = g.mixed != 0;
+#define PIMD_FU(PT)                                                                         \
+    if (mixed) {                                                                            \
+        if (d == 1) force_units_batch<1, true, PT><<<blocks, PT, 0, st>>>(ra, fu);          \
+        else if (d == 2) force_units_batch<2, true, PT><<<blocks, PT, 0, st>>>(ra, fu);     \
+        else force_units_batch<3, true, PT><<<blocks, PT, 0, st>>>(ra, fu);                 \
+    } else {                                                                                \
+        if (d == 1) force_units_batch<1, false, PT><<<blocks, PT, 0, st>>>(ra, fu);         \
+        else if (d == 2) force_units_batch<2, false, PT><<<blocks, PT, 0, st>>>(ra, fu);    \
+        else force_units_batch<3, false, PT><<<blocks, PT, 0, st>>>(ra, fu);                \
+    }
+    if (g.pair_t == 64) {
+        PIMD_FU(64)
+    } else if (g.pair_t == 256) {
+        PIMD_FU(256)
+    } else {
+        PIMD_FU(128)
+    }
+#undef PIMD_FU
     return cudaGetLastError();
 }
 

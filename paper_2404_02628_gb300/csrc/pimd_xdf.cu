@@ -5,6 +5,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
+
 #include "pimd_batch.cuh"
 #include "pimd_forcework.cuh"
 
@@ -372,11 +374,12 @@ __device__ __forceinline__ void load_tab_smem(float2* tab_s, const float2* tab)
 // ------------------------------------------------------------------------
 // prep: double-float endpoints, row constants, link energy, flags
 
-__device__ __forceinline__ void prep_body(const XView& v)
+// (bx, gx): this block's index and the number of blocks sharing the work.
+__device__ __forceinline__ void prep_body(const XView& v, int bx, int gx)
 {
     __shared__ double red[64];
     double acc[2] = {0.0, 0.0};
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < v.npad; q += gridDim.x * blockDim.x) {
+    for (int q = bx * blockDim.x + threadIdx.x; q < v.npad; q += gx * blockDim.x) {
         for (int c = 0; c < 3; ++c) {
             df a = df{0.f, 0.f}, b = df{0.f, 0.f};
             if (c < v.d && q < v.N) {
@@ -419,15 +422,15 @@ __device__ __forceinline__ void prep_body(const XView& v)
         }
     }
     const int nflags = 2 * v.nb + 2 * v.nb * v.S;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nflags; j += gridDim.x * blockDim.x) v.flags[j] = 0;
+    for (int j = bx * blockDim.x + threadIdx.x; j < nflags; j += gx * blockDim.x) v.flags[j] = 0;
     block_reduce<2>(acc, red);
     if (threadIdx.x == 0) {
-        v.lsum[blockIdx.x * 2 + 0] = acc[0];
-        v.lsum[blockIdx.x * 2 + 1] = acc[1];
+        v.lsum[bx * 2 + 0] = acc[0];
+        v.lsum[bx * 2 + 1] = acc[1];
     }
 }
 
-__global__ void __launch_bounds__(256) xdf_prep_kernel(XView v) { prep_body(v); }
+__global__ void __launch_bounds__(256) xdf_prep_kernel(XView v) { prep_body(v, blockIdx.x, gridDim.x); }
 
 // ------------------------------------------------------------------------
 // factor table: M tiles (all in store mode, band |J-I| < W otherwise)
@@ -437,13 +440,13 @@ __global__ void __launch_bounds__(256) xdf_prep_kernel(XView v) { prep_body(v); 
 // in shared memory once per tile; each element then needs only double-float
 // arithmetic (difference, TwoProduct square, sum, scale) and the exp.
 template <int D>
-__device__ __forceinline__ void table_body_t(const XView& v, long long ntiles)
+__device__ __forceinline__ void table_body_t(const XView& v, long long ntiles, int bx, int gx)
 {
     __shared__ float2 tab[256];
     __shared__ float sa[3][2][32], sb[3][2][32], scr[2][32];
     load_tab_smem(tab, v.tab);
     const df kap = df{v.kap_h, v.kap_l};
-    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    for (long long t = bx; t < ntiles; t += gx) {
         int J, I;
         if (v.store) {  // t = J(J+1)/2 + I; float estimate then integer correction
             J = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
@@ -498,27 +501,29 @@ __device__ __forceinline__ void table_body_t(const XView& v, long long ntiles)
 }
 
 // the dimension as a template argument, so the per-element coordinate loop unrolls
-__device__ __forceinline__ void table_body(const XView& v, long long ntiles)
+__device__ __forceinline__ void table_body(const XView& v, long long ntiles, int bx, int gx)
 {
-    if (v.d == 1) table_body_t<1>(v, ntiles);
-    else if (v.d == 2) table_body_t<2>(v, ntiles);
-    else table_body_t<3>(v, ntiles);
+    if (v.d == 1) table_body_t<1>(v, ntiles, bx, gx);
+    else if (v.d == 2) table_body_t<2>(v, ntiles, bx, gx);
+    else table_body_t<3>(v, ntiles, bx, gx);
 }
 
-__global__ void __launch_bounds__(256) xdf_table_kernel(XView v, long long ntiles) { table_body(v, ntiles); }
+__global__ void __launch_bounds__(256) xdf_table_kernel(XView v, long long ntiles)
+{
+    table_body(v, ntiles, blockIdx.x, gridDim.x);
+}
 
 // ------------------------------------------------------------------------
 // block operators: G_J = (I - M_JJ)^{-1}, Q_J = G_J M_{J,J-1}, P_J = M_{J+1,J} G_J
 
 // part 0: G_J and Q_J; part 1: P_J (G_J recomputed); part -1: all three.
-__device__ __forceinline__ void blockops_body(const XView& v, int part)
+__device__ __forceinline__ void blockops_body(const XView& v, int part, int J)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     DfwTile* L = reinterpret_cast<DfwTile*>(smem_raw);
     DfwTile* G = L + 1;
     DfwTile* Ms = L + 2;
     DfwTile* Mp = L + 3;
-    const int J = blockIdx.x;
     if (J >= v.nb) return;  // a block past this replica's blocks
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     {
@@ -579,7 +584,7 @@ constexpr int XDF_BLOCKOPS_T = 1024;  // one warp per column of G
 // redoes it.
 __global__ void __launch_bounds__(XDF_BLOCKOPS_T) xdf_blockops_kernel(XView v)
 {
-    blockops_body(v, gridDim.y == 2 ? (int)blockIdx.y : -1);
+    blockops_body(v, gridDim.y == 2 ? (int)blockIdx.y : -1, blockIdx.x);
 }
 
 // ------------------------------------------------------------------------
@@ -1281,7 +1286,7 @@ __global__ void __launch_bounds__(XDF_THREADS, 1) xdf_recursion_kernel(XView v, 
 // Band sums: forward row block J over tiles I in [J-W+1, J]; backward column
 // block I over row blocks [I, I+W-1].  Warp w takes tiles m = w, w + nw, ...
 // (nw = warps of the block) and the warps' sums are merged in warp order.
-__device__ __forceinline__ void band_body(const XView& v)
+__device__ __forceinline__ void band_body(const XView& v, int blk, int dir)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nw = blockDim.x >> 5;
@@ -1289,7 +1294,6 @@ __device__ __forceinline__ void band_body(const XView& v)
     WeightSmem* Ws = reinterpret_cast<WeightSmem*>(smem_raw + nw * sizeof(DfwTile));
     DVAcc* hm = reinterpret_cast<DVAcc*>(smem_raw + nw * (sizeof(DfwTile) + sizeof(WeightSmem)));
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int blk = blockIdx.x, dir = blockIdx.y;
     if (blk >= v.nb) return;  // a block past this replica's blocks
     DVAcc a = dv_zero();
     for (int m = w; m < v.W; m += nw) {
@@ -1313,7 +1317,7 @@ __device__ __forceinline__ void band_body(const XView& v)
     }
 }
 
-__global__ void __launch_bounds__(256) xdf_band_kernel(XView v) { band_body(v); }
+__global__ void __launch_bounds__(256) xdf_band_kernel(XView v) { band_body(v, blockIdx.x, blockIdx.y); }
 
 __device__ __forceinline__ dfw xget(const float* h, const float* l, const int* e, int i) { return dfw{h[i], l[i], e[i]}; }
 
@@ -1657,27 +1661,30 @@ __global__ void __launch_bounds__(XDF_THREADS, 1) xsolo_batch(const RepArgs* ra)
     else xsolo<1>(v, T, ss);
 }
 
-__global__ void __launch_bounds__(256) prep_batch(const RepArgs* ra) { prep_body(ra[blockIdx.z].xv); }
+__global__ void __launch_bounds__(256) prep_batch(const RepArgs* ra)
+{
+    prep_body(ra[blockIdx.z].xv, blockIdx.x, gridDim.x);
+}
 
 __global__ void __launch_bounds__(256) table_batch(const RepArgs* ra)
 {
     const XView& v = ra[blockIdx.z].xv;
     if (v.xi_zero) return;
-    table_body(v, xdf_ntiles(v.nb, v.W, v.store));
+    table_body(v, xdf_ntiles(v.nb, v.W, v.store), blockIdx.x, gridDim.x);
 }
 
 __global__ void __launch_bounds__(XDF_BLOCKOPS_T) blockops_batch(const RepArgs* ra)
 {
     const XView& v = ra[blockIdx.z].xv;
     if (v.xi_zero) return;
-    blockops_body(v, -1);
+    blockops_body(v, -1, blockIdx.x);
 }
 
 __global__ void __launch_bounds__(256) band_batch(const RepArgs* ra)
 {
     const XView& v = ra[blockIdx.z].xv;
     if (v.xi_zero) return;
-    band_body(v);
+    band_body(v, blockIdx.x, blockIdx.y);
 }
 
 __global__ void __launch_bounds__(256) finalize_batch(const RepArgs* ra)
@@ -1686,6 +1693,62 @@ __global__ void __launch_bounds__(256) finalize_batch(const RepArgs* ra)
     if (a.xv.d == 1) finalize_body<1>(a.xv, a.fo);
     else if (a.xv.d == 2) finalize_body<2>(a.xv, a.fo);
     else finalize_body<3>(a.xv, a.fo);
+}
+
+// The batched exchange step as one persistent launch (work list in
+// pimd_batch.cuh).  A recursion item runs the self-contained solve of one
+// replica and direction (xsolo), reading tiles that other blocks wrote in
+// this launch through the async proxy, hence the proxy fence after the
+// acquire.
+__global__ void __launch_bounds__(XDF_THREADS, 2) batch_exch_persistent(const RepArgs* ra, BatchSched sc)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_item, s_ok;
+    const int tid = threadIdx.x;
+    for (;;) {
+        block_sync();  // every thread has read the previous item's s_item and s_ok
+        if (tid == 0) s_item = atomicAdd(sc.next, 1);
+        block_sync();
+        const int i = s_item;
+        if (i >= sc.n_items) return;
+        const BatchItem it = sc.items[i];
+        const XView& v = ra[it.r].xv;
+        if (tid == 0) {
+            int ok = 1;
+            if (it.type != BI_PREP) {
+                const int ph = it.type - 1;
+                ok = wait_flag(&sc.done[it.r * 4 + ph], sc.need[it.r * 4 + ph], sc.err, sc.spin_limit,
+                               0x900000 + (it.type << 16) + (it.r & 0xFFFF));
+            }
+            s_ok = ok;
+        }
+        block_sync();
+        if (s_ok) {
+            switch (it.type) {
+            case BI_PREP:
+                prep_body(v, 0, 1);
+                // the other prep partial slots of the replica (a: their count) hold zero
+                for (int q = 2 + tid; q < 2 * it.a; q += blockDim.x) v.lsum[q] = 0.0;
+                break;
+            case BI_TABLE: table_body(v, xdf_ntiles(v.nb, v.W, v.store), it.a, it.b); break;
+            case BI_BLOCKOPS: blockops_body(v, -1, it.a); break;
+            case BI_REC: {
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+                DfwTile* T = reinterpret_cast<DfwTile*>(smem_raw);
+                SoloS* ss = reinterpret_cast<SoloS*>(smem_raw + XS_SLOTS * sizeof(DfwTile));
+                if (it.a == 0) xsolo<0>(v, T, ss);
+                else xsolo<1>(v, T, ss);
+                break;
+            }
+            default: band_body(v, it.a, it.b); break;
+            }
+        }
+        block_sync();
+        if (tid == 0 && it.type != BI_BAND) {
+            __threadfence();
+            atomicAdd(&sc.done[it.r * 4 + it.type], 1);
+        }
+    }
 }
 
 // V_ends = V_xi - sum E_int = (sum_l g(l, l+1) - ln W_N)/beta with
@@ -1902,6 +1965,29 @@ cudaError_t batch_launch_exchange(const RepArgs* ra, const BatchGrid& g, cudaStr
     prof_mark(pm, "batch_exch_band", st);
     finalize_batch<<<dim3(g.gx_fin, 1, g.R), XDF_FIN_T, 0, st>>>(ra);
     prof_mark(pm, "batch_exch_finalize", st);
+    return cudaGetLastError();
+}
+
+static size_t persistent_smem()
+{
+    return std::max(std::max(xsolo_smem(), band_smem(8)), blockops_smem());
+}
+
+cudaError_t batch_launch_exchange_persistent(const RepArgs* ra, const BatchSched& sc, int blocks, cudaStream_t st)
+{
+    static DeviceOnce attr_once;
+    cudaError_t e = device_once(attr_once, [] {
+        return cudaFuncSetAttribute(batch_exch_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)persistent_smem());
+    });
+    if (e != cudaSuccess) return e;
+    batch_exch_persistent<<<blocks, XDF_THREADS, persistent_smem(), st>>>(ra, sc);
+    return cudaGetLastError();
+}
+
+cudaError_t batch_launch_finalize(const RepArgs* ra, const BatchGrid& g, cudaStream_t st)
+{
+    finalize_batch<<<dim3(g.gx_fin, 1, g.R), XDF_FIN_T, 0, st>>>(ra);
     return cudaGetLastError();
 }
 
