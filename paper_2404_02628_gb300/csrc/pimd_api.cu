@@ -1339,51 +1339,37 @@ struct pimd_batch {
     int sched = PIMD_BATCH_PERSISTENT;
     std::vector<BatchItem> items;
     std::vector<int> need, prefix;
-    size_t off_items = 0, off_need = 0, off_cnt = 0, off_prefix = 0;
+    std::vector<int2> tiles, blocks;  // flat (replica, tile) and (replica, diagonal block) lists
+    size_t off_items = 0, off_need = 0, off_cnt = 0, off_prefix = 0, off_tiles = 0, off_blocks = 0;
     std::vector<size_t> off_parts;  // per replica: springs and pair partial regions
     size_t parts_bytes = 0;
     cudaStream_t side = nullptr;    // second stream of the step (springs and pairs)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
-// Table tiles per work item of the persistent schedule.
-constexpr int BATCH_TABLE_CHUNK = 8;
-
-// The persistent schedule's work list (see BatchItem): phase by phase; the
-// exchange phases take replicas longest first, the band sums shortest first
-// (their recursions end first).  need[r][phase] counts the items of each phase.
+// The persistent launch's work list (see BatchItem): the recursions longest
+// replica first, then the band sums shortest replica first (their recursions
+// end first); need[r][BI_REC] counts a replica's recursion items.  Also the
+// flat (replica, tile) and (replica, diagonal block) lists of the factor-tile
+// and block-operator kernels.
 static void batch_items(pimd_batch* b)
 {
     std::vector<int> order(b->R);
     for (int r = 0; r < b->R; ++r) order[r] = r;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->N[x] > b->N[y]; });
     auto nbof = [&](int r) { return (b->N[r] + 1 + 31) / 32; };
-    auto chunks = [&](int r) {
-        const long long nt = xdf_ntiles(nbof(r), nbof(r), 1);
-        return (int)((nt + BATCH_TABLE_CHUNK - 1) / BATCH_TABLE_CHUNK);
-    };
     b->items.clear();
+    b->tiles.clear();
+    b->blocks.clear();
     b->need.assign((size_t)b->R * 4, 0);
     for (int r : order) {
-        b->items.push_back({BI_PREP, r, b->grid.gx_prep, 0});
-        b->need[r * 4 + BI_PREP] = 1;
-    }
-    for (int r : order) {
         if (b->xi[r] == 0.0) continue;  // no exchange recursion at xi = 0
-        const int K = chunks(r);
-        for (int k = 0; k < K; ++k) b->items.push_back({BI_TABLE, r, k, K});
-        b->need[r * 4 + BI_TABLE] = K;
-    }
-    for (int r : order) {
-        if (b->xi[r] == 0.0) continue;
-        for (int J = 0; J < nbof(r); ++J) b->items.push_back({BI_BLOCKOPS, r, J, 0});
-        b->need[r * 4 + BI_BLOCKOPS] = nbof(r);
-    }
-    for (int r : order) {
-        if (b->xi[r] == 0.0) continue;
         b->items.push_back({BI_REC, r, 0, 0});
         b->items.push_back({BI_REC, r, 1, 0});
         b->need[r * 4 + BI_REC] = 2;
+        const long long nt = xdf_ntiles(nbof(r), nbof(r), 1);
+        for (long long t = 0; t < nt; ++t) b->tiles.push_back(make_int2(r, (int)t));
+        for (int J = 0; J < nbof(r); ++J) b->blocks.push_back(make_int2(r, J));
     }
     for (int q = b->R - 1; q >= 0; --q) {
         const int r = order[q];
@@ -1520,6 +1506,8 @@ static void batch_layout(pimd_batch* b, std::vector<XLayout>& xl, std::vector<si
     b->off_need = b->L.add((size_t)b->R * 4 * sizeof(int));
     b->off_cnt = b->L.add(((size_t)b->R * 4 + 1) * sizeof(int));
     b->off_prefix = b->L.add(((size_t)b->R + 1) * sizeof(int));
+    b->off_tiles = b->L.add(b->tiles.size() * sizeof(int2));
+    b->off_blocks = b->L.add(b->blocks.size() * sizeof(int2));
 }
 
 // Per-replica springs and pair partial sums: slots a schedule does not write
@@ -1580,15 +1568,16 @@ static pimd_status batch_enqueue_forces(pimd_batch* b, cudaStream_t st, ProfMark
     const int sms = std::max(1, device_sms());
     // the side stream only when not profiling: per-kernel event times need one stream
     const bool fork = (pm == nullptr);
-    e = cudaMemsetAsync(base + b->off_cnt, 0, ((size_t)b->R * 4 + 1) * sizeof(int), st);
-    if (e != cudaSuccess) return bcuda(b, e, "batch schedule reset");
     if (fork) {
         e = cudaEventRecord(b->ev_fork, st);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->ev_fork, 0);
         if (e != cudaSuccess) return bcuda(b, e, "batch fork");
     }
-    // the exchange launch first, one block per SM, so that its blocks are
-    // resident before the force units fill the SMs' remaining room
+    e = batch_launch_prep_tables_ops(ra, b->grid, st, pm);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + b->off_cnt, 0, ((size_t)b->R * 4 + 1) * sizeof(int), st);
+    if (e != cudaSuccess) return bcuda(b, e, "batch prep, factor tiles and block operators");
+    // the recursion launch one block per SM, ahead of the force units in
+    // issue order, so that its blocks find room beside them
     e = batch_launch_exchange_persistent(ra, sc, sms, st);
     prof_mark(pm, "batch_exch_persistent", st);
     if (e != cudaSuccess) return bcuda(b, e, "batch persistent exchange");
@@ -1729,6 +1718,14 @@ extern "C" pimd_status pimd_batch_bind(pimd_batch_t b, const pimd_batch_buffers*
     e = cudaMemcpy(base + b->off_items, b->items.data(), b->items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(base + b->off_need, b->need.data(), b->need.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !b->tiles.empty())
+        e = cudaMemcpy(base + b->off_tiles, b->tiles.data(), b->tiles.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !b->blocks.empty())
+        e = cudaMemcpy(base + b->off_blocks, b->blocks.data(), b->blocks.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    b->grid.tiles = (const int2*)(base + b->off_tiles);
+    b->grid.n_tiles = (int)b->tiles.size();
+    b->grid.blocks = (const int2*)(base + b->off_blocks);
+    b->grid.n_blocks = (int)b->blocks.size();
     if (e != cudaSuccess) return bcuda(b, e, "pimd_batch_bind: work list");
     if (e == cudaSuccess && b->cfg.thermostat) {
         const size_t n = (size_t)M * b->off[b->R];

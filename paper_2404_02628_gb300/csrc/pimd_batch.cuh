@@ -24,24 +24,29 @@ struct BatchGrid {
     int gx_spr, gx_pair, gx_md, gx_prep, gx_fin, gx_table, nb_max;
     int pair_t;       // pair-kernel block size (particles per block), 64/128/256
     int gx_pair_max;  // pair partial-sum blocks per slice allocated (for the smallest block)
+    const int2* tiles;   // device: (replica, factor tile) of every replica with xi > 0
+    int n_tiles;
+    const int2* blocks;  // device: (replica, diagonal block) of every replica with xi > 0
+    int n_blocks;
 };
 
-// Work list of the batched exchange step run as one persistent launch: each
-// block claims the next item, waits (bounded) until every item of the
-// replica's previous phase is done, runs it, and counts it done.  Items are
-// listed phase by phase (prep, factor table, block operators, recursion,
-// band sums), so every item depends only on items listed before it, which
-// were claimed by blocks already running: the launch needs no co-residency.
-enum { BI_PREP = 0, BI_TABLE = 1, BI_BLOCKOPS = 2, BI_REC = 3, BI_BAND = 4 };
+// Work list of the batched recursion and band sums, run as one persistent
+// launch after the prep, factor-tile and block-operator kernels: each block
+// claims the next item, waits (bounded) until the items its item depends on
+// are done, runs it, and counts it done.  Recursion items (longest replicas
+// first) come before all band items, and a band item depends only on the
+// two recursion items of its replica, which were claimed by blocks already
+// running: the launch needs no co-residency.
+enum { BI_REC = 3, BI_BAND = 4 };
 struct BatchItem {
-    int type, r, a, b;  // phase, replica, and per phase: table chunk/chunks, block, direction, block/direction
+    int type, r, a, b;  // kind, replica; recursion: a = direction; band: a = block, b = direction
 };
 struct BatchSched {
     const BatchItem* items;
     int n_items;
     int* next;        // next item to claim (zeroed before each launch)
-    int* done;        // [R][4] finished items of prep, table, block operators, recursion (zeroed before each launch)
-    const int* need;  // [R][4] items of each of those phases
+    int* done;        // [R][4] finished recursion items at [r][3] (zeroed before each launch)
+    const int* need;  // [R][4] recursion items of each replica at [r][3]
     int* err;
     int spin_limit;
 };
@@ -59,6 +64,8 @@ cudaError_t batch_launch_exchange_persistent(const RepArgs* ra, const BatchSched
 cudaError_t batch_launch_force_units(const RepArgs* ra, const ForceUnits& fu, const BatchGrid& g, int blocks,
                                      cudaStream_t st);
 cudaError_t batch_launch_finalize(const RepArgs* ra, const BatchGrid& g, cudaStream_t st);
+cudaError_t batch_launch_prep_tables_ops(const RepArgs* ra, const BatchGrid& g, cudaStream_t st, ProfMarks* pm);
+cudaError_t batch_launch_tables_ops(const RepArgs* ra, const BatchGrid& g, cudaStream_t st, ProfMarks* pm);
 cudaError_t batch_launch_md(const RepArgs* ra, const BatchGrid& g, bool pre, cudaStream_t st);
 cudaError_t batch_launch_forces(const RepArgs* ra, const BatchGrid& g, cudaStream_t st, ProfMarks* pm);
 cudaError_t batch_launch_exchange(const RepArgs* ra, const BatchGrid& g, cudaStream_t st, ProfMarks* pm);

@@ -439,14 +439,15 @@ __global__ void __launch_bounds__(256) xdf_prep_kernel(XView v) { prep_body(v, b
 // endpoints a_{n-1}, row constants c_n and 32 column endpoints b_k are staged
 // in shared memory once per tile; each element then needs only double-float
 // arithmetic (difference, TwoProduct square, sum, scale) and the exp.
+struct TableStage {
+    float sa[3][2][32], sb[3][2][32], scr[2][32];
+};
+
 template <int D>
-__device__ __forceinline__ void table_body_t(const XView& v, long long ntiles, int bx, int gx)
+__device__ __forceinline__ void table_tile_t(const XView& v, long long t, const float2* tab, TableStage& st)
 {
-    __shared__ float2 tab[256];
-    __shared__ float sa[3][2][32], sb[3][2][32], scr[2][32];
-    load_tab_smem(tab, v.tab);
     const df kap = df{v.kap_h, v.kap_l};
-    for (long long t = bx; t < ntiles; t += gx) {
+    {
         int J, I;
         if (v.store) {  // t = J(J+1)/2 + I; float estimate then integer correction
             J = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
@@ -463,17 +464,17 @@ __device__ __forceinline__ void table_body_t(const XView& v, long long ntiles, i
             const bool on = n >= 1 && n <= v.N;
             for (int c = 0; c < 3; ++c) {
                 const bool cc = on && c < v.d;
-                sa[c][0][r] = cc ? v.ah[(size_t)c * v.npad + n - 1] : 0.f;
-                sa[c][1][r] = cc ? v.al[(size_t)c * v.npad + n - 1] : 0.f;
+                st.sa[c][0][r] = cc ? v.ah[(size_t)c * v.npad + n - 1] : 0.f;
+                st.sa[c][1][r] = cc ? v.al[(size_t)c * v.npad + n - 1] : 0.f;
             }
-            scr[0][r] = on ? v.crh[n] : 0.f;
-            scr[1][r] = on ? v.crl[n] : 0.f;
+            st.scr[0][r] = on ? v.crh[n] : 0.f;
+            st.scr[1][r] = on ? v.crl[n] : 0.f;
         } else if (threadIdx.x < 64 && I >= 0) {
             const int cl = threadIdx.x - 32, k = 32 * I + cl;
             for (int c = 0; c < 3; ++c) {
                 const bool cc = c < v.d;
-                sb[c][0][cl] = cc ? v.bh[(size_t)c * v.npad + k] : 0.f;
-                sb[c][1][cl] = cc ? v.bl[(size_t)c * v.npad + k] : 0.f;
+                st.sb[c][0][cl] = cc ? v.bh[(size_t)c * v.npad + k] : 0.f;
+                st.sb[c][1][cl] = cc ? v.bl[(size_t)c * v.npad + k] : 0.f;
             }
         }
         block_sync();
@@ -485,12 +486,12 @@ __device__ __forceinline__ void table_body_t(const XView& v, long long ntiles, i
                 df g = df{0.f, 0.f};
 #pragma unroll
                 for (int cc = 0; cc < D; ++cc) {
-                    const df x = df_sub(df{sa[cc][0][r], sa[cc][1][r]}, df{sb[cc][0][c], sb[cc][1][c]});
+                    const df x = df_sub(df{st.sa[cc][0][r], st.sa[cc][1][r]}, df{st.sb[cc][0][c], st.sb[cc][1][c]});
                     df sq = two_prod(x.h, x.h);
                     sq.l = __fmaf_rn(2.f * x.h, x.l, sq.l);
                     g = df_add(g, sq);
                 }
-                m = dfw_exp(df_sub(df{scr[0][r], scr[1][r]}, df_mul(g, kap)), tab);
+                m = dfw_exp(df_sub(df{st.scr[0][r], st.scr[1][r]}, df_mul(g, kap)), tab);
             }
             const int o = RIDX(r, c);
             Mt->h[o] = m.h;
@@ -498,6 +499,15 @@ __device__ __forceinline__ void table_body_t(const XView& v, long long ntiles, i
             Mt->e[o] = m.e;
         }
     }
+}
+
+template <int D>
+__device__ __forceinline__ void table_body_t(const XView& v, long long ntiles, int bx, int gx)
+{
+    __shared__ float2 tab[256];
+    __shared__ TableStage st;
+    load_tab_smem(tab, v.tab);
+    for (long long t = bx; t < ntiles; t += gx) table_tile_t<D>(v, t, tab, st);
 }
 
 // the dimension as a template argument, so the per-element coordinate loop unrolls
@@ -1666,19 +1676,27 @@ __global__ void __launch_bounds__(256) prep_batch(const RepArgs* ra)
     prep_body(ra[blockIdx.z].xv, blockIdx.x, gridDim.x);
 }
 
-__global__ void __launch_bounds__(256) table_batch(const RepArgs* ra)
+
+// Factor tiles of every replica from a flat list of (replica, tile) pairs, grid-stride.
+template <int D>
+__global__ void __launch_bounds__(256) table_flat(const RepArgs* ra, const int2* list, int n)
 {
-    const XView& v = ra[blockIdx.z].xv;
-    if (v.xi_zero) return;
-    table_body(v, xdf_ntiles(v.nb, v.W, v.store), blockIdx.x, gridDim.x);
+    __shared__ float2 tab[256];
+    __shared__ TableStage st;
+    load_tab_smem(tab, ra[0].xv.tab);  // one exp table for the whole batch
+    for (int i = blockIdx.x; i < n; i += gridDim.x) {
+        const int2 e = list[i];
+        table_tile_t<D>(ra[e.x].xv, e.y, tab, st);
+    }
 }
 
-__global__ void __launch_bounds__(XDF_BLOCKOPS_T) blockops_batch(const RepArgs* ra)
+// Block operators of every replica, one block per (replica, diagonal block) pair of a flat list.
+__global__ void __launch_bounds__(XDF_BLOCKOPS_T) blockops_flat(const RepArgs* ra, const int2* list)
 {
-    const XView& v = ra[blockIdx.z].xv;
-    if (v.xi_zero) return;
-    blockops_body(v, -1, blockIdx.x);
+    const int2 e = list[blockIdx.x];
+    blockops_body(ra[e.x].xv, -1, e.y);
 }
+
 
 __global__ void __launch_bounds__(256) band_batch(const RepArgs* ra)
 {
@@ -1695,11 +1713,10 @@ __global__ void __launch_bounds__(256) finalize_batch(const RepArgs* ra)
     else finalize_body<3>(a.xv, a.fo);
 }
 
-// The batched exchange step as one persistent launch (work list in
-// pimd_batch.cuh).  A recursion item runs the self-contained solve of one
-// replica and direction (xsolo), reading tiles that other blocks wrote in
-// this launch through the async proxy, hence the proxy fence after the
-// acquire.
+// The recursion and band sums of the batched exchange step as one persistent
+// launch (work list in pimd_batch.cuh): recursion items (the self-contained
+// solve of one replica and direction, xsolo) longest first, then band items,
+// each waiting until both recursions of its replica are done.
 __global__ void __launch_bounds__(XDF_THREADS, 2) batch_exch_persistent(const RepArgs* ra, BatchSched sc)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1715,32 +1732,20 @@ __global__ void __launch_bounds__(XDF_THREADS, 2) batch_exch_persistent(const Re
         const XView& v = ra[it.r].xv;
         if (tid == 0) {
             int ok = 1;
-            if (it.type != BI_PREP) {
-                const int ph = it.type - 1;
-                ok = wait_flag(&sc.done[it.r * 4 + ph], sc.need[it.r * 4 + ph], sc.err, sc.spin_limit,
-                               0x900000 + (it.type << 16) + (it.r & 0xFFFF));
-            }
+            if (it.type == BI_BAND)
+                ok = wait_flag(&sc.done[it.r * 4 + BI_REC], sc.need[it.r * 4 + BI_REC], sc.err, sc.spin_limit,
+                               0x900000 + (it.r & 0xFFFF));
             s_ok = ok;
         }
         block_sync();
         if (s_ok) {
-            switch (it.type) {
-            case BI_PREP:
-                prep_body(v, 0, 1);
-                // the other prep partial slots of the replica (a: their count) hold zero
-                for (int q = 2 + tid; q < 2 * it.a; q += blockDim.x) v.lsum[q] = 0.0;
-                break;
-            case BI_TABLE: table_body(v, xdf_ntiles(v.nb, v.W, v.store), it.a, it.b); break;
-            case BI_BLOCKOPS: blockops_body(v, -1, it.a); break;
-            case BI_REC: {
-                asm volatile("fence.proxy.async.global;" ::: "memory");
+            if (it.type == BI_REC) {
                 DfwTile* T = reinterpret_cast<DfwTile*>(smem_raw);
                 SoloS* ss = reinterpret_cast<SoloS*>(smem_raw + XS_SLOTS * sizeof(DfwTile));
                 if (it.a == 0) xsolo<0>(v, T, ss);
                 else xsolo<1>(v, T, ss);
-                break;
-            }
-            default: band_body(v, it.a, it.b); break;
+            } else {
+                band_body(v, it.a, it.b);
             }
         }
         block_sync();
@@ -1949,16 +1954,14 @@ cudaError_t batch_launch_exchange(const RepArgs* ra, const BatchGrid& g, cudaStr
         if (r == cudaSuccess)
             r = cudaFuncSetAttribute(band_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)band_smem(8));
         if (r == cudaSuccess)
-            r = cudaFuncSetAttribute(blockops_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)blockops_smem());
+            r = cudaFuncSetAttribute(blockops_flat, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)blockops_smem());
         return r;
     });
     if (e != cudaSuccess) return e;
     prep_batch<<<dim3(g.gx_prep, 1, g.R), XDF_SMALL_T, 0, st>>>(ra);
     prof_mark(pm, "batch_exch_prep", st);
-    table_batch<<<dim3(g.gx_table, 1, g.R), 256, 0, st>>>(ra);
-    prof_mark(pm, "batch_exch_table", st);
-    blockops_batch<<<dim3(g.nb_max, 1, g.R), XDF_BLOCKOPS_T, blockops_smem(), st>>>(ra);
-    prof_mark(pm, "batch_exch_blockops", st);
+    e = batch_launch_tables_ops(ra, g, st, pm);
+    if (e != cudaSuccess) return e;
     xsolo_batch<<<dim3(2, g.R), XDF_THREADS, xsolo_smem(), st>>>(ra);
     prof_mark(pm, "batch_exch_recursion", st);
     band_batch<<<dim3(g.nb_max, 2, g.R), 256, band_smem(8), st>>>(ra);
@@ -1982,6 +1985,34 @@ cudaError_t batch_launch_exchange_persistent(const RepArgs* ra, const BatchSched
     });
     if (e != cudaSuccess) return e;
     batch_exch_persistent<<<blocks, XDF_THREADS, persistent_smem(), st>>>(ra, sc);
+    return cudaGetLastError();
+}
+
+// prep, factor tiles and block operators of every replica (flat lists, no idle blocks)
+cudaError_t batch_launch_prep_tables_ops(const RepArgs* ra, const BatchGrid& g, cudaStream_t st, ProfMarks* pm)
+{
+    static DeviceOnce attr_once;
+    cudaError_t e = device_once(attr_once, [] {
+        return cudaFuncSetAttribute(blockops_flat, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)blockops_smem());
+    });
+    if (e != cudaSuccess) return e;
+    prep_batch<<<dim3(g.gx_prep, 1, g.R), XDF_SMALL_T, 0, st>>>(ra);
+    prof_mark(pm, "batch_exch_prep", st);
+    e = batch_launch_tables_ops(ra, g, st, pm);
+    return e;
+}
+
+cudaError_t batch_launch_tables_ops(const RepArgs* ra, const BatchGrid& g, cudaStream_t st, ProfMarks* pm)
+{
+    if (g.n_tiles > 0) {
+        const int grid = std::min(g.n_tiles, 152 * 8);
+        if (g.d == 1) table_flat<1><<<grid, 256, 0, st>>>(ra, g.tiles, g.n_tiles);
+        else if (g.d == 2) table_flat<2><<<grid, 256, 0, st>>>(ra, g.tiles, g.n_tiles);
+        else table_flat<3><<<grid, 256, 0, st>>>(ra, g.tiles, g.n_tiles);
+    }
+    prof_mark(pm, "batch_exch_table", st);
+    if (g.n_blocks > 0) blockops_flat<<<g.n_blocks, XDF_BLOCKOPS_T, blockops_smem(), st>>>(ra, g.blocks);
+    prof_mark(pm, "batch_exch_blockops", st);
     return cudaGetLastError();
 }
 
