@@ -120,10 +120,13 @@ constexpr int EX_STREAMS = 4;
 
 // Workspace regions of the double-float exchange path.
 struct XLayout {
-    size_t ah, al, bh, bl, crh, crl, tab, M, G, Q, P, yh, yl, ye, ch, cl, ce, uh, ul,
+    size_t ah, al, bh, bl, crh, crl, tab, lnn, M, G, Q, P, yh, yl, ye, ch, cl, ce, uh, ul,
         wh, wl,
         parth, partl, parte, bandh, bandl, bande, flags, err, lsum, lam;
 };
+
+// entries of an ln n table that covers every row index of an N-particle exchange part
+static int ln_entries(int N) { return (N + 1 + 31) / 32 * 32; }
 
 void xdf_layout(Layout& L, XLayout& o, int N, int S, int W, int store)
 {
@@ -137,6 +140,7 @@ void xdf_layout(Layout& L, XLayout& o, int N, int S, int W, int store)
     o.crh = L.add(np * f);
     o.crl = L.add(np * f);
     o.tab = L.add(256 * sizeof(float2));
+    o.lnn = L.add(np * sizeof(double));
     o.M = L.add((size_t)nt * sizeof(XTile));
     o.G = L.add((size_t)nb * sizeof(XTile));
     o.Q = L.add((size_t)nb * sizeof(XTile));
@@ -157,7 +161,7 @@ void xdf_layout(Layout& L, XLayout& o, int N, int S, int W, int store)
     o.bandh = L.add((size_t)2 * nb * 32 * 4 * f);
     o.bandl = L.add((size_t)2 * nb * 32 * 4 * f);
     o.bande = L.add((size_t)2 * nb * 32 * i4);
-    o.flags = L.add((size_t)(2 * nb + 2 * nb * S) * i4);
+    o.flags = L.add((size_t)(2 * nb + 2 * nb * S + 1) * i4);  // chain, partial flags, band-item counter
     o.err = L.add(4 * i4);
     o.lsum = L.add((size_t)xdf_prep_blocks(np) * 2 * sizeof(double));
     o.lam = L.add(4 * sizeof(double));
@@ -189,6 +193,7 @@ XView xdf_view(char* base, const XLayout& o, int N, int P, int d, double beta, d
 #define XP(name, T) v.name = (T*)(base + o.name)
     XP(ah, float); XP(al, float); XP(bh, float); XP(bl, float); XP(crh, float); XP(crl, float);
     v.tab = (const float2*)(base + o.tab);
+    v.lnn = (const double*)(base + o.lnn);
     XP(M, XTile); XP(G, XTile); XP(Q, XTile); XP(P, XTile);
     XP(yh, float); XP(yl, float); XP(ye, int); XP(ch, float); XP(cl, float); XP(ce, int);
     XP(uh, float); XP(ul, float); XP(wh, float); XP(wl, float);
@@ -225,7 +230,7 @@ struct pimd_ctx {
     ExchLayout exs[PIMD_MAXSP];
     XLayout xls[PIMD_MAXSP];
     bool use_df = true;
-    size_t off_spr, off_pair, off_fin, off_md, off_sc, off_flag;
+    size_t off_lnn, off_spr, off_pair, off_fin, off_md, off_sc, off_flag;
     int n_help;
     int pair_t = 128;  // pair-kernel block size (pimd_autotune)
     int n_force = 0;   // force-worker blocks folded into the recursion launch (0: separate kernels)
@@ -374,6 +379,9 @@ static void ctx_layout(pimd_ctx* c)
 {
     c->L = Layout();
     c->use_df = c->cfg.exchange_arith == PIMD_XARITH_DF;
+    // ln n for every species, first so that its offset never moves (the
+    // autotuner re-lays the rest out for other band widths)
+    c->off_lnn = c->L.add((size_t)ln_entries(c->N) * sizeof(double));
     for (int sp = 0; sp < c->nsp; ++sp) {
         if (c->use_df)
             xdf_layout(c->L, c->xls[sp], c->sp_n[sp], EX_STREAMS, cfg_band(c->cfg), c->cfg.table_mode == PIMD_TABLE_STORE);
@@ -418,6 +426,7 @@ static void ctx_views(pimd_ctx* c)
                 c->xds[sp].err = c->xds[0].err;
                 c->xds[sp].tab = c->xds[0].tab;
             }
+            c->xds[sp].lnn = (const double*)((char*)b->work + c->off_lnn);
         } else {
             c->xvs[sp] = exch_view((char*)b->work, c->exs[sp], c->sp_n[sp], c->P, c->d, c->beta, c->xi, EX_STREAMS,
                                    c->cfg.table_mode == PIMD_TABLE_STORE, rP, r1, np, np, c->cfg.spin_limit, c->n_help);
@@ -646,7 +655,8 @@ extern "C" pimd_status pimd_bind(pimd_t c, const pimd_buffers* b, void* stream)
     if (e != cudaSuccess) return cuda_fail(c, e, "pimd_bind: error word reset");
     if (c->use_df) {
         e = xdf_upload_table((float2*)c->xds[0].tab, c->st);
-        if (e != cudaSuccess) return cuda_fail(c, e, "pimd_bind: exp table upload");
+        if (e == cudaSuccess) e = xdf_fill_lntab((double*)c->xds[0].lnn, ln_entries(c->N), c->st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "pimd_bind: exp and log table upload");
     }
     e = cudaMemsetAsync((char*)b->work + c->off_flag, 0, 4 * sizeof(int), c->st);
     if (e != cudaSuccess) return cuda_fail(c, e, "pimd_bind: flag reset");
@@ -1255,6 +1265,7 @@ extern "C" pimd_status pimd_vb_forward(pimd_vb_t h, const double* r1, const doub
                        h->n_help);
     cudaError_t e = cudaMemsetAsync(v.err, 0, sizeof(int), st);
     if (e == cudaSuccess) e = xdf_upload_table((float2*)v.tab, st);
+    if (e == cudaSuccess) e = xdf_fill_lntab((double*)v.lnn, v.npad, st);
     if (e == cudaSuccess) e = xdf_launch_forward(v, st, nullptr);
     if (e == cudaSuccess) e = xdf_launch_vb_value(v, V_out, st);
     if (e != cudaSuccess) return fail(nullptr, PIMD_ECUDA, std::string("pimd_vb_forward: ") + cudaGetErrorString(e));
@@ -1737,6 +1748,9 @@ extern "C" pimd_status pimd_batch_bind(pimd_batch_t b, const pimd_batch_buffers*
     if (e != cudaSuccess) return bcuda(b, e, "pimd_batch_bind: setup");
     pimd_status us = batch_upload_args(b);
     if (us != PIMD_OK) return us;
+    for (const auto& a : b->args)
+        if (e == cudaSuccess) e = xdf_fill_lntab((double*)a.xv.lnn, a.xv.npad, b->st);
+    if (e != cudaSuccess) return bcuda(b, e, "pimd_batch_bind: log tables");
     b->bound = true;
     b->steps = 0;
     pimd_status s = batch_enqueue_forces(b, b->st);

@@ -40,6 +40,64 @@ __device__ __forceinline__ double f2d_exact(float x)
     return __hiloint2double((int)hi, (int)(b << 29));
 }
 
+// FP64 <-> double-float on the integer pipe: the FP64 conversions and adds
+// run on the FP64 pipe, which on this part is the bottleneck of the
+// thermostat kernels, so both directions take the bit fields apart instead.
+// FP64 -> df: the high part is x with its significand truncated to 24 bits,
+// the low part the remaining 29 significand bits as a float (rounded to 24
+// bits: about 2^-47 relative overall).  Exponents outside [-70, 100] (and
+// zero, infinities, NaN) take the FP64 route.
+__device__ __forceinline__ df d2df(double x)
+{
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const int E = (int)((hi >> 20) & 0x7FFu) - 1023;
+    if (E < -70 || E > 100) {
+        const float h = d2f_trunc(x);
+        return df{h, d2f_trunc(x - (double)h)};
+    }
+    const unsigned sgn = hi & 0x80000000u;
+    const float h = __uint_as_float(sgn | ((unsigned)(E + 127) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
+    const float scale = __uint_as_float((unsigned)(E - 52 + 127) << 23);  // 2^(E-52), a normal float
+    const float l = __uint_as_float(__float_as_uint(__uint2float_rn(lo & 0x1FFFFFFFu) * scale) | sgn);
+    return df{h, l};
+}
+
+// df -> FP64: the 24-bit significand of h widened to 53 bits, the low part's
+// significand added (or subtracted) at its offset, one renormalising shift.
+// Bits of l below the FP64 unit are truncated (at most 2 ulp).  Parts outside
+// the normal range, or an l too large for a normalised pair, take the FP64
+// route.
+__device__ __forceinline__ double df2d(df a)
+{
+    const unsigned hb = __float_as_uint(a.h), lb = __float_as_uint(a.l);
+    const int Eh = (int)((hb >> 23) & 0xFFu) - 127;
+    const int El = (int)((lb >> 23) & 0xFFu) - 127;
+    const int sh = El - Eh + 29;  // offset of l's significand in units of 2^(Eh-52)
+    const bool l_zero = (lb & 0x7FFFFFFFu) == 0u;
+    if (Eh < -100 || Eh > 100 || (!l_zero && (El == -127 || sh > 6))) return (double)a.h + (double)a.l;
+    unsigned long long M = (unsigned long long)((hb & 0x7FFFFFu) | 0x800000u) << 29;
+    int E = Eh;
+    if (!l_zero && sh > -25) {
+        const unsigned long long ml = (lb & 0x7FFFFFu) | 0x800000u;
+        const unsigned long long L = sh >= 0 ? ml << sh : ml >> (-sh);
+        if ((hb ^ lb) & 0x80000000u) {
+            M -= L;
+            if (M < (1ull << 52)) {
+                M <<= 1;
+                E -= 1;
+            }
+        } else {
+            M += L;
+            if (M >= (1ull << 53)) {
+                M >>= 1;
+                E += 1;
+            }
+        }
+    }
+    const unsigned long long bits = ((unsigned long long)(hb & 0x80000000u) << 32) |
+                                    ((unsigned long long)(E + 1023) << 52) | (M & ((1ull << 52) - 1));
+    return __longlong_as_double((long long)bits);
+}
 // (a1) Internal ring-polymer springs (Sec. III interior-bead formula and the
 // within-particle half of the exterior-bead formulas): F_l^j = -k (2 r^j -
 // r^{j+1} - r^{j-1}), with the missing neighbour of beads 1 and P dropped.
@@ -236,8 +294,10 @@ struct ForceWork {
 // Shared-memory bytes a force worker needs (blockDim.x = 256 particles).
 constexpr int FW_SMEM = 16 + 96 * 8 + 3 * 256 * 8;
 
-template <int D, bool MIXED>
-__device__ void force_worker_t(const ForceWork& w, unsigned char* smem)
+// `between` runs before each unit is claimed (every thread of the block; it
+// may use the shared memory for other work and must leave it free).
+template <int D, bool MIXED, class Between>
+__device__ void force_worker_t(const ForceWork& w, unsigned char* smem, Between& between)
 {
     constexpr int PT = 256;
     int* su = reinterpret_cast<int*>(smem);
@@ -248,6 +308,7 @@ __device__ void force_worker_t(const ForceWork& w, unsigned char* smem)
     fs.accumulate = 0;
     fq.accumulate = 1;
     for (;;) {
+        between();
         if (threadIdx.x == 0) *su = atomicAdd(w.counter, 1);
         block_sync();
         const int u = *su;
@@ -257,13 +318,15 @@ __device__ void force_worker_t(const ForceWork& w, unsigned char* smem)
         springs_unit(w.b, fs, w.b.f, w.part_spr, bx, j, w.gx, red + 64);
         if (MIXED) pair_unit_f32<D, PT>(w.b, fq, w.b.f, w.part_pair, bx, j, w.gx, reinterpret_cast<float2*>(sx), red);
         else pair_unit_f64<D, PT>(w.b, fq, w.b.f, w.part_pair, bx, j, w.gx, reinterpret_cast<double*>(sx), red);
+        block_sync();  // the unit's shared memory is free for `between`
     }
 }
 
-__device__ __forceinline__ void force_worker(const ForceWork& w, unsigned char* smem)
+template <class Between>
+__device__ __forceinline__ void force_worker(const ForceWork& w, unsigned char* smem, Between& between)
 {
     const bool mixed = w.fp.mixed != 0;
-    if (w.b.d == 1) mixed ? force_worker_t<1, true>(w, smem) : force_worker_t<1, false>(w, smem);
-    else if (w.b.d == 2) mixed ? force_worker_t<2, true>(w, smem) : force_worker_t<2, false>(w, smem);
-    else mixed ? force_worker_t<3, true>(w, smem) : force_worker_t<3, false>(w, smem);
+    if (w.b.d == 1) mixed ? force_worker_t<1, true>(w, smem, between) : force_worker_t<1, false>(w, smem, between);
+    else if (w.b.d == 2) mixed ? force_worker_t<2, true>(w, smem, between) : force_worker_t<2, false>(w, smem, between);
+    else mixed ? force_worker_t<3, true>(w, smem, between) : force_worker_t<3, false>(w, smem, between);
 }

@@ -75,64 +75,6 @@ __global__ void __launch_bounds__(PT) pair_kernel_f32(BeadView b, ForceParams fp
 // momentum scaled by exp(-tau p_1/Q), positions eta += tau p_eta/Q, then the
 // links again in the opposite order.
 
-// FP64 <-> double-float on the integer pipe: the FP64 conversions and adds
-// run on the FP64 pipe, which on this part is the bottleneck of the
-// thermostat kernels, so both directions take the bit fields apart instead.
-// FP64 -> df: the high part is x with its significand truncated to 24 bits,
-// the low part the remaining 29 significand bits as a float (rounded to 24
-// bits: about 2^-47 relative overall).  Exponents outside [-70, 100] (and
-// zero, infinities, NaN) take the FP64 route.
-__device__ __forceinline__ df d2df(double x)
-{
-    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
-    const int E = (int)((hi >> 20) & 0x7FFu) - 1023;
-    if (E < -70 || E > 100) {
-        const float h = d2f_trunc(x);
-        return df{h, d2f_trunc(x - (double)h)};
-    }
-    const unsigned sgn = hi & 0x80000000u;
-    const float h = __uint_as_float(sgn | ((unsigned)(E + 127) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
-    const float scale = __uint_as_float((unsigned)(E - 52 + 127) << 23);  // 2^(E-52), a normal float
-    const float l = __uint_as_float(__float_as_uint(__uint2float_rn(lo & 0x1FFFFFFFu) * scale) | sgn);
-    return df{h, l};
-}
-
-// df -> FP64: the 24-bit significand of h widened to 53 bits, the low part's
-// significand added (or subtracted) at its offset, one renormalising shift.
-// Bits of l below the FP64 unit are truncated (at most 2 ulp).  Parts outside
-// the normal range, or an l too large for a normalised pair, take the FP64
-// route.
-__device__ __forceinline__ double df2d(df a)
-{
-    const unsigned hb = __float_as_uint(a.h), lb = __float_as_uint(a.l);
-    const int Eh = (int)((hb >> 23) & 0xFFu) - 127;
-    const int El = (int)((lb >> 23) & 0xFFu) - 127;
-    const int sh = El - Eh + 29;  // offset of l's significand in units of 2^(Eh-52)
-    const bool l_zero = (lb & 0x7FFFFFFFu) == 0u;
-    if (Eh < -100 || Eh > 100 || (!l_zero && (El == -127 || sh > 6))) return (double)a.h + (double)a.l;
-    unsigned long long M = (unsigned long long)((hb & 0x7FFFFFu) | 0x800000u) << 29;
-    int E = Eh;
-    if (!l_zero && sh > -25) {
-        const unsigned long long ml = (lb & 0x7FFFFFu) | 0x800000u;
-        const unsigned long long L = sh >= 0 ? ml << sh : ml >> (-sh);
-        if ((hb ^ lb) & 0x80000000u) {
-            M -= L;
-            if (M < (1ull << 52)) {
-                M <<= 1;
-                E -= 1;
-            }
-        } else {
-            M += L;
-            if (M >= (1ull << 53)) {
-                M >>= 1;
-                E += 1;
-            }
-        }
-    }
-    const unsigned long long bits = ((unsigned long long)(hb & 0x80000000u) << 32) |
-                                    ((unsigned long long)(E + 1023) << 52) | (M & ((1ull << 52) - 1));
-    return __longlong_as_double((long long)bits);
-}
 __device__ __forceinline__ df dfc(const float (&c)[2]) { return df{c[0], c[1]}; }
 
 // e^x for a double-float x, |x| <= 1/32: the Taylor series to x^4 in
@@ -244,48 +186,48 @@ __device__ __forceinline__ void nhc_half_step_f32(double& p, double (&eta)[M], d
     }
 }
 
+// One degree of freedom: row (slice j, component c) = blockIdx.y, particle
+// l = blockIdx.x * MD_T + threadIdx.x (a 2-D grid, so no index division).
 template <bool PRE, int M>
 __device__ __forceinline__ void md_body(const BeadView& b, const MDParams& mp)
 {
+    const int l = blockIdx.x * MD_T + threadIdx.x;
+    if (l >= b.N || (int)blockIdx.y >= b.P * b.d) return;
     const size_t stride = (size_t)b.P * b.d * b.ld;
-    const bool narrow = (stride >> 32) == 0;  // 32-bit remainder suffices
-    for (size_t o = (size_t)blockIdx.x * MD_T + threadIdx.x; o < stride; o += (size_t)gridDim.x * MD_T) {
-        const int l = narrow ? (int)((unsigned)o % (unsigned)b.ld) : (int)(o % b.ld);
-        if (l >= b.N) continue;
-        double p = b.p[o];
-        double eta[M], pe[M];
-        if (mp.thermostat) {
+    const size_t o = (size_t)blockIdx.y * b.ld + l;
+    double p = b.p[o];
+    double eta[M], pe[M];
+    if (mp.thermostat) {
 #pragma unroll
-            for (int k = 0; k < M; ++k) {
-                eta[k] = b.eta[k * stride + o];
-                pe[k] = b.peta[k * stride + o];
-            }
+        for (int k = 0; k < M; ++k) {
+            eta[k] = b.eta[k * stride + o];
+            pe[k] = b.peta[k * stride + o];
         }
-        if (PRE) {
-            if (mp.thermostat) {
-                if (mp.nhc_fp32)
-                    nhc_half_step_f32<M>(p, eta, pe, mp.f_inv_mass, mp.f_inv_Q, mp.f_kT, mp.f_half_dt);
-                else
-                    nhc_half_step<M>(p, eta, pe, mp.nc);
-            }
-            p += 0.5 * mp.dt * b.f[o];
-            b.r[o] = fma(mp.dt * mp.inv_mass, p, b.r[o]);
-        } else {
-            p += 0.5 * mp.dt * b.f[o];
-            if (mp.thermostat) {
-                if (mp.nhc_fp32)
-                    nhc_half_step_f32<M>(p, eta, pe, mp.f_inv_mass, mp.f_inv_Q, mp.f_kT, mp.f_half_dt);
-                else
-                    nhc_half_step<M>(p, eta, pe, mp.nc);
-            }
-        }
-        b.p[o] = p;
+    }
+    if (PRE) {
         if (mp.thermostat) {
+            if (mp.nhc_fp32)
+                nhc_half_step_f32<M>(p, eta, pe, mp.f_inv_mass, mp.f_inv_Q, mp.f_kT, mp.f_half_dt);
+            else
+                nhc_half_step<M>(p, eta, pe, mp.nc);
+        }
+        p += 0.5 * mp.dt * b.f[o];
+        b.r[o] = fma(mp.dt * mp.inv_mass, p, b.r[o]);
+    } else {
+        p += 0.5 * mp.dt * b.f[o];
+        if (mp.thermostat) {
+            if (mp.nhc_fp32)
+                nhc_half_step_f32<M>(p, eta, pe, mp.f_inv_mass, mp.f_inv_Q, mp.f_kT, mp.f_half_dt);
+            else
+                nhc_half_step<M>(p, eta, pe, mp.nc);
+        }
+    }
+    b.p[o] = p;
+    if (mp.thermostat) {
 #pragma unroll
-            for (int k = 0; k < M; ++k) {
-                b.eta[k * stride + o] = eta[k];
-                b.peta[k * stride + o] = pe[k];
-            }
+        for (int k = 0; k < M; ++k) {
+            b.eta[k * stride + o] = eta[k];
+            b.peta[k * stride + o] = pe[k];
         }
     }
 }
@@ -461,6 +403,8 @@ int md_blocks(int N, int P, int d)
     long long b = (n + MD_T - 1) / MD_T;
     return (int)(b < 152 * 8 ? b : 152 * 8);
 }
+// grid of the per-degree-of-freedom kernels: particles in x, (slice, component) rows in y
+static dim3 md_grid(int N, int P, int d) { return dim3((N + MD_T - 1) / MD_T, P * d); }
 
 cudaError_t launch_springs(const BeadView& b, const ForceParams& fp, double* f_out, double* part, cudaStream_t st)
 {
@@ -494,7 +438,7 @@ cudaError_t launch_pair(const BeadView& b, const ForceParams& fp, double* f_out,
 template <bool PRE>
 static cudaError_t launch_md(const BeadView& b, const MDParams& mp, cudaStream_t st)
 {
-    const int g = md_blocks(b.N, b.P, b.d);
+    const dim3 g = md_grid(b.N, b.P, b.d);
     switch (b.M) {
     case 1: md_kernel<PRE, 1><<<g, MD_T, 0, st>>>(b, mp); break;
     case 2: md_kernel<PRE, 2><<<g, MD_T, 0, st>>>(b, mp); break;
@@ -650,7 +594,7 @@ int batch_md_blocks(int nmax, int P, int d) { return (int)(((long long)nmax * P 
 cudaError_t batch_launch_md(const RepArgs* ra, const BatchGrid& g, bool pre, cudaStream_t st)
 {
     const int M = g.M;
-    const dim3 grid(g.gx_md, 1, g.R);
+    const dim3 grid((g.nb_max * 32 + MD_T - 1) / MD_T, g.P * g.d, g.R);  // covers the largest replica
 #define PIMD_MDB(m)                                                         \
     case m:                                                                 \
         if (pre) md_batch<true, m><<<grid, MD_T, 0, st>>>(ra);              \

@@ -198,17 +198,37 @@ __device__ __forceinline__ dfw dfw_sum8(const dfw (&t)[8], int n)
     return dfw_sum_k<8>(t);
 }
 
-// (A B)[r][c] over t in [t0, t1)
-__device__ __forceinline__ dfw dot_mat(const DfwTile* A, const DfwTile* B, int r, int c, int t0, int t1)
+// (A B)[r][c] over t in [t0, t1), both multiples of 8, in one pass: each
+// 8-term chunk's largest exponent rescales the running sum as in dot_seg.
+// Zero entries (exponent WEF_ZERO_E) add nothing, so the range may cover them.
+__device__ __forceinline__ dfw dot_mat8(const DfwTile* A, const DfwTile* B, int r, int c, int t0, int t1)
 {
     int E = WEF_ZERO_E;
-    for (int t = t0; t < t1; ++t) E = max(E, A->e[RIDX(r, t)] + B->e[RIDX(t, c)]);
-    if (E <= WEF_ZERO_E / 2) return dfw_zero();
     df s = df{0.f, 0.f};
-    for (int t = t0; t < t1; ++t) {
-        const int qa = RIDX(r, t), qb = RIDX(t, c);
-        acc_term(s, A->h[qa], A->l[qa], B->h[qb], B->l[qb], pow2f(A->e[qa] + B->e[qb] - E));
+    for (int tc = t0; tc < t1; tc += 8) {
+        float ah[8], al[8], bh[8], bl[8];
+        int k[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int qa = RIDX(r, tc + u), qb = RIDX(tc + u, c);
+            ah[u] = A->h[qa];
+            al[u] = A->l[qa];
+            bh[u] = B->h[qb];
+            bl[u] = B->l[qb];
+            k[u] = A->e[qa] + B->e[qb];
+        }
+        int Ec = k[0];
+#pragma unroll
+        for (int u = 1; u < 8; ++u) Ec = max(Ec, k[u]);
+        const int En = max(E, Ec);
+        const float g = pow2f(E - En);
+        s.h = __fmul_rn(s.h, g);
+        s.l = __fmul_rn(s.l, g);
+        E = En;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc_term(s, ah[u], al[u], bh[u], bl[u], pow2f(k[u] - E));
     }
+    if (E <= WEF_ZERO_E / 2) return dfw_zero();
     return dfw_norm(fast_two_sum(s.h, s.l), E);
 }
 
@@ -375,6 +395,9 @@ __device__ __forceinline__ void load_tab_smem(float2* tab_s, const float2* tab)
 // prep: double-float endpoints, row constants, link energy, flags
 
 // (bx, gx): this block's index and the number of blocks sharing the work.
+// FP64 -> double-float splits run on the integer pipe (d2df) and ln n comes
+// from the workspace table, so the FP64 pipe does only the squared
+// distances and the sums.
 __device__ __forceinline__ void prep_body(const XView& v, int bx, int gx)
 {
     __shared__ double red[64];
@@ -383,8 +406,8 @@ __device__ __forceinline__ void prep_body(const XView& v, int bx, int gx)
         for (int c = 0; c < 3; ++c) {
             df a = df{0.f, 0.f}, b = df{0.f, 0.f};
             if (c < v.d && q < v.N) {
-                a = df_from_double(v.a[(size_t)c * v.lda + q]);
-                b = df_from_double(v.b[(size_t)c * v.ldb + q]);
+                a = d2df(v.a[(size_t)c * v.lda + q]);
+                b = d2df(v.b[(size_t)c * v.ldb + q]);
             }
             v.ah[(size_t)c * v.npad + q] = a.h;
             v.al[(size_t)c * v.npad + q] = a.l;
@@ -400,8 +423,7 @@ __device__ __forceinline__ void prep_body(const XView& v, int bx, int gx)
                     const double x = v.a[(size_t)c * v.lda + q - 1] - v.b[(size_t)c * v.ldb + q];
                     gl = fma(x, x, gl);
                 }
-            gl *= v.kappa;
-            cr = df_from_double(gl - log((double)q) - v.log_xi);
+            cr = d2df(fma(gl, v.kappa, -v.lnn[q]) - v.log_xi);
         }
         v.crh[q] = cr.h;
         v.crl[q] = cr.l;
@@ -415,13 +437,11 @@ __device__ __forceinline__ void prep_body(const XView& v, int bx, int gx)
                 const double y = v.a[(size_t)c * v.lda + q] - v.b[(size_t)c * v.ldb + q];
                 gd = fma(y, y, gd);
             }
-            gl *= v.kappa;
-            gd *= v.kappa;
-            acc[0] += gl;
-            if (v.xi_zero) acc[1] += gl - log((double)(q + 1)) - gd;
+            acc[0] = fma(gl, v.kappa, acc[0]);
+            if (v.xi_zero) acc[1] += v.kappa * (gl - gd) - v.lnn[q + 1];
         }
     }
-    const int nflags = 2 * v.nb + 2 * v.nb * v.S;
+    const int nflags = 2 * v.nb + 2 * v.nb * v.S + 1;  // chain, partial flags, band-item counter
     for (int j = bx * blockDim.x + threadIdx.x; j < nflags; j += gx * blockDim.x) v.flags[j] = 0;
     block_reduce<2>(acc, red);
     if (threadIdx.x == 0) {
@@ -553,19 +573,36 @@ __device__ __forceinline__ void blockops_body(const XView& v, int part, int J)
     block_sync();
     // G = (I - L)^{-1} by forward substitution, one column per warp (lane =
     // row; 32 warps, all columns at once): after step t, lane t holds its
-    // final G[t][c], which is broadcast and applied to the rows below.
+    // final G[t][c], which is broadcast and applied to the rows below.  Every
+    // entry is non-negative, so each lane keeps a compensated sum s relative
+    // to a running exponent E (s >= 1 once non-zero, far from the FP32 limits)
+    // and adds one term per step; the raw (s, E) of lane t is what is broadcast.
     for (int c = w; c < 32; c += blockDim.x >> 5) {
-        dfw acc = (lane == c) ? dfw{1.f, 0.f, 0} : dfw_zero();
+        df s = (lane == c) ? df{1.f, 0.f} : df{0.f, 0.f};
+        int E = (lane == c) ? 0 : WEF_ZERO_E;
         for (int t = c; t < 31; ++t) {
-            dfw gt;
-            gt.h = __shfl_sync(0xffffffffu, acc.h, t);
-            gt.l = __shfl_sync(0xffffffffu, acc.l, t);
-            gt.e = __shfl_sync(0xffffffffu, acc.e, t);
-            if (lane > t) acc = dfw_add(acc, dfw_mul(tile_get(L, lane, t), gt));
+            const float gh = __shfl_sync(0xffffffffu, s.h, t);
+            const float gl = __shfl_sync(0xffffffffu, s.l, t);
+            const int ge = __shfl_sync(0xffffffffu, E, t);
+            if (lane > t) {
+                const int q = RIDX(lane, t);
+                const int k = L->e[q] + ge;
+                if (k > E) {
+                    const float f = pow2f(E - k);
+                    s.h = __fmul_rn(s.h, f);
+                    s.l = __fmul_rn(s.l, f);
+                    E = k;
+                }
+                acc_term(s, L->h[q], L->l[q], gh, gl, pow2f(k - E));
+            }
         }
-        tile_put(G, lane, c, (lane >= c) ? acc : dfw_zero());
+        const dfw g = (lane >= c && E > WEF_ZERO_E / 2) ? dfw_norm(fast_two_sum(s.h, s.l), E) : dfw_zero();
+        tile_put(G, lane, c, g);
     }
     block_sync();
+    // Q = G M_{J,J-1} (G lower triangular: t <= r, r uniform over a warp) and
+    // P = M_{J+1,J} G (all t; the zeros of G add nothing, and every lane runs
+    // the same range)
     for (int q = threadIdx.x; q < 1024; q += blockDim.x) {
         const int r = q >> 5, c = q & 31, o = RIDX(r, c);
         if (part != 1) {
@@ -573,14 +610,14 @@ __device__ __forceinline__ void blockops_body(const XView& v, int part, int J)
             v.G[J].l[o] = G->l[o];
             v.G[J].e[o] = G->e[o];
             dfw Q = dfw_zero();
-            if (J >= 1) Q = dot_mat(G, Ms, r, c, 0, r + 1);
+            if (J >= 1) Q = dot_mat8(G, Ms, r, c, 0, (r + 8) & ~7);
             v.Q[J].h[o] = Q.h;
             v.Q[J].l[o] = Q.l;
             v.Q[J].e[o] = Q.e;
         }
         if (part != 0) {
             dfw Pm = dfw_zero();
-            if (J + 1 < v.nb) Pm = dot_mat(Mp, G, r, c, c, 32);
+            if (J + 1 < v.nb) Pm = dot_mat8(Mp, G, r, c, 0, 32);
             v.P[J].h[o] = Pm.h;
             v.P[J].l[o] = Pm.l;
             v.P[J].e[o] = Pm.e;
@@ -1274,6 +1311,9 @@ __device__ void xhelper(const XView& v, DfwTile* T, WeightSmem* Ws, ChainS* cs, 
     }
 }
 
+__device__ void band_worker(const XView& v);
+__device__ void band_try(const XView& v);
+
 __global__ void __launch_bounds__(XDF_THREADS, 1) xdf_recursion_kernel(XView v, ForceWork fw)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1288,14 +1328,24 @@ __global__ void __launch_bounds__(XDF_THREADS, 1) xdf_recursion_kernel(XView v, 
     const int bid = blockIdx.x;
     if (bid == 0) xchain<0>(v, T, cs);
     else if (bid == 1) xchain<1>(v, T, cs);
-    else if (bid - 2 < v.n_help_f) xhelper<0>(v, T, Ws, cs, tab, bid - 2);
-    else if (bid - 2 - v.n_help_f < v.n_help_b) xhelper<1>(v, T, Ws, cs, tab, bid - 2 - v.n_help_f);
-    else force_worker(fw, smem_raw);
+    else {
+        if (bid - 2 < v.n_help_f) xhelper<0>(v, T, Ws, cs, tab, bid - 2);
+        else if (bid - 2 - v.n_help_f < v.n_help_b) xhelper<1>(v, T, Ws, cs, tab, bid - 2 - v.n_help_f);
+        else {
+            // between force units, a band item whose inputs are published
+            auto ready_band = [&v]() { band_try(v); };
+            force_worker(fw, smem_raw, ready_band);
+        }
+        block_sync();
+        band_worker(v);
+    }
 }
 
 // Band sums: forward row block J over tiles I in [J-W+1, J]; backward column
-// block I over row blocks [I, I+W-1].  Warp w takes tiles m = w, w + nw, ...
-// (nw = warps of the block) and the warps' sums are merged in warp order.
+// block I over row blocks [I, I+W-1].  The W tiles are cut into W H ranges of
+// 32/H columns (forward) or rows (backward), H the largest power of two with
+// W H <= nw (nw = warps of the block, at least 1); warp w takes ranges w,
+// w + nw, ... and the warps' sums are merged in warp order.
 __device__ __forceinline__ void band_body(const XView& v, int blk, int dir)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1305,8 +1355,12 @@ __device__ __forceinline__ void band_body(const XView& v, int blk, int dir)
     DVAcc* hm = reinterpret_cast<DVAcc*>(smem_raw + nw * (sizeof(DfwTile) + sizeof(WeightSmem)));
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (blk >= v.nb) return;  // a block past this replica's blocks
+    int H = 1;
+    while (H < 32 && v.W * 2 * H <= nw) H *= 2;
+    const int span = 32 / H;
     DVAcc a = dv_zero();
-    for (int m = w; m < v.W; m += nw) {
+    for (int u = w; u < v.W * H; u += nw) {
+        const int m = u / H, t0 = (u % H) * span;
         const int J = dir == 0 ? blk : blk + m, I = dir == 0 ? blk - m : blk;
         if (I < 0 || J >= v.nb) continue;
         fetch_tile_warp(v, &T[w], J, I, lane);
@@ -1315,45 +1369,119 @@ __device__ __forceinline__ void band_body(const XView& v, int blk, int dir)
         else load_wb(v, &Ws[w], J, lane);
         cp_wait<0>();
         __syncwarp();
-        dv_add(a, dir == 0 ? weighted_rows(&T[w], &Ws[w], lane, v.d) : weighted_cols(&T[w], &Ws[w], lane, v.d));
+        dv_add(a, dir == 0 ? weighted_rows(&T[w], &Ws[w], lane, v.d, t0, t0 + span)
+                           : weighted_cols(&T[w], &Ws[w], lane, v.d, t0, t0 + span));
         __syncwarp();
     }
+    // the block's helper partials join the band sum here (warp w adds
+    // partials w, w + nw, ...), so the endpoint forces read one sum per row and
+    // column; they were all released before the chain formed this block, whose
+    // flag the caller waited for.  Then a tree over the warps.
+    const int ns = dir == 0 ? min(v.S, blk - v.W + 1) : min(v.S, v.nb - blk - v.W);
+    for (int k = w; k < ns; k += nw) dv_add(a, load_dv(v.parth, v.partl, v.parte, xpart_index(v, dir, blk, k, lane)));
     hm[w * 32 + lane] = a;
     block_sync();
-    if (w == 0) {
-        DVAcc t = dv_zero();
-        for (int q = 0; q < nw; ++q) dv_add(t, hm[q * 32 + lane]);
-        store_dv(v.bandh, v.bandl, v.bande, xband_index(v, dir, blk, lane), t);
+    for (int h = 1; h < nw; h <<= 1) {
+        if ((w & (2 * h - 1)) == 0 && w + h < nw) {
+            DVAcc t = hm[w * 32 + lane];
+            dv_add(t, hm[(w + h) * 32 + lane]);
+            hm[w * 32 + lane] = t;
+        }
+        block_sync();
+    }
+    if (w == 0) store_dv(v.bandh, v.bandl, v.bande, xband_index(v, dir, blk, lane), hm[lane]);
+}
+
+// Band sums inside the recursion launch: a force-worker block runs a band
+// item whose inputs are already published between two force units
+// (band_try); once its own work is done, a helper or force-worker block takes
+// band items from the same counter, in the order the two
+// chains publish their inputs (item u: direction u & 1, the (u >> 1)-th block
+// of that chain), and starts each as soon as the chain flag of the item's
+// last input block is set (forward row block J needs y up to block J,
+// backward column block I needs c down to block I).  A wait that gives up
+// ends the loop; the error word already holds the reason.
+__device__ void band_worker(const XView& v)
+{
+    __shared__ int s_item;
+    int* ctr = v.flags + 2 * v.nb + 2 * v.nb * v.S;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int u = atomicAdd(ctr, 1);
+            if (u < 2 * v.nb) {
+                const int dir = u & 1, blk = dir == 0 ? (u >> 1) : v.nb - 1 - (u >> 1);
+                if (!wait_flag(v.flags + dir * v.nb + blk, 1, v.err, v.spin_limit, 0x5b0000 + u)) u = 2 * v.nb;
+            }
+            s_item = u;
+        }
+        block_sync();
+        const int u = s_item;
+        if (u >= 2 * v.nb) break;
+        const int dir = u & 1, blk = dir == 0 ? (u >> 1) : v.nb - 1 - (u >> 1);
+        band_body(v, blk, dir);
+        block_sync();  // shared memory and s_item are reused by the next item
     }
 }
 
-__global__ void __launch_bounds__(256) xdf_band_kernel(XView v) { band_body(v, blockIdx.x, blockIdx.y); }
+// The next band item if its inputs are already published (no wait): claimed
+// only by moving the counter from that item, so an item is never skipped.
+__device__ void band_try(const XView& v)
+{
+    __shared__ int s_item;
+    int* ctr = v.flags + 2 * v.nb + 2 * v.nb * v.S;
+    if (threadIdx.x == 0) {
+        int got = -1;
+        const int u = *(volatile int*)ctr;
+        if (u < 2 * v.nb) {
+            const int dir = u & 1, blk = dir == 0 ? (u >> 1) : v.nb - 1 - (u >> 1);
+            if (ld_acquire(v.flags + dir * v.nb + blk) >= 1 && atomicCAS(ctr, u, u + 1) == u) got = u;
+        }
+        s_item = got;
+    }
+    block_sync();
+    const int u = s_item;
+    if (u < 0) return;
+    band_body(v, (u & 1) == 0 ? (u >> 1) : v.nb - 1 - (u >> 1), u & 1);
+    block_sync();
+}
 
 __device__ __forceinline__ dfw xget(const float* h, const float* l, const int* e, int i) { return dfw{h[i], l[i], e[i]}; }
 
-// Sum of the ns helper partials and the band partial of row (dir 0) or
-// column (dir 1) `lane` of block `blk`: all loads issued first, then a tree
-// of additions.
-__device__ __forceinline__ DVAcc sum_partials(const XView& v, int dir, int blk, int lane, int ns)
+
+// x * 2^e as FP64 for a double-float x of any sign: the significand is built
+// on the integer pipe (df2d) and e added into the exponent field while the
+// result stays a normal double; zero, non-finite and out-of-range results
+// take FP64 multiplications.
+__device__ __forceinline__ double df_scaled_to_double(df x, int e)
 {
-    DVAcc q[XDF_MAXS + 1];
-#pragma unroll
-    for (int t = 0; t < XDF_MAXS; ++t)
-        q[t] = (t < ns) ? load_dv(v.parth, v.partl, v.parte, xpart_index(v, dir, blk, t, lane)) : dv_zero();
-    q[XDF_MAXS] = load_dv(v.bandh, v.bandl, v.bande, xband_index(v, dir, blk, lane));
-#pragma unroll
-    for (int h = 1; h <= XDF_MAXS; h <<= 1)
-#pragma unroll
-        for (int t = 0; t + h <= XDF_MAXS; t += 2 * h) dv_add(q[t], q[t + h]);
-    return q[0];
+    const double m = df2d(x);
+    const long long bits = __double_as_longlong(m);
+    const int E = (int)((bits >> 52) & 0x7FF);
+    if (E > 0 && E < 0x7FF && E + e > 0 && E + e < 0x7FF) return __longlong_as_double(bits + ((long long)e << 52));
+    if (m == 0.0 || E == 0x7FF) return m;
+    if (e > 2000) return m * INFINITY;
+    if (e < -2200) return m * 0.0;
+    const int e1 = e / 2;
+    return (m * pow2i(e1)) * pow2i(e - e1);
 }
 
+__device__ __forceinline__ double dfw_value(dfw a) { return df_scaled_to_double(df{a.h, a.l}, a.e); }
+
+// a.v[c] * 2^a.e * scale, the product formed in double-float
 __device__ __forceinline__ double dv_comp(const DVAcc& a, int c, dfw scale)
 {
-    // a.v[c] * 2^a.e * scale
-    dfw s = scale;
-    s.e += a.e;
-    return df_to_double(a.v[c]) * dfw_to_double(s);
+    return df_scaled_to_double(df_mul(a.v[c], df{scale.h, scale.l}), a.e + scale.e);
+}
+
+// 1 / Z for a non-zero dfw Z: the FP32 reciprocal of the high part refined by
+// one Newton step in double-float (r + r (1 - z r)), about 2^-47 relative.
+__device__ __forceinline__ dfw dfw_recip(dfw z)
+{
+    const float r0 = __frcp_rn(z.h);
+    const df t = df_mul(df{z.h, z.l}, df{r0, 0.f});
+    const df e1 = df_sub(df{1.f, 0.f}, t);
+    const df r = df_add(df{r0, 0.f}, df_mul(df{r0, 0.f}, e1));
+    return dfw_norm(r, -z.e);
 }
 
 // Endpoint forces (Sec. III exterior-bead formulas, factorised form).  D is
@@ -1378,10 +1506,9 @@ __device__ __forceinline__ void finalize_body(const XView& v, const FinalizeOut&
         const int Jk = l >> 5, rk = l & 31;
         DVAcc R = dv_zero(), C = dv_zero();
         if (!v.xi_zero) {
-            // every partial of the row (then of the column) is loaded before
-            // any is added, so the loads overlap
-            R = sum_partials(v, 0, Jn, rn, min(v.S, Jn - v.W + 1));
-            C = sum_partials(v, 1, Jk, rk, min(v.S, v.nb - Jk - v.W));
+            // the band sums hold the helper partials too (band_body)
+            R = load_dv(v.bandh, v.bandl, v.bande, xband_index(v, 0, Jn, rn));
+            C = load_dv(v.bandh, v.bandl, v.bande, xband_index(v, 1, Jk, rk));
         }
         {
             double a[D], b[D];
@@ -1398,13 +1525,11 @@ __device__ __forceinline__ void finalize_body(const XView& v, const FinalizeOut&
                 }
                 link = linkin = 0.0;
             } else {
-                const dfw Z = xget(v.yh, v.yl, v.ye, v.N);
-                const double zm = df_to_double(df{Z.h, Z.l});
-                const dfw iZ = dfw_norm(df_from_double(1.0 / zm), -Z.e);
+                const dfw iZ = dfw_recip(xget(v.yh, v.yl, v.ye, v.N));
                 const dfw yn = xget(v.yh, v.yl, v.ye, n), cn = xget(v.ch, v.cl, v.ce, n);
                 const dfw yl = xget(v.yh, v.yl, v.ye, l), cl = xget(v.ch, v.cl, v.ce, l);
-                rowtot = dfw_to_double(dfw_mul(dfw_mul(yn, cn), iZ));
-                coltot = dfw_to_double(dfw_mul(dfw_mul(yl, cl), iZ));
+                rowtot = dfw_value(dfw_mul(dfw_mul(yn, cn), iZ));
+                coltot = dfw_value(dfw_mul(dfw_mul(yl, cl), iZ));
                 const dfw fr = dfw_mul(cn, iZ), fc = dfw_mul(yl, iZ);
                 for (int c = 0; c < D; ++c) {
                     PB[c] = dv_comp(R, c, fr);
@@ -1885,8 +2010,6 @@ cudaError_t xdf_launch_forward(const XView& v, cudaStream_t st, ProfMarks* pm, c
         if (r == cudaSuccess)
             r = cudaFuncSetAttribute(xdf_recursion_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)xdf_recursion_smem(XDF_MAXW));
-        if (r == cudaSuccess)
-            r = cudaFuncSetAttribute(xdf_band_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)band_smem(8));
         return r;
     });
     if (e != cudaSuccess) return e;
@@ -1895,6 +2018,8 @@ cudaError_t xdf_launch_forward(const XView& v, cudaStream_t st, ProfMarks* pm, c
     prof_mark(pm, "exch_blockops", st);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    // the helper and force-worker blocks form the band sums at their end
+    if (band_smem(8) > xdf_recursion_smem(v.W) || v.n_help_f + v.n_help_b < 1) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
     ForceWork none;
     memset(&none, 0, sizeof none);
@@ -1915,14 +2040,26 @@ cudaError_t xdf_launch_forward(const XView& v, cudaStream_t st, ProfMarks* pm, c
 
 cudaError_t xdf_launch_adjoint(const XView& v, const FinalizeOut& o, cudaStream_t st, ProfMarks* pm)
 {
-    if (!v.xi_zero) {
-        xdf_band_kernel<<<dim3(v.nb, 2), 32 * v.W, band_smem(v.W), st>>>(v);
-        prof_mark(pm, "exch_band", st);
-    }
+    // the band sums were formed inside the recursion launch (band_worker)
     if (v.d == 1) xdf_finalize_kernel<1><<<xdf_finalize_blocks(v.N), XDF_FIN_T, 0, st>>>(v, o);
     else if (v.d == 2) xdf_finalize_kernel<2><<<xdf_finalize_blocks(v.N), XDF_FIN_T, 0, st>>>(v, o);
     else xdf_finalize_kernel<3><<<xdf_finalize_blocks(v.N), XDF_FIN_T, 0, st>>>(v, o);
     prof_mark(pm, "exch_finalize", st);
+    return cudaGetLastError();
+}
+
+static __global__ void xdf_lntab_kernel(double* lnn, int n)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n) lnn[q] = q >= 1 ? log((double)q) : 0.0;
+}
+
+// ln n for n < npad (entry 0 is 0), once per workspace: the row constants
+// need ln n every step.
+cudaError_t xdf_fill_lntab(double* dev_lnn, int npad, cudaStream_t st)
+{
+    if (npad < 1) return cudaSuccess;
+    xdf_lntab_kernel<<<(npad + 255) / 256, 256, 0, st>>>(dev_lnn, npad);
     return cudaGetLastError();
 }
 

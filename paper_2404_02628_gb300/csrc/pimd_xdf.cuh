@@ -56,6 +56,7 @@ struct XView {
     float* bh; float* bl;        // [3][npad] b_k in double-float
     float* crh; float* crl;      // [npad] row constants c_n
     const float2* tab;           // [256] 2^(j/256) as double-floats
+    const double* lnn;           // [npad] ln n (entry 0 unused), filled once per workspace
     XTile* M;                    // factor tiles, index xdf_tile_index
     XTile* G;                    // [nb] (I - M_JJ)^{-1}
     XTile* Q;                    // [nb] G_J M_{J,J-1}
@@ -89,6 +90,7 @@ int xdf_prep_blocks(int npad);
 int xdf_finalize_blocks(int N);
 size_t xdf_recursion_smem(int W);
 cudaError_t xdf_upload_table(float2* dev_table, cudaStream_t st);
+cudaError_t xdf_fill_lntab(double* dev_lnn, int npad, cudaStream_t st);
 struct ForceWork;
 // fw (nullable) with n_force > 0 folds the springs and trap + pair forces into
 // the recursion launch as n_force extra blocks.
