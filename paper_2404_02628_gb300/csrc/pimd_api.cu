@@ -158,9 +158,9 @@ void xdf_layout(Layout& L, XLayout& o, int N, int S, int W, int store)
     o.parth = L.add((size_t)2 * nb * S * 32 * 4 * f);
     o.partl = L.add((size_t)2 * nb * S * 32 * 4 * f);
     o.parte = L.add((size_t)2 * nb * S * 32 * i4);
-    o.bandh = L.add((size_t)2 * nb * 32 * 4 * f);
-    o.bandl = L.add((size_t)2 * nb * 32 * 4 * f);
-    o.bande = L.add((size_t)2 * nb * 32 * i4);
+    o.bandh = L.add((size_t)4 * nb * 32 * 4 * f);  // band sums, then diagonal-tile sums
+    o.bandl = L.add((size_t)4 * nb * 32 * 4 * f);
+    o.bande = L.add((size_t)4 * nb * 32 * i4);
     o.flags = L.add((size_t)(2 * nb + 2 * nb * S + 1) * i4);  // chain, partial flags, band-item counter
     o.err = L.add(4 * i4);
     o.lsum = L.add((size_t)xdf_prep_blocks(np) * 2 * sizeof(double));

@@ -276,6 +276,135 @@ __device__ __forceinline__ void pair_unit_f32(const BeadView& b, const ForcePara
     }
 }
 
+// Block-wide sums of NV double-float values per thread on the FP32 pipe (the
+// FP64 pipe of this part is slow); the totals, as FP64, in `out` of thread 0.
+// red: 2 * 32 * NV floats.
+template <int NV>
+__device__ __forceinline__ void block_reduce_df(df (&v)[NV], float* red, double (&out)[NV])
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; ++q)
+        for (int o = 16; o > 0; o >>= 1)
+            v[q] = df_add(v[q], df{__shfl_down_sync(0xffffffffu, v[q].h, o), __shfl_down_sync(0xffffffffu, v[q].l, o)});
+    block_sync();
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            red[2 * (w * NV + q)] = v[q].h;
+            red[2 * (w * NV + q) + 1] = v[q].l;
+        }
+    block_sync();
+    if (w == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            df t = lane < nw ? df{red[2 * (lane * NV + q)], red[2 * (lane * NV + q) + 1]} : df{0.f, 0.f};
+            for (int o = 16; o > 0; o >>= 1)
+                t = df_add(t, df{__shfl_down_sync(0xffffffffu, t.h, o), __shfl_down_sync(0xffffffffu, t.l, o)});
+            if (lane == 0) out[q] = df2d(t);
+        }
+    }
+    block_sync();
+}
+
+// (a1) + (a4) in mixed precision for one (slice j, particle block bx) unit,
+// PT = blockDim.x particles: the springs and the trap + pair forces are summed
+// in FP32 and stored once (overwriting F); the slice's spring energy (FP64
+// differences, double-float squares and sums) and its trap + pair energy and
+// virial (FP32 per particle, double-float sums) go to part_spr[j gx + bx] and
+// part_pair[2 (j gx + bx)].  Same forces and energies as springs_unit followed
+// by pair_unit_f32, with one FP32 rounding more on the force and no FP64
+// arithmetic beyond one difference per coordinate.
+template <int D, int PT>
+__device__ __forceinline__ void force_unit_mixed(const BeadView& b, const ForceParams& fp, double* f, double* part_spr,
+                                                 double* part_pair, int bx, int j, int gx, float2* sx, float* red)
+{
+    const int slot = j * gx + bx;
+    if (bx * PT >= b.N) {  // a block past this replica's particles
+        if (threadIdx.x == 0) {
+            part_spr[slot] = 0.0;
+            part_pair[2 * slot + 0] = 0.0;
+            part_pair[2 * slot + 1] = 0.0;
+        }
+        return;
+    }
+    const int i = bx * PT + threadIdx.x;
+    const size_t row = (size_t)D * b.ld;
+    const double* rs = b.r + (size_t)j * row;
+    const float sc = fp.sc32, ks = (float)fp.ks;
+    float xf[D], fs[D];
+    float2 xi[D], g[D];
+    df es = df{0.f, 0.f};
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        xf[c] = 0.f;
+        fs[c] = 0.f;
+        if (i < b.N) {
+            const double* p = rs + (size_t)c * b.ld + i;
+            const double x = *p;
+            const double xm = (j > 0) ? p[-(ptrdiff_t)row] : x;
+            const double xp = (j < b.P - 1) ? p[row] : x;
+            xf[c] = d2f_trunc(x);
+            fs[c] = -ks * ((xf[c] - d2f_trunc(xm)) + (xf[c] - d2f_trunc(xp)));
+            if (j < b.P - 1) {
+                const df dd = d2df(xp - x);
+                es = df_add(es, df_mul(dd, dd));
+            }
+        }
+        const float xs = xf[c] * sc;
+        xi[c] = make_float2(xs, xs);
+        g[c] = make_float2(0.f, 0.f);
+    }
+    float2 esum = make_float2(0.f, 0.f);
+    if (fp.A != 0.0) {
+        for (int k0 = 0; k0 < b.N; k0 += PT) {
+            const int k = k0 + threadIdx.x;
+            float* sxf = reinterpret_cast<float*>(sx);
+#pragma unroll
+            for (int c = 0; c < D; ++c)
+                sxf[c * PT + threadIdx.x] = (k < b.N) ? -d2f_trunc(rs[(size_t)c * b.ld + k]) * sc : -1.0e18f;
+            __syncthreads();
+#pragma unroll 4
+            for (int kk = 0; kk < PT / 2; ++kk) {
+                float2 dx[D];
+#pragma unroll
+                for (int c = 0; c < D; ++c) dx[c] = __fadd2_rn(xi[c], sx[c * (PT / 2) + kk]);
+                float2 q2 = __fmul2_rn(dx[0], dx[0]);
+#pragma unroll
+                for (int c = 1; c < D; ++c) q2 = __ffma2_rn(dx[c], dx[c], q2);
+                const float2 ee = make_float2(ex2_approx(-q2.x), ex2_approx(-q2.y));
+                esum = __fadd2_rn(esum, ee);
+#pragma unroll
+                for (int c = 0; c < D; ++c) g[c] = __ffma2_rn(ee, dx[c], g[c]);
+            }
+            __syncthreads();
+        }
+    }
+    df v[3] = {es, df{0.f, 0.f}, df{0.f, 0.f}};
+    if (i < b.N) {
+        const float cpair = (float)fp.cpair32, om2 = (float)fp.omega2, mip = -(float)fp.inv_P;
+        float t2 = 0.f, vir = 0.f;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            const float grad = fmaf(om2, xf[c], cpair * (g[c].x + g[c].y));
+            f[((size_t)j * D + c) * b.ld + i] = f2d_exact(fmaf(grad, mip, fs[c]));
+            t2 = fmaf(xf[c], xf[c], t2);
+            vir = fmaf(xf[c], grad, vir);
+        }
+        // the k == i term contributed exp(0) = 1 and no force
+        const float es2 = fp.A != 0.0 ? (esum.x - 1.0f) + esum.y : 0.f;
+        v[1] = df{fmaf(0.5f * om2, t2, 0.5f * (float)fp.A * es2), 0.f};
+        v[2] = df{vir, 0.f};
+    }
+    double out[3];
+    block_reduce_df<3>(v, red, out);
+    if (threadIdx.x == 0) {
+        part_spr[slot] = 0.5 * fp.ks * out[0];
+        part_pair[2 * slot + 0] = out[1];
+        part_pair[2 * slot + 1] = out[2];
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Force work folded into the persistent exchange launch: the blocks after the
 // chain and helper blocks take (slice, particle-block) units from a counter
@@ -315,9 +444,13 @@ __device__ void force_worker_t(const ForceWork& w, unsigned char* smem, Between&
         block_sync();  // every thread has the unit before thread 0 takes the next
         if (u >= nu) break;
         const int j = u / w.gx, bx = u % w.gx;
-        springs_unit(w.b, fs, w.b.f, w.part_spr, bx, j, w.gx, red + 64);
-        if (MIXED) pair_unit_f32<D, PT>(w.b, fq, w.b.f, w.part_pair, bx, j, w.gx, reinterpret_cast<float2*>(sx), red);
-        else pair_unit_f64<D, PT>(w.b, fq, w.b.f, w.part_pair, bx, j, w.gx, reinterpret_cast<double*>(sx), red);
+        if (MIXED) {
+            force_unit_mixed<D, PT>(w.b, w.fp, w.b.f, w.part_spr, w.part_pair, bx, j, w.gx, reinterpret_cast<float2*>(sx),
+                                    reinterpret_cast<float*>(red));
+        } else {
+            springs_unit(w.b, fs, w.b.f, w.part_spr, bx, j, w.gx, red + 64);
+            pair_unit_f64<D, PT>(w.b, fq, w.b.f, w.part_pair, bx, j, w.gx, reinterpret_cast<double*>(sx), red);
+        }
         block_sync();  // the unit's shared memory is free for `between`
     }
 }

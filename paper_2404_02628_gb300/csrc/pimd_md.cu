@@ -358,12 +358,16 @@ __global__ void __launch_bounds__(PT) force_units_batch(const RepArgs* ra, Force
         }
         const RepArgs& a = ra[lo];
         const int gxr = (a.bv.N + PT - 1) / PT, k = u - fu.prefix[lo], j = k / gxr, bx = k - j * gxr;
-        ForceParams fs = a.fp, fq = a.fp;
-        fs.accumulate = 0;
-        fq.accumulate = 1;
-        springs_unit(a.bv, fs, a.bv.f, a.part_spr, bx, j, fu.gx, red + 64);
-        if (MIXED) pair_unit_f32<D, PT>(a.bv, fq, a.bv.f, a.part_pair, bx, j, fu.gx, reinterpret_cast<float2*>(sx), red);
-        else pair_unit_f64<D, PT>(a.bv, fq, a.bv.f, a.part_pair, bx, j, fu.gx, reinterpret_cast<double*>(sx), red);
+        if (MIXED) {
+            force_unit_mixed<D, PT>(a.bv, a.fp, a.bv.f, a.part_spr, a.part_pair, bx, j, fu.gx,
+                                    reinterpret_cast<float2*>(sx), reinterpret_cast<float*>(red));
+        } else {
+            ForceParams fs = a.fp, fq = a.fp;
+            fs.accumulate = 0;
+            fq.accumulate = 1;
+            springs_unit(a.bv, fs, a.bv.f, a.part_spr, bx, j, fu.gx, red + 64);
+            pair_unit_f64<D, PT>(a.bv, fq, a.bv.f, a.part_pair, bx, j, fu.gx, reinterpret_cast<double*>(sx), red);
+        }
         __syncthreads();  // shared scratch is reused by the next unit
     }
 }

@@ -365,6 +365,11 @@ __device__ __forceinline__ size_t xband_index(const XView& v, int dir, int blk, 
 {
     return (((size_t)dir * v.nb + blk) << 5) + lane;
 }
+// the diagonal tile's sums (with the helper partials) sit after the band sums
+__device__ __forceinline__ size_t xdiag_index(const XView& v, int dir, int blk, int lane)
+{
+    return (((size_t)(2 + dir) * v.nb + blk) << 5) + lane;
+}
 
 __device__ __forceinline__ void store_dv(float* h, float* l, int* e, size_t idx, const DVAcc& a)
 {
@@ -1299,10 +1304,17 @@ __device__ void xhelper(const XView& v, DfwTile* T, WeightSmem* Ws, ChainS* cs, 
             cs->u.hm[w][lane] = run_to_dv(ra);
             block_sync();
             if (cs->abort) return;  // every thread reads it after the barrier
+            // tree over the warps' sums (three levels), then warp 0 publishes
+            for (int hs = 1; hs < XDF_WARPS; hs <<= 1) {
+                if ((w & (2 * hs - 1)) == 0) {
+                    DVAcc t = cs->u.hm[w][lane];
+                    dv_add(t, cs->u.hm[w + hs][lane]);
+                    cs->u.hm[w][lane] = t;
+                }
+                block_sync();
+            }
             if (w == 0) {
-                DVAcc t = dv_zero();
-                for (int q2 = 0; q2 < XDF_WARPS; ++q2) dv_add(t, cs->u.hm[q2][lane]);
-                store_dv(v.parth, v.partl, v.parte, xpart_index(v, DIR, B, si, lane), t);
+                store_dv(v.parth, v.partl, v.parte, xpart_index(v, DIR, B, si, lane), cs->u.hm[0][lane]);
                 __syncwarp();
                 if (lane == 0) st_release(&flag_part[B * v.S + si], 1);
             }
@@ -1342,43 +1354,74 @@ __global__ void __launch_bounds__(XDF_THREADS, 1) xdf_recursion_kernel(XView v, 
 }
 
 // Band sums: forward row block J over tiles I in [J-W+1, J]; backward column
-// block I over row blocks [I, I+W-1].  The W tiles are cut into W H ranges of
-// 32/H columns (forward) or rows (backward), H the largest power of two with
-// W H <= nw (nw = warps of the block, at least 1); warp w takes ranges w,
-// w + nw, ... and the warps' sums are merged in warp order.
-__device__ __forceinline__ void band_body(const XView& v, int blk, int dir)
+// block I over row blocks [I, I+W-1], in two parts:
+//   kind 0  the off-diagonal tiles (forward I < J, backward J > I), into the
+//           band sums;
+//   kind 1  the diagonal tile and the block's helper partials, into the
+//           diagonal sums (the endpoint forces add the two);
+//   kind -1 all tiles and partials into the band sums, the diagonal sums zero.
+// The part's nt tiles are cut into nt H ranges of 32/H columns (forward) or
+// rows (backward), H the largest power of two with nt H <= nw (nw = warps of
+// the block); warp w takes ranges w, w + nw, ... and warp w adds helper
+// partials w, w + nw, ...; a tree over the warps merges their sums.  With
+// `wait` set, the first tiles are copied before thread 0 waits (bounded) for
+// that flag, and the weights are read after it; false if the wait gave up.
+__device__ __forceinline__ bool band_body(const XView& v, int blk, int dir, int kind, const int* wait = nullptr,
+                                          int code = 0)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_ok;
     const int nw = blockDim.x >> 5;
     DfwTile* T = reinterpret_cast<DfwTile*>(smem_raw);
     WeightSmem* Ws = reinterpret_cast<WeightSmem*>(smem_raw + nw * sizeof(DfwTile));
     DVAcc* hm = reinterpret_cast<DVAcc*>(smem_raw + nw * (sizeof(DfwTile) + sizeof(WeightSmem)));
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (blk >= v.nb) return;  // a block past this replica's blocks
+    if (blk >= v.nb) return true;  // a block past this replica's blocks
+    const int m0 = kind == 0 ? 1 : 0, nt = (kind == 1 ? 1 : v.W) - m0;
     int H = 1;
-    while (H < 32 && v.W * 2 * H <= nw) H *= 2;
-    const int span = 32 / H;
-    DVAcc a = dv_zero();
-    for (int u = w; u < v.W * H; u += nw) {
-        const int m = u / H, t0 = (u % H) * span;
-        const int J = dir == 0 ? blk : blk + m, I = dir == 0 ? blk - m : blk;
-        if (I < 0 || J >= v.nb) continue;
+    while (H < 32 && nt * 2 * H <= nw) H *= 2;
+    const int span = 32 / H, nu = nt * H;
+    int J = 0, I = 0, t0 = 0;
+    auto fetch = [&](int u) {
+        const int m = m0 + u / H;
+        t0 = (u % H) * span;
+        J = dir == 0 ? blk : blk + m;
+        I = dir == 0 ? blk - m : blk;
+        if (I < 0 || J >= v.nb) return false;
         fetch_tile_warp(v, &T[w], J, I, lane);
         cp_commit();
-        if (dir == 0) load_wf(v, &Ws[w], I, lane);
-        else load_wb(v, &Ws[w], J, lane);
-        cp_wait<0>();
-        __syncwarp();
-        dv_add(a, dir == 0 ? weighted_rows(&T[w], &Ws[w], lane, v.d, t0, t0 + span)
-                           : weighted_cols(&T[w], &Ws[w], lane, v.d, t0, t0 + span));
-        __syncwarp();
+        return true;
+    };
+    bool have = w < nu && fetch(w);
+    if (wait) {
+        if (threadIdx.x == 0) s_ok = wait_flag(wait, 1, v.err, v.spin_limit, code);
+        block_sync();
+        if (!s_ok) {
+            cp_wait<0>();  // the copies land before the shared memory is reused
+            return false;
+        }
     }
-    // the block's helper partials join the band sum here (warp w adds
-    // partials w, w + nw, ...), so the endpoint forces read one sum per row and
-    // column; they were all released before the chain formed this block, whose
-    // flag the caller waited for.  Then a tree over the warps.
-    const int ns = dir == 0 ? min(v.S, blk - v.W + 1) : min(v.S, v.nb - blk - v.W);
-    for (int k = w; k < ns; k += nw) dv_add(a, load_dv(v.parth, v.partl, v.parte, xpart_index(v, dir, blk, k, lane)));
+    DVAcc a = dv_zero();
+    for (int u = w; u < nu;) {
+        if (have) {
+            if (dir == 0) load_wf(v, &Ws[w], I, lane);
+            else load_wb(v, &Ws[w], J, lane);
+            cp_wait<0>();
+            __syncwarp();
+            dv_add(a, dir == 0 ? weighted_rows(&T[w], &Ws[w], lane, v.d, t0, t0 + span)
+                               : weighted_cols(&T[w], &Ws[w], lane, v.d, t0, t0 + span));
+            __syncwarp();
+        }
+        u += nw;
+        have = u < nu && fetch(u);
+    }
+    // the helper partials of the block were all released before the chain
+    // formed the block, whose flag the caller waited for
+    if (kind != 0) {
+        const int ns = dir == 0 ? min(v.S, blk - v.W + 1) : min(v.S, v.nb - blk - v.W);
+        for (int k = w; k < ns; k += nw)
+            dv_add(a, load_dv(v.parth, v.partl, v.parte, xpart_index(v, dir, blk, k, lane)));
+    }
     hm[w * 32 + lane] = a;
     block_sync();
     for (int h = 1; h < nw; h <<= 1) {
@@ -1389,37 +1432,53 @@ __device__ __forceinline__ void band_body(const XView& v, int blk, int dir)
         }
         block_sync();
     }
-    if (w == 0) store_dv(v.bandh, v.bandl, v.bande, xband_index(v, dir, blk, lane), hm[lane]);
+    if (w == 0) {
+        const size_t bi = xband_index(v, dir, blk, lane), di = xdiag_index(v, dir, blk, lane);
+        store_dv(v.bandh, v.bandl, v.bande, kind == 1 ? di : bi, hm[lane]);
+        if (kind == -1) store_dv(v.bandh, v.bandl, v.bande, di, dv_zero());
+    }
+    return true;
+}
+
+// Band items of the recursion launch, four per chain step it: forward and
+// backward off-diagonal parts of the step's blocks (ready once the chain has
+// published the block before), then their diagonal parts (ready once the
+// block itself is published).  Their readiness is non-decreasing in u.
+struct BandItem {
+    int blk, dir, kind;
+    const int* flag;  // chain flag to wait for (null: none)
+};
+__device__ __forceinline__ BandItem band_item(const XView& v, int u)
+{
+    BandItem b;
+    const int it = u >> 2;
+    b.dir = u & 1;
+    b.kind = (u >> 1) & 1;
+    b.blk = b.dir == 0 ? it : v.nb - 1 - it;
+    const int src = b.kind == 1 ? b.blk : (b.dir == 0 ? b.blk - 1 : b.blk + 1);
+    b.flag = (src >= 0 && src < v.nb) ? v.flags + b.dir * v.nb + src : nullptr;
+    return b;
 }
 
 // Band sums inside the recursion launch: a force-worker block runs a band
 // item whose inputs are already published between two force units
 // (band_try); once its own work is done, a helper or force-worker block takes
-// band items from the same counter, in the order the two
-// chains publish their inputs (item u: direction u & 1, the (u >> 1)-th block
-// of that chain), and starts each as soon as the chain flag of the item's
-// last input block is set (forward row block J needs y up to block J,
-// backward column block I needs c down to block I).  A wait that gives up
-// ends the loop; the error word already holds the reason.
+// band items from the same counter in order, copying the item's tiles before
+// waiting for its chain flag.  A wait that gives up ends the loop; the error
+// word already holds the reason.
 __device__ void band_worker(const XView& v)
 {
     __shared__ int s_item;
     int* ctr = v.flags + 2 * v.nb + 2 * v.nb * v.S;
     for (;;) {
-        if (threadIdx.x == 0) {
-            int u = atomicAdd(ctr, 1);
-            if (u < 2 * v.nb) {
-                const int dir = u & 1, blk = dir == 0 ? (u >> 1) : v.nb - 1 - (u >> 1);
-                if (!wait_flag(v.flags + dir * v.nb + blk, 1, v.err, v.spin_limit, 0x5b0000 + u)) u = 2 * v.nb;
-            }
-            s_item = u;
-        }
+        if (threadIdx.x == 0) s_item = atomicAdd(ctr, 1);
         block_sync();
         const int u = s_item;
-        if (u >= 2 * v.nb) break;
-        const int dir = u & 1, blk = dir == 0 ? (u >> 1) : v.nb - 1 - (u >> 1);
-        band_body(v, blk, dir);
+        if (u >= 4 * v.nb) break;
+        const BandItem b = band_item(v, u);
+        const bool ok = band_body(v, b.blk, b.dir, b.kind, b.flag, 0x5b0000 + u);
         block_sync();  // shared memory and s_item are reused by the next item
+        if (!ok) break;
     }
 }
 
@@ -1432,16 +1491,17 @@ __device__ void band_try(const XView& v)
     if (threadIdx.x == 0) {
         int got = -1;
         const int u = *(volatile int*)ctr;
-        if (u < 2 * v.nb) {
-            const int dir = u & 1, blk = dir == 0 ? (u >> 1) : v.nb - 1 - (u >> 1);
-            if (ld_acquire(v.flags + dir * v.nb + blk) >= 1 && atomicCAS(ctr, u, u + 1) == u) got = u;
+        if (u < 4 * v.nb) {
+            const BandItem b = band_item(v, u);
+            if ((!b.flag || ld_acquire(b.flag) >= 1) && atomicCAS(ctr, u, u + 1) == u) got = u;
         }
         s_item = got;
     }
     block_sync();
     const int u = s_item;
     if (u < 0) return;
-    band_body(v, (u & 1) == 0 ? (u >> 1) : v.nb - 1 - (u >> 1), u & 1);
+    const BandItem b = band_item(v, u);
+    band_body(v, b.blk, b.dir, b.kind);
     block_sync();
 }
 
@@ -1506,9 +1566,11 @@ __device__ __forceinline__ void finalize_body(const XView& v, const FinalizeOut&
         const int Jk = l >> 5, rk = l & 31;
         DVAcc R = dv_zero(), C = dv_zero();
         if (!v.xi_zero) {
-            // the band sums hold the helper partials too (band_body)
+            // band and diagonal sums (with the helper partials, band_body)
             R = load_dv(v.bandh, v.bandl, v.bande, xband_index(v, 0, Jn, rn));
             C = load_dv(v.bandh, v.bandl, v.bande, xband_index(v, 1, Jk, rk));
+            dv_add(R, load_dv(v.bandh, v.bandl, v.bande, xdiag_index(v, 0, Jn, rn)));
+            dv_add(C, load_dv(v.bandh, v.bandl, v.bande, xdiag_index(v, 1, Jk, rk)));
         }
         {
             double a[D], b[D];
@@ -1827,7 +1889,7 @@ __global__ void __launch_bounds__(256) band_batch(const RepArgs* ra)
 {
     const XView& v = ra[blockIdx.z].xv;
     if (v.xi_zero) return;
-    band_body(v, blockIdx.x, blockIdx.y);
+    band_body(v, blockIdx.x, blockIdx.y, -1);
 }
 
 __global__ void __launch_bounds__(256) finalize_batch(const RepArgs* ra)
@@ -1870,7 +1932,7 @@ __global__ void __launch_bounds__(XDF_THREADS, 2) batch_exch_persistent(const Re
                 if (it.a == 0) xsolo<0>(v, T, ss);
                 else xsolo<1>(v, T, ss);
             } else {
-                band_body(v, it.a, it.b);
+                band_body(v, it.a, it.b, -1);
             }
         }
         block_sync();

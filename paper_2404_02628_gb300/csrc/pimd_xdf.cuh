@@ -66,7 +66,7 @@ struct XView {
     float* uh; float* ul;            // [3][npad] y[k] b_k (mantissa of y times b_k), published with y
     float* wh; float* wl;            // [3][npad] c[n] a_{n-1}, published with c
     float* parth; float* partl; int* parte;  // helper partials [2][nb][S][32] x 4 / x 1
-    float* bandh; float* bandl; int* bande;  // band sums [2][nb][32] x 4 / x 1
+    float* bandh; float* bandl; int* bande;  // band sums [2][nb][32], then diagonal-tile sums [2][nb][32]; x 4 / x 1
     int* flags;                  // [2][nb] chain flags, then [2][nb][S] partial flags
     int* err;
     int spin_limit;
