@@ -232,8 +232,11 @@ __device__ __forceinline__ void pair_unit_f32(const BeadView& b, const ForcePara
             for (int c = 0; c < D; ++c)
                 sxf[c * PT + threadIdx.x] = (k < b.N) ? -d2f_trunc(rs[(size_t)c * b.ld + k]) * sc : -1.0e18f;
             __syncthreads();
+            // partner pairs holding at least one particle (the padding past N
+            // sits at -1e18 and adds exp2(-inf) = 0)
+            const int nkk = (min(PT, b.N - k0) + 1) >> 1;
 #pragma unroll 4
-            for (int kk = 0; kk < PT / 2; ++kk) {
+            for (int kk = 0; kk < nkk; ++kk) {
                 float2 dx[D];
 #pragma unroll
                 for (int c = 0; c < D; ++c) dx[c] = __fadd2_rn(xi[c], sx[c * (PT / 2) + kk]);
@@ -364,8 +367,11 @@ __device__ __forceinline__ void force_unit_mixed(const BeadView& b, const ForceP
             for (int c = 0; c < D; ++c)
                 sxf[c * PT + threadIdx.x] = (k < b.N) ? -d2f_trunc(rs[(size_t)c * b.ld + k]) * sc : -1.0e18f;
             __syncthreads();
+            // partner pairs holding at least one particle (the padding past N
+            // sits at -1e18 and adds exp2(-inf) = 0)
+            const int nkk = (min(PT, b.N - k0) + 1) >> 1;
 #pragma unroll 4
-            for (int kk = 0; kk < PT / 2; ++kk) {
+            for (int kk = 0; kk < nkk; ++kk) {
                 float2 dx[D];
 #pragma unroll
                 for (int c = 0; c < D; ++c) dx[c] = __fadd2_rn(xi[c], sx[c * (PT / 2) + kk]);

@@ -670,6 +670,13 @@ struct ChainS {
     unsigned long long mb_set[XDF_NSETS];       // tile-set arrival (bulk copies)
 };
 
+// the recursion block's dynamic shared memory (tiles, weight slots, chain or
+// helper state, exp table) plus its static variables fit the 227 KB opt-in
+static_assert(XDF_TILES * sizeof(DfwTile) + XDF_WSLOTS * sizeof(WeightSmem) + sizeof(ChainS) + 16 +
+                      256 * sizeof(float2) + 64 <=
+                  232448,
+              "recursion block shared memory");
+
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void mbar_init(unsigned long long* mb, int count)
