@@ -1514,6 +1514,24 @@ __device__ void band_try(const XView& v)
 
 __device__ __forceinline__ dfw xget(const float* h, const float* l, const int* e, int i) { return dfw{h[i], l[i], e[i]}; }
 
+// ln of a positive dfw, m 2^e with m = h + l in [1, 2): x0 = ln h in FP32,
+// then one step of Newton's iteration for e^x = m taken to second order,
+// ln m = x0 + t - t^2/2 with t = m e^{-x0} - 1 (|t| < 2^-20, so the neglected
+// t^3/3 is below 2^-60), e^{-x0} by dfw_exp_core; FP64 only for the final
+// e ln 2 + ln m.  The FP64 library logarithm costs microseconds of the FP64
+// pipe on this part.
+__device__ __forceinline__ double dfw_log_df(dfw a, const float2* tab)
+{
+    if (!(a.h > 0.0f)) return a.h == 0.0f ? -INFINITY : dfw_to_double(a);
+    const float x0 = logf(a.h);
+    const dfw ex = dfw_exp_core(df{-x0, 0.0f}, tab);
+    const df p = df_scale(df_mul(df{a.h, a.l}, df{ex.h, ex.l}), pow2f(ex.e));
+    const df t = df_sub(p, df{1.0f, 0.0f});
+    const df lm = df_add(df{x0, 0.0f}, df_add(t, df{-0.5f * t.h * t.h, 0.0f}));
+    const double ln2 = 0.6931471805599453;
+    return fma((double)a.e, ln2, df_to_double(lm));
+}
+
 
 // x * 2^e as FP64 for a double-float x of any sign: the significand is built
 // on the integer pipe (df2d) and e added into the exponent field while the
@@ -1559,13 +1577,12 @@ __device__ __forceinline__ void finalize_body(const XView& v, const FinalizeOut&
     __shared__ double red[32];
     double esum[1] = {0.0};
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
-    if (blockIdx.x == 0 && threadIdx.x == 0 && v.lam) {
-        if (v.xi_zero) {
-            v.lam[0] = v.lam[1] = 0.0;
-        } else {
-            v.lam[0] = v.N * v.log_xi + dfw_log(xget(v.yh, v.yl, v.ye, v.N));
-            v.lam[1] = v.N * v.log_xi + dfw_log(xget(v.ch, v.cl, v.ce, 0));
-        }
+    // ln Z of both directions, each on the first thread of its own block (the
+    // FP64 logarithm is long on this part), the last block taking the second
+    if (threadIdx.x == 0 && v.lam && (blockIdx.x == 0 || blockIdx.x == gridDim.x - 1)) {
+        if (blockIdx.x == 0) v.lam[0] = v.xi_zero ? 0.0 : v.N * v.log_xi + dfw_log_df(xget(v.yh, v.yl, v.ye, v.N), v.tab);
+        if (blockIdx.x == gridDim.x - 1)
+            v.lam[1] = v.xi_zero ? 0.0 : v.N * v.log_xi + dfw_log_df(xget(v.ch, v.cl, v.ce, 0), v.tab);
     }
     if (l < v.N) {
         const int n = l + 1;  // row of bead P of particle l
@@ -1966,7 +1983,7 @@ __global__ void xdf_vb_value_kernel(XView v, int nprep, double* V_out)
         gl += v.lsum[2 * i];
         l0 += v.lsum[2 * i + 1];
     }
-    const double lam = v.xi_zero ? l0 : v.N * v.log_xi + dfw_log(xget(v.yh, v.yl, v.ye, v.N));
+    const double lam = v.xi_zero ? l0 : v.N * v.log_xi + dfw_log_df(xget(v.yh, v.yl, v.ye, v.N), v.tab);
     *V_out = (gl - lam) / v.beta;
 }
 
