@@ -28,16 +28,25 @@ __device__ __forceinline__ float d2f_trunc(double x)
     return __uint_as_float(b);
 }
 
-// float -> double on the integer pipe (exact): exponent rebiased, significand
-// shifted into place.  Zero, subnormal, infinite and NaN inputs take the
-// hardware conversion.
+// float -> double on the integer pipe (exact), every case by bit
+// manipulation so that no FP64-pipe conversion is ever issued (a predicated
+// one would be, in every thread): the exponent rebiased and the significand
+// shifted into place; zero keeps its sign, a subnormal is normalised with a
+// leading-zero count, infinities and NaN keep an all-ones exponent.
 __device__ __forceinline__ double f2d_exact(float x)
 {
     const unsigned b = __float_as_uint(x);
-    const unsigned e = (b >> 23) & 0xFFu;
-    if (e == 0u || e == 0xFFu) return (double)x;
-    const unsigned hi = (b & 0x80000000u) | ((e - 127u + 1023u) << 20) | ((b & 0x7FFFFFu) >> 3);
-    return __hiloint2double((int)hi, (int)(b << 29));
+    const unsigned sgn = b & 0x80000000u, e = (b >> 23) & 0xFFu, m = b & 0x7FFFFFu;
+    unsigned hi = sgn | ((e - 127u + 1023u) << 20) | (m >> 3), lo = m << 29;
+    if (e == 0xFFu) hi = sgn | 0x7FF00000u | (m >> 3);
+    if (e == 0u) {
+        // m 2^-149: the highest set bit s of m becomes the implicit one
+        const int s = 31 - __clz(m | 1u);
+        const unsigned long long f = ((unsigned long long)(m ^ (1u << s))) << (52 - s);
+        hi = m == 0u ? sgn : (sgn | ((unsigned)(s + 874) << 20) | (unsigned)(f >> 32));
+        lo = m == 0u ? 0u : (unsigned)f;
+    }
+    return __hiloint2double((int)hi, (int)lo);
 }
 
 // FP64 <-> double-float on the integer pipe: the FP64 conversions and adds
@@ -47,14 +56,20 @@ __device__ __forceinline__ double f2d_exact(float x)
 // the low part the remaining 29 significand bits as a float (rounded to 24
 // bits: about 2^-47 relative overall).  Exponents outside [-70, 100] (and
 // zero, infinities, NaN) take the FP64 route.
+// The rare wide-range cases of d2df / df2d on the FP64 pipe, out of line so
+// that the common path never issues them as predicated instructions.
+static __device__ __noinline__ df d2df_wide(double x)
+{
+    const float h = d2f_trunc(x);
+    return df{h, d2f_trunc(x - (double)h)};
+}
+static __device__ __noinline__ double df2d_wide(df a) { return (double)a.h + (double)a.l; }
+
 __device__ __forceinline__ df d2df(double x)
 {
     const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
     const int E = (int)((hi >> 20) & 0x7FFu) - 1023;
-    if (E < -70 || E > 100) {
-        const float h = d2f_trunc(x);
-        return df{h, d2f_trunc(x - (double)h)};
-    }
+    if (E < -70 || E > 100) return d2df_wide(x);
     const unsigned sgn = hi & 0x80000000u;
     const float h = __uint_as_float(sgn | ((unsigned)(E + 127) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
     const float scale = __uint_as_float((unsigned)(E - 52 + 127) << 23);  // 2^(E-52), a normal float
@@ -74,7 +89,7 @@ __device__ __forceinline__ double df2d(df a)
     const int El = (int)((lb >> 23) & 0xFFu) - 127;
     const int sh = El - Eh + 29;  // offset of l's significand in units of 2^(Eh-52)
     const bool l_zero = (lb & 0x7FFFFFFFu) == 0u;
-    if (Eh < -100 || Eh > 100 || (!l_zero && (El == -127 || sh > 6))) return (double)a.h + (double)a.l;
+    if (Eh < -100 || Eh > 100 || (!l_zero && (El == -127 || sh > 6))) return df2d_wide(a);
     unsigned long long M = (unsigned long long)((hb & 0x7FFFFFu) | 0x800000u) << 29;
     int E = Eh;
     if (!l_zero && sh > -25) {

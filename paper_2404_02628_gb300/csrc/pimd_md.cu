@@ -211,10 +211,10 @@ __device__ __forceinline__ void md_body(const BeadView& b, const MDParams& mp)
             else
                 nhc_half_step<M>(p, eta, pe, mp.nc);
         }
-        p += 0.5 * mp.dt * b.f[o];
-        b.r[o] = fma(mp.dt * mp.inv_mass, p, b.r[o]);
+        p = fma(mp.half_dt, b.f[o], p);
+        b.r[o] = fma(mp.dt_inv_mass, p, b.r[o]);
     } else {
-        p += 0.5 * mp.dt * b.f[o];
+        p = fma(mp.half_dt, b.f[o], p);
         if (mp.thermostat) {
             if (mp.nhc_fp32)
                 nhc_half_step_f32<M>(p, eta, pe, mp.f_inv_mass, mp.f_inv_Q, mp.f_kT, mp.f_half_dt);
@@ -684,6 +684,8 @@ static void split_df(double x, float (&out)[2])
 
 void nhc_constants(MDParams& mp)
 {
+    mp.half_dt = 0.5 * mp.dt;
+    mp.dt_inv_mass = mp.dt * mp.inv_mass;
     const double tau = 0.5 * mp.dt;
     split_df(mp.inv_mass, mp.nc.inv_m);
     split_df(mp.inv_Q, mp.nc.inv_Q);

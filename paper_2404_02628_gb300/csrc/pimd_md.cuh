@@ -41,6 +41,7 @@ struct NhcConst {
 struct MDParams {
     double dt, mass, Q, kT;
     double inv_mass, inv_Q;   // 1/mass and 1/Q, formed on the host
+    double half_dt, dt_inv_mass;  // dt/2 and dt/mass, formed on the host (nhc_constants)
     int thermostat;
     int nhc_fp32;             // thermostat chain arithmetic in FP32
     float f_inv_mass, f_inv_Q, f_kT, f_half_dt;  // FP32 copies for that mode
