@@ -700,6 +700,9 @@ class System:
         pimd_autotune(self.h, cache_path)
         return pimd_tuning(self.h)
 
+    def tuning(self):
+        return pimd_tuning(self.h)
+
     def estimators(self):
         return pimd_estimators(self.h)
 

@@ -630,6 +630,84 @@ __device__ __forceinline__ void blockops_body(const XView& v, int part, int J)
     }
 }
 
+// Block operators in two launches of 256-thread blocks: the substitution for
+// eight columns of G_J (one column per warp), then a row quarter of
+// Q_J = G_J M_{J,J-1} or P_J = M_{J+1,J} G_J (one entry per thread).  The
+// arithmetic of every entry and its order are those of blockops_body, so the
+// operators agree bit for bit with the one-kernel form, which forms G twice
+// per block (once for each product) in 1024-thread blocks; these split the
+// same work over four times as many smaller blocks.
+__device__ __forceinline__ void blockops_g_item(const XView& v, int J, int gq, unsigned char* smem)
+{
+    DfwTile* L = reinterpret_cast<DfwTile*>(smem);
+    const int tid = threadIdx.x, lane = tid & 31, c = 8 * gq + (tid >> 5);
+    tile_copy(L, v.M + xdf_tile_index(v, J, J), tid, blockDim.x);
+    cp_commit();
+    cp_wait<0>();
+    block_sync();
+    df s = (lane == c) ? df{1.f, 0.f} : df{0.f, 0.f};
+    int E = (lane == c) ? 0 : WEF_ZERO_E;
+    for (int t = c; t < 31; ++t) {
+        const float gh = __shfl_sync(0xffffffffu, s.h, t);
+        const float gl = __shfl_sync(0xffffffffu, s.l, t);
+        const int ge = __shfl_sync(0xffffffffu, E, t);
+        if (lane > t) {
+            const int q = RIDX(lane, t);
+            const int k = L->e[q] + ge;
+            if (k > E) {
+                const float f = pow2f(E - k);
+                s.h = __fmul_rn(s.h, f);
+                s.l = __fmul_rn(s.l, f);
+                E = k;
+            }
+            acc_term(s, L->h[q], L->l[q], gh, gl, pow2f(k - E));
+        }
+    }
+    const int q = RIDX(lane, c);
+    const dfw g = (lane >= c && E > WEF_ZERO_E / 2) ? dfw_norm(fast_two_sum(s.h, s.l), E) : dfw_zero();
+    v.G[J].h[q] = g.h;
+    v.G[J].l[q] = g.l;
+    v.G[J].e[q] = g.e;
+}
+
+// Row quarter `qr` (rows 8 qr .. 8 qr + 7) of Q_J (part 0) or P_J (part 1);
+// G_J has been published.
+__device__ __forceinline__ void blockops_prod_item(const XView& v, int J, int part, int qr, unsigned char* smem)
+{
+    DfwTile* G = reinterpret_cast<DfwTile*>(smem);
+    DfwTile* Mt = G + 1;
+    const int tid = threadIdx.x;
+    const bool on = part == 0 ? J >= 1 : J + 1 < v.nb;
+    if (on) {
+        tile_copy(G, v.G + J, tid, blockDim.x);
+        tile_copy(Mt, v.M + (part == 0 ? xdf_tile_index(v, J, J - 1) : xdf_tile_index(v, J + 1, J)), tid, blockDim.x);
+        cp_commit();
+        cp_wait<0>();
+    }
+    block_sync();
+    const int r = 8 * qr + (tid >> 5), c = tid & 31, o = RIDX(r, c);
+    dfw x = dfw_zero();
+    if (on) x = part == 0 ? dot_mat8(G, Mt, r, c, 0, (r + 8) & ~7) : dot_mat8(Mt, G, r, c, 0, 32);
+    XTile* dst = (part == 0 ? v.Q : v.P) + J;
+    dst->h[o] = x.h;
+    dst->l[o] = x.l;
+    dst->e[o] = x.e;
+}
+
+// grid (4, nb): part blockIdx.x of G_J, J = blockIdx.y
+__global__ void __launch_bounds__(256) xdf_gparts_kernel(XView v)
+{
+    __shared__ __align__(16) unsigned char sm[sizeof(DfwTile)];
+    blockops_g_item(v, blockIdx.y, blockIdx.x, sm);
+}
+
+// grid (8, nb): Q_J quarters 0-3, then P_J quarters 0-3, J = blockIdx.y
+__global__ void __launch_bounds__(256) xdf_prods_kernel(XView v)
+{
+    __shared__ __align__(16) unsigned char sm[2 * sizeof(DfwTile)];
+    blockops_prod_item(v, blockIdx.y, blockIdx.x >> 2, blockIdx.x & 3, sm);
+}
+
 constexpr int XDF_BLOCKOPS_T = 1024;  // one warp per column of G
 // With gridDim.y = 2, two blocks per diagonal block J (blockIdx.y = part):
 // the G recurrence is short next to the two 32 x 32 products, so each block
@@ -2099,9 +2177,11 @@ cudaError_t xdf_launch_forward(const XView& v, cudaStream_t st, ProfMarks* pm, c
         return r;
     });
     if (e != cudaSuccess) return e;
-    // two blocks per diagonal block while 2 nb blocks fit one wave (two 1024-thread blocks per SM)
-    xdf_blockops_kernel<<<dim3(v.nb, v.nb <= 152 ? 2 : 1), XDF_BLOCKOPS_T, blockops_smem(), st>>>(v);
-    prof_mark(pm, "exch_blockops", st);
+    // block operators: G_J in 8-column parts, then the row quarters of Q_J and P_J
+    xdf_gparts_kernel<<<dim3(4, v.nb), 256, 0, st>>>(v);
+    prof_mark(pm, "exch_gparts", st);
+    xdf_prods_kernel<<<dim3(8, v.nb), 256, 0, st>>>(v);
+    prof_mark(pm, "exch_prods", st);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // the helper and force-worker blocks form the band sums at their end

@@ -42,6 +42,27 @@ def test_exchange_forces_and_potential(N, P, d, beta, xi, table, arith):
     S.close()
 
 
+@pytest.mark.parametrize("N,P,d", [(40, 8, 2), (300, 4, 2), (129, 4, 3)])
+def test_first_launch_with_force_workers(N, P, d):
+    """The forces formed when the buffers are bound -- the first recursion
+    launch on a workspace that still holds another system's factors and
+    operators -- match the oracle with force workers in the launch: no item
+    reads a factor tile, operator or band tile before this launch wrote it."""
+    import paper_2404_02628_gb300 as pkg
+    beta, xi, g, s = 2.0, 1.0, 3.0, 0.5
+    # leave another configuration's workspace in the allocator's cache
+    T = make_system(N, P, d, 3.0, 1.0, 1.0, s, 0.5, beads(N, P, d, 7))
+    T.step(2)
+    T.close()
+    del T
+    r = beads(N, P, d, 130 + N)
+    S = make_system(N, P, d, beta, 1.0, g, s, xi, r)
+    assert S.tuning()["force_blocks"] > 0
+    Fo, _ = oracle.forces(r, beta, xi, 1.0, amplitude(g, s), s)
+    assert rel_inf(S.forces_array(), Fo) < TOL64
+    S.close()
+
+
 @pytest.mark.parametrize("W", [2, 3, 4, 5])
 @pytest.mark.parametrize("N,xi", [(700, 1.0), (450, 0.5)])
 def test_exchange_band_widths(N, xi, W):
