@@ -242,15 +242,19 @@ const char* pimd_profile_slot_name(pimd_t ctx, int slot);
  * block of 64, 128 or 256 particles, and (double-float recursion with
  * g != 0) the split of the SMs between recursion helper blocks and force
  * workers that compute springs and trap + pair forces inside the recursion
- * launch -- and keeps the fastest.  cache_path
+ * launch, and the number of helper partial sums per block (2, 3 or 4) --
+ * and keeps the fastest.  cache_path
  * (nullable): a text file of "device problem|choice" lines; a hit skips the
  * timing, a miss appends the new choice.  The step graph is re-captured on
  * the next pimd_step.  Synchronises. */
 pimd_status pimd_autotune(pimd_t ctx, const char* cache_path);
 /* The current tuned values (host only).  helpers: recursion helper blocks;
  * force_blocks: force-worker blocks in the recursion launch (0: springs and
- * pairs run as kernels of their own).  helpers and force_blocks may be NULL. */
-pimd_status pimd_tuning(pimd_t ctx, int* exch_band, int* pair_block, int* helpers, int* force_blocks);
+ * pairs run as kernels of their own); streams: helper partial sums per block
+ * of the double-float recursion (the off-band tiles of a block row or column
+ * are dealt to that many helper items, 1..4; default 3).  helpers,
+ * force_blocks and streams may be NULL. */
+pimd_status pimd_tuning(pimd_t ctx, int* exch_band, int* pair_block, int* helpers, int* force_blocks, int* streams);
 
 /* Debug cross-check (Sec. III, the O(N^3 P) evaluation the paper replaces
  * by its quadratic algorithm): every cycle energy E^[u,v], 1 <= u <= v <= N,

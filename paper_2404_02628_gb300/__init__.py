@@ -140,7 +140,7 @@ _SIGS = {
     "pimd_batch_schedule": ([_vp, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "pimd_init_state": ([_vp, ctypes.c_ulonglong], ctypes.c_int),
     "pimd_batch_init_state": ([_vp, ctypes.c_ulonglong], ctypes.c_int),
-    "pimd_tuning": ([_vp] + [ctypes.POINTER(ctypes.c_int)] * 4, ctypes.c_int),
+    "pimd_tuning": ([_vp] + [ctypes.POINTER(ctypes.c_int)] * 5, ctypes.c_int),
     "pimd_batch_autotune": ([_vp, ctypes.c_char_p], ctypes.c_int),
     "pimd_cycle_energies_naive": ([_vp, _vp, ctypes.c_int], ctypes.c_int),
     "pimd_set_species": ([_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
@@ -481,9 +481,11 @@ def pimd_autotune(h, cache_path=None):
 
 
 def pimd_tuning(h):
-    W, T, H, F = (ctypes.c_int() for _ in range(4))
-    _check(lib().pimd_tuning(h, ctypes.byref(W), ctypes.byref(T), ctypes.byref(H), ctypes.byref(F)), h)
-    return {"exch_band": W.value, "pair_block": T.value, "helpers": H.value, "force_blocks": F.value}
+    W, T, H, F, S = (ctypes.c_int() for _ in range(5))
+    _check(lib().pimd_tuning(h, ctypes.byref(W), ctypes.byref(T), ctypes.byref(H), ctypes.byref(F),
+                             ctypes.byref(S)), h)
+    return {"exch_band": W.value, "pair_block": T.value, "helpers": H.value, "force_blocks": F.value,
+            "streams": S.value}
 
 
 def probe_chain_latency(split=2, nblk=4, n_iter=400, seed=0, device="cuda"):

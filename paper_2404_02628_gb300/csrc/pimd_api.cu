@@ -116,7 +116,10 @@ int default_helpers(const pimd_config& cfg)
     return sms > 4 ? sms - 2 : 2;
 }
 
-constexpr int EX_STREAMS = 4;
+constexpr int EX_STREAMS = 4;  // helper-partial streams per block the workspace holds
+// streams a single system's double-float recursion uses before autotuning
+// (at most EX_STREAMS; measured best or near it at N = 1600 and 10000)
+constexpr int XDF_STREAMS_DEFAULT = 3;
 
 // Workspace regions of the double-float exchange path.
 struct XLayout {
@@ -234,6 +237,7 @@ struct pimd_ctx {
     int n_help;
     int pair_t = 128;  // pair-kernel block size (pimd_autotune)
     int n_force = 0;   // force-worker blocks folded into the recursion launch (0: separate kernels)
+    int n_streams = XDF_STREAMS_DEFAULT;  // helper-partial streams per block of the recursion (1..EX_STREAMS)
     struct HostReport {  // pinned: device error word, non-finite flag and scalar slots, read in one round trip
         int err, flag;
         double sc[SC_COUNT];
@@ -419,7 +423,7 @@ static void ctx_views(pimd_ctx* c)
         const double* rP = b->r + (size_t)(c->P - 1) * c->d * np + c->sp_off[sp];
         const double* r1 = b->r + c->sp_off[sp];
         if (c->use_df) {
-            c->xds[sp] = xdf_view((char*)b->work, c->xls[sp], c->sp_n[sp], c->P, c->d, c->beta, c->xi, EX_STREAMS,
+            c->xds[sp] = xdf_view((char*)b->work, c->xls[sp], c->sp_n[sp], c->P, c->d, c->beta, c->xi, c->n_streams,
                                   cfg_band(c->cfg), c->cfg.table_mode == PIMD_TABLE_STORE, rP, r1, np, np,
                                   c->cfg.spin_limit, c->n_help);
             if (sp > 0) {
@@ -924,7 +928,7 @@ extern "C" pimd_status pimd_autotune(pimd_t c, const char* cache_path)
              c->cfg.precision, c->cfg.exchange_arith, c->cfg.table_mode, c->xi == 0.0, c->A == 0.0, c->nsp);
     const std::string key = device_key() + " " + kb;
     std::string val;
-    int bestW = cfg_band(c->cfg), bestT = c->pair_t, bestH = c->n_help, bestF = c->n_force;
+    int bestW = cfg_band(c->cfg), bestT = c->pair_t, bestH = c->n_help, bestF = c->n_force, bestS = c->n_streams;
     const int sms = device_sms();
     const bool can_fold = c->use_df && c->A != 0.0 && c->xi != 0.0 && c->nsp == 1;
     if (cache_lookup(cache_path, key, val)) {
@@ -932,6 +936,7 @@ extern "C" pimd_status pimd_autotune(pimd_t c, const char* cache_path)
         bestT = cache_field(val, "pair_t", bestT);
         bestH = cache_field(val, "help", bestH);
         bestF = cache_field(val, "fold", bestF);
+        bestS = cache_field(val, "S", bestS);
     } else {
         std::vector<int> Ws, Ts;
         if (c->use_df && c->xi != 0.0) {
@@ -957,40 +962,49 @@ extern "C" pimd_status pimd_autotune(pimd_t c, const char* cache_path)
             }
             for (int H : Hs) shapes.push_back({c->pair_t, H, sms - 2 - H});
         }
+        // helper-partial streams per block of the double-float recursion
+        std::vector<int> Ss;
+        if (c->use_df && c->xi != 0.0) Ss = {2, 3, 4};
+        else Ss = {c->n_streams};
         double best = 1e30;
         const int W0 = c->cfg.exch_band;
         for (int W : Ws)
-            for (const Shape& sh : shapes) {
-                c->cfg.exch_band = W;
-                c->pair_t = sh.T;
-                c->n_help = sh.H;
-                c->n_force = sh.F;
-                ctx_views(c);
-                pimd_status st = PIMD_OK;
-                const double ms = time_ms(c->st, 5, [&] {
-                    if (st == PIMD_OK) st = enqueue_forces(c, c->st, c->buf.f, true, true);
-                });
-                if (st != PIMD_OK) return st;
-                if (ms < best) {
-                    best = ms;
-                    bestW = W;
-                    bestT = sh.T;
-                    bestH = sh.H;
-                    bestF = sh.F;
+            for (const Shape& sh : shapes)
+                for (int S : Ss) {
+                    c->cfg.exch_band = W;
+                    c->pair_t = sh.T;
+                    c->n_help = sh.H;
+                    c->n_force = sh.F;
+                    c->n_streams = S;
+                    ctx_views(c);
+                    pimd_status st = PIMD_OK;
+                    const double ms = time_ms(c->st, 5, [&] {
+                        if (st == PIMD_OK) st = enqueue_forces(c, c->st, c->buf.f, true, true);
+                    });
+                    if (st != PIMD_OK) return st;
+                    if (ms < best) {
+                        best = ms;
+                        bestW = W;
+                        bestT = sh.T;
+                        bestH = sh.H;
+                        bestF = sh.F;
+                        bestS = S;
+                    }
                 }
-            }
         c->cfg.exch_band = W0;
         char vb[96];
-        snprintf(vb, sizeof vb, "W=%d;pair_t=%d;help=%d;fold=%d", bestW, bestT, bestH, bestF);
+        snprintf(vb, sizeof vb, "W=%d;pair_t=%d;help=%d;fold=%d;S=%d", bestW, bestT, bestH, bestF, bestS);
         cache_store(cache_path, key, vb);
     }
-    if (bestW < 2 || bestW > XDF_MAXW || !pair_block_ok(bestT) || bestH < 2 || bestF < 0 ||
+    if (bestW < 2 || bestW > XDF_MAXW || !pair_block_ok(bestT) || bestH < 2 || bestF < 0 || bestS < 1 ||
+        bestS > EX_STREAMS ||
         (bestF > 0 && (!can_fold || 2 + bestH + bestF > sms)))
         return fail(c, PIMD_EINVAL, "pimd_autotune: bad cache entry");
     if (c->use_df && xdf_footprint(c, bestW) > xdf_footprint(c, cfg_band(c->cfg)))
         bestW = cfg_band(c->cfg);  // cached choice does not fit this workspace
     c->cfg.exch_band = bestW;
     c->pair_t = bestT;
+    c->n_streams = bestS;
     c->n_help = bestH;
     c->n_force = bestF;
     ctx_layout(c);
@@ -1001,13 +1015,15 @@ extern "C" pimd_status pimd_autotune(pimd_t c, const char* cache_path)
     return check_device_error(c);
 }
 
-extern "C" pimd_status pimd_tuning(pimd_t c, int* exch_band, int* pair_block, int* helpers, int* force_blocks)
+extern "C" pimd_status pimd_tuning(pimd_t c, int* exch_band, int* pair_block, int* helpers, int* force_blocks,
+                                   int* streams)
 {
     if (!c || !exch_band || !pair_block) return fail(c, PIMD_EINVAL, "pimd_tuning: NULL argument");
     *exch_band = cfg_band(c->cfg);
     *pair_block = c->pair_t;
     if (helpers) *helpers = c->n_help;
     if (force_blocks) *force_blocks = c->n_force;
+    if (streams) *streams = c->n_streams;
     return PIMD_OK;
 }
 

@@ -54,6 +54,37 @@ def test_every_candidate_gives_the_same_forces(tmp_path, prec, tol):
                 assert rel_inf(F, ref) < tol, (W, T)
 
 
+@pytest.mark.parametrize("N,P,d,g", [(700, 8, 2, 3.0), (1100, 4, 3, 0.0), (129, 6, 1, 3.0)])
+def test_every_stream_count_matches_oracle(tmp_path, N, P, d, g):
+    """Helper partial sums per block S = 1..4 (the autotuner's choice is
+    forced through its cache file): forces and V agree with the oracle at
+    1e-10 and with one another to rounding order."""
+    import paper_2404_02628_gb300 as pkg
+    beta, xi, s = 2.0, 0.8, 0.5
+    r = beads(N, P, d, 1730 + N)
+    Fo, info = oracle.forces(r, beta, xi, 1.0, amplitude(g, s), s)
+    ref = None
+    for S_ in (1, 2, 3, 4):
+        Sy = pkg.System(N, P, d, beta, 1.0, g, s, xi, r=r)
+        probe = str(tmp_path / ("probe_s%d_%d.txt" % (N, S_)))
+        t0 = Sy.autotune(probe)
+        key = open(probe).read().split("|")[0]
+        forced = str(tmp_path / ("forced_s%d_%d.txt" % (N, S_)))
+        open(forced, "w").write("%s|W=%d;pair_t=%d;help=%d;fold=%d;S=%d\n" % (
+            key, t0["exch_band"], t0["pair_block"], t0["helpers"], t0["force_blocks"], S_))
+        t = Sy.autotune(forced)
+        assert t["streams"] == S_
+        V = Sy.forces()
+        F = Sy.forces_array()
+        Sy.close()
+        assert rel_inf(F, Fo) < 1e-10, S_
+        assert abs(V - (info["V_xi"] + info["U_over_P"])) < 1e-10 * abs(V), S_
+        if ref is None:
+            ref = F
+        else:
+            assert rel_inf(F, ref) < 1e-12, S_
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("N,P,d", [(1600, 32, 2), (257, 6, 3), (1000, 4, 1)])
 def test_folded_force_workers_match_oracle(tmp_path, prec, N, P, d):
