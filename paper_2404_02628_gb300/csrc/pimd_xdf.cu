@@ -551,92 +551,18 @@ __global__ void __launch_bounds__(256) xdf_table_kernel(XView v, long long ntile
 // ------------------------------------------------------------------------
 // block operators: G_J = (I - M_JJ)^{-1}, Q_J = G_J M_{J,J-1}, P_J = M_{J+1,J} G_J
 
-// part 0: G_J and Q_J; part 1: P_J (G_J recomputed); part -1: all three.
-__device__ __forceinline__ void blockops_body(const XView& v, int part, int J)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    DfwTile* L = reinterpret_cast<DfwTile*>(smem_raw);
-    DfwTile* G = L + 1;
-    DfwTile* Ms = L + 2;
-    DfwTile* Mp = L + 3;
-    if (J >= v.nb) return;  // a block past this replica's blocks
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    {
-        const long long t = xdf_tile_index(v, J, J);
-        tile_copy(L, v.M + t, threadIdx.x, blockDim.x);
-        if (J >= 1 && part != 1) {
-            const long long ts = xdf_tile_index(v, J, J - 1);
-            tile_copy(Ms, v.M + ts, threadIdx.x, blockDim.x);
-        }
-        if (J + 1 < v.nb && part != 0) {
-            const long long tp = xdf_tile_index(v, J + 1, J);
-            tile_copy(Mp, v.M + tp, threadIdx.x, blockDim.x);
-        }
-        cp_commit();
-        cp_wait<0>();
-    }
-    block_sync();
-    // G = (I - L)^{-1} by forward substitution, one column per warp (lane =
-    // row; 32 warps, all columns at once): after step t, lane t holds its
-    // final G[t][c], which is broadcast and applied to the rows below.  Every
-    // entry is non-negative, so each lane keeps a compensated sum s relative
-    // to a running exponent E (s >= 1 once non-zero, far from the FP32 limits)
-    // and adds one term per step; the raw (s, E) of lane t is what is broadcast.
-    for (int c = w; c < 32; c += blockDim.x >> 5) {
-        df s = (lane == c) ? df{1.f, 0.f} : df{0.f, 0.f};
-        int E = (lane == c) ? 0 : WEF_ZERO_E;
-        for (int t = c; t < 31; ++t) {
-            const float gh = __shfl_sync(0xffffffffu, s.h, t);
-            const float gl = __shfl_sync(0xffffffffu, s.l, t);
-            const int ge = __shfl_sync(0xffffffffu, E, t);
-            if (lane > t) {
-                const int q = RIDX(lane, t);
-                const int k = L->e[q] + ge;
-                if (k > E) {
-                    const float f = pow2f(E - k);
-                    s.h = __fmul_rn(s.h, f);
-                    s.l = __fmul_rn(s.l, f);
-                    E = k;
-                }
-                acc_term(s, L->h[q], L->l[q], gh, gl, pow2f(k - E));
-            }
-        }
-        const dfw g = (lane >= c && E > WEF_ZERO_E / 2) ? dfw_norm(fast_two_sum(s.h, s.l), E) : dfw_zero();
-        tile_put(G, lane, c, g);
-    }
-    block_sync();
-    // Q = G M_{J,J-1} (G lower triangular: t <= r, r uniform over a warp) and
-    // P = M_{J+1,J} G (all t; the zeros of G add nothing, and every lane runs
-    // the same range)
-    for (int q = threadIdx.x; q < 1024; q += blockDim.x) {
-        const int r = q >> 5, c = q & 31, o = RIDX(r, c);
-        if (part != 1) {
-            v.G[J].h[o] = G->h[o];
-            v.G[J].l[o] = G->l[o];
-            v.G[J].e[o] = G->e[o];
-            dfw Q = dfw_zero();
-            if (J >= 1) Q = dot_mat8(G, Ms, r, c, 0, (r + 8) & ~7);
-            v.Q[J].h[o] = Q.h;
-            v.Q[J].l[o] = Q.l;
-            v.Q[J].e[o] = Q.e;
-        }
-        if (part != 0) {
-            dfw Pm = dfw_zero();
-            if (J + 1 < v.nb) Pm = dot_mat8(Mp, G, r, c, 0, 32);
-            v.P[J].h[o] = Pm.h;
-            v.P[J].l[o] = Pm.l;
-            v.P[J].e[o] = Pm.e;
-        }
-    }
-}
-
-// Block operators in two launches of 256-thread blocks: the substitution for
-// eight columns of G_J (one column per warp), then a row quarter of
-// Q_J = G_J M_{J,J-1} or P_J = M_{J+1,J} G_J (one entry per thread).  The
-// arithmetic of every entry and its order are those of blockops_body, so the
-// operators agree bit for bit with the one-kernel form, which forms G twice
-// per block (once for each product) in 1024-thread blocks; these split the
-// same work over four times as many smaller blocks.
+// Two launches of 256-thread blocks: the substitution for eight columns of
+// G_J (one column per warp), then a row quarter of Q_J = G_J M_{J,J-1} or
+// P_J = M_{J+1,J} G_J (one entry per thread).  Many small blocks keep the
+// SMs busy where one 1024-thread block per operator set left a third of
+// them idle.
+//
+// G = (I - L)^{-1} by forward substitution, lane = row: after step t, lane t
+// holds its final G[t][c], which is broadcast and applied to the rows below.
+// Every entry is non-negative, so each lane keeps a compensated sum s
+// relative to a running exponent E (s >= 1 once non-zero, far from the FP32
+// limits) and adds one term per step; the raw (s, E) of lane t is what is
+// broadcast.
 __device__ __forceinline__ void blockops_g_item(const XView& v, int J, int gq, unsigned char* smem)
 {
     DfwTile* L = reinterpret_cast<DfwTile*>(smem);
@@ -708,14 +634,6 @@ __global__ void __launch_bounds__(256) xdf_prods_kernel(XView v)
     blockops_prod_item(v, blockIdx.y, blockIdx.x >> 2, blockIdx.x & 3, sm);
 }
 
-constexpr int XDF_BLOCKOPS_T = 1024;  // one warp per column of G
-// With gridDim.y = 2, two blocks per diagonal block J (blockIdx.y = part):
-// the G recurrence is short next to the two 32 x 32 products, so each block
-// redoes it.
-__global__ void __launch_bounds__(XDF_BLOCKOPS_T) xdf_blockops_kernel(XView v)
-{
-    blockops_body(v, gridDim.y == 2 ? (int)blockIdx.y : -1, blockIdx.x);
-}
 
 // ------------------------------------------------------------------------
 // recursion: chain blocks and helpers
@@ -1979,11 +1897,21 @@ __global__ void __launch_bounds__(256) table_flat(const RepArgs* ra, const int2*
     }
 }
 
-// Block operators of every replica, one block per (replica, diagonal block) pair of a flat list.
-__global__ void __launch_bounds__(XDF_BLOCKOPS_T) blockops_flat(const RepArgs* ra, const int2* list)
+// Block operators of every replica over a flat list of (replica, diagonal
+// block) pairs: G_J in 8-column parts (grid (4, n)), then Q_J and P_J in row
+// quarters (grid (8, n)).
+__global__ void __launch_bounds__(256) gparts_flat(const RepArgs* ra, const int2* list)
 {
-    const int2 e = list[blockIdx.x];
-    blockops_body(ra[e.x].xv, -1, e.y);
+    __shared__ __align__(16) unsigned char sm[sizeof(DfwTile)];
+    const int2 e = list[blockIdx.y];
+    blockops_g_item(ra[e.x].xv, e.y, blockIdx.x, sm);
+}
+
+__global__ void __launch_bounds__(256) prods_flat(const RepArgs* ra, const int2* list)
+{
+    __shared__ __align__(16) unsigned char sm[2 * sizeof(DfwTile)];
+    const int2 e = list[blockIdx.y];
+    blockops_prod_item(ra[e.x].xv, e.y, blockIdx.x >> 2, blockIdx.x & 3, sm);
 }
 
 
@@ -2156,7 +2084,6 @@ size_t xdf_recursion_smem(int W)
 }
 
 static size_t band_smem(int nw) { return nw * (sizeof(DfwTile) + sizeof(WeightSmem) + 32 * sizeof(DVAcc)); }
-static size_t blockops_smem() { return 4 * sizeof(DfwTile); }
 
 cudaError_t xdf_launch_forward(const XView& v, cudaStream_t st, ProfMarks* pm, const ForceWork* fw, int n_force)
 {
@@ -2169,12 +2096,8 @@ cudaError_t xdf_launch_forward(const XView& v, cudaStream_t st, ProfMarks* pm, c
     prof_mark(pm, "exch_table", st);
     static DeviceOnce attr_once;
     cudaError_t e = device_once(attr_once, [] {
-        cudaError_t r = cudaFuncSetAttribute(xdf_blockops_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)blockops_smem());
-        if (r == cudaSuccess)
-            r = cudaFuncSetAttribute(xdf_recursion_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)xdf_recursion_smem(XDF_MAXW));
-        return r;
+        return cudaFuncSetAttribute(xdf_recursion_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)xdf_recursion_smem(XDF_MAXW));
     });
     if (e != cudaSuccess) return e;
     // block operators: G_J in 8-column parts, then the row quarters of Q_J and P_J
@@ -2256,8 +2179,6 @@ cudaError_t batch_launch_exchange(const RepArgs* ra, const BatchGrid& g, cudaStr
         cudaError_t r = cudaFuncSetAttribute(xsolo_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsolo_smem());
         if (r == cudaSuccess)
             r = cudaFuncSetAttribute(band_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)band_smem(8));
-        if (r == cudaSuccess)
-            r = cudaFuncSetAttribute(blockops_flat, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)blockops_smem());
         return r;
     });
     if (e != cudaSuccess) return e;
@@ -2274,10 +2195,7 @@ cudaError_t batch_launch_exchange(const RepArgs* ra, const BatchGrid& g, cudaStr
     return cudaGetLastError();
 }
 
-static size_t persistent_smem()
-{
-    return std::max(std::max(xsolo_smem(), band_smem(8)), blockops_smem());
-}
+static size_t persistent_smem() { return std::max(xsolo_smem(), band_smem(8)); }
 
 cudaError_t batch_launch_exchange_persistent(const RepArgs* ra, const BatchSched& sc, int blocks, cudaStream_t st)
 {
@@ -2294,14 +2212,9 @@ cudaError_t batch_launch_exchange_persistent(const RepArgs* ra, const BatchSched
 // prep, factor tiles and block operators of every replica (flat lists, no idle blocks)
 cudaError_t batch_launch_prep_tables_ops(const RepArgs* ra, const BatchGrid& g, cudaStream_t st, ProfMarks* pm)
 {
-    static DeviceOnce attr_once;
-    cudaError_t e = device_once(attr_once, [] {
-        return cudaFuncSetAttribute(blockops_flat, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)blockops_smem());
-    });
-    if (e != cudaSuccess) return e;
     prep_batch<<<dim3(g.gx_prep, 1, g.R), XDF_SMALL_T, 0, st>>>(ra);
     prof_mark(pm, "batch_exch_prep", st);
-    e = batch_launch_tables_ops(ra, g, st, pm);
+    cudaError_t e = batch_launch_tables_ops(ra, g, st, pm);
     return e;
 }
 
@@ -2314,7 +2227,10 @@ cudaError_t batch_launch_tables_ops(const RepArgs* ra, const BatchGrid& g, cudaS
         else table_flat<3><<<grid, 256, 0, st>>>(ra, g.tiles, g.n_tiles);
     }
     prof_mark(pm, "batch_exch_table", st);
-    if (g.n_blocks > 0) blockops_flat<<<g.n_blocks, XDF_BLOCKOPS_T, blockops_smem(), st>>>(ra, g.blocks);
+    if (g.n_blocks > 0) {
+        gparts_flat<<<dim3(4, g.n_blocks), 256, 0, st>>>(ra, g.blocks);
+        prods_flat<<<dim3(8, g.n_blocks), 256, 0, st>>>(ra, g.blocks);
+    }
     prof_mark(pm, "batch_exch_blockops", st);
     return cudaGetLastError();
 }
