@@ -15,7 +15,7 @@
  *   r[((l-1)*P + (j-1))*d + c]  =  component c of bead j of particle l.
  * Forces use the same layout.
  *
- * Readings of the paper taken here (each also listed in the design doc):
+ * Readings of the paper taken here:
  *  - spring constant m*omega_P^2 = P/beta^2           (Sec. III, omega_P = sqrt(P)/(beta hbar))
  *  - forward base case V^[1,0] = 0                     (Sec. III, forward recursion)
  *  - backward base case V^[N+1,N] = 0 (printed "V^[N,N]=0" contradicts the
