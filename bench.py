@@ -145,7 +145,7 @@ class ClockSampler:
 # roofline bookkeeping: algorithmic work per launch of each kernel
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
-# ncu capture of the gauss1600 bench command (profiles/xdf_recursion_gauss1600_full.md),
+# ncu capture of the gauss1600 bench command (the recursion kernel's capture summary under profiles/),
 # valid only while the kernel's source files are unchanged (first 16 hex digits of the
 # SHA-256 of their concatenation at capture time); otherwise the roofline line
 # reports traffic null.
